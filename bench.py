@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of the matrix-free neo-Hookean tangent application on one GB300.
+
+One step = one application v = A(u) du of the constrained tangent operator (Algorithm 1 /
+its cached-point variant) on the Q2 64^3 unit-cube workload (6,440,067 DoFs), FP64.
+`value` is whole-job GDoF/s (DoFs per step / device time per step, summed over replicas).
+
+Also printed on the same JSON line: the other strategies and precisions and the Q4 32^3
+companion workload (`variants`), the roofline of the apply kernel, an end-to-end number
+through the C ABI with host buffers, the CPU oracle timed on a bounded sample, clocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nhmf_inputs as inp  # noqa: E402
+
+METRIC = "tangent-apply GDoF/s (FP64, FP32) and Newton time to 1e-8 vs plain FP64 CG"
+MAIN = "q2_64_clamp"
+COMPANION = "q4_32_clamp"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP64: 2 DFMA per clock per SM (measured 1.20 TFLOP/s on this GPU with an FMA loop);
+# FP32: 128 FFMA per clock per SM.  Peaks at the maximum SM clock.
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def canonical_flops(w: inp.Workload, strategy: str) -> float:
+    """Algorithmic FLOPs of one apply: 2 n^4 per 1D pass per scalar field per element
+    (54 passes on the fly: 18 for u, 18 for du, 18 back; 36 cached) plus the point code
+    (230 FLOP per point on the fly, 150 cached; FMA = 2)."""
+    n = w.degree + 1
+    passes, point = (54, 230) if strategy == "otf" else (36, 150)
+    return w.n_elements * passes * 2 * n ** 4 + w.n_qp * point
+
+
+def compulsory_bytes(w: inp.Workload, strategy: str, b: int) -> float:
+    """Bytes one apply must move: u, du, v (on the fly) or du, v and the 10-value cache."""
+    if strategy == "otf":
+        return 3 * b * w.n_dofs
+    return 2 * b * w.n_dofs + 10 * b * w.n_qp
+
+
+def describe(w: inp.Workload) -> str:
+    u = "u=(h/p)U(+-%g)" % w.u_amp if w.u_rule == "scaled" else "u=U(+-%g)" % w.u_amp
+    du = "du~N(0,1)" if w.du_rule == "normal" else "du=U(+-%g)" % w.du_amp
+    bc = {0: "no Dirichlet", 1: "clamp x=0", 2: "compression"}[w.bc]
+    return (f"Q{w.degree} hex {w.n_el}^3 unit cube ({w.n_dofs:,} DoFs, {w.n_qp:,} Gauss points), "
+            f"mu={w.mu:g}, lambda={w.lam:g}, {bc}, {u}, {du}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[3], parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3][1:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(w: inp.Workload, u, du, budget_s: float, max_elems: int):
+    """Time the oracle's apply on growing element samples until `budget_s` is spent."""
+    from oracle.fem import Operator
+    from oracle.mesh import Mesh
+    op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
+    n = 256
+    spent, elems_done = 0.0, 0
+    while spent < budget_s and n <= max_elems:
+        t0 = time.perf_counter()
+        op.apply(u, du, elems=np.arange(n))
+        dt = time.perf_counter() - t0
+        spent += dt
+        elems_done += n
+        n *= 2
+    gdofs = elems_done / w.n_elements * w.n_dofs / spent / 1e9
+    return gdofs, elems_done, spent
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = inp.WORKLOADS[MAIN]
+    u, du = inp.draw_u(w), inp.draw_du(w)
+    from oracle.fem import Operator
+    from oracle.mesh import Mesh
+    op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
+    sample = 512                      # elements per step: a bounded sample of the workload
+    for _ in range(args.warmup):
+        op.apply(u, du, elems=np.arange(sample))
+    times = []
+    for k in range(args.steps):
+        el = (np.arange(sample) + k * sample) % w.n_elements
+        t0 = time.perf_counter()
+        op.apply(u, du, elems=el)
+        times.append(time.perf_counter() - t0)
+    step = sum(times) / len(times)
+    value = sample / w.n_elements * w.n_dofs / step / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{MAIN}: " + describe(w) + "; FP64 tangent apply",
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of {w.n_elements} elements per step (FP64 NumPy oracle, "
+                                   "explicit L per point, single thread), scaled to DoFs"},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU
+def time_applies(torch, prob, nhmf, du, v, prec, strat, steps, flush):
+    """Mean device time per apply (ms) with an L2 flush between steps, and kernel-only time."""
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    nhmf.nhmf_profile_read(prob.ctx, nhmf.NHMF_KIND_APPLY)
+    nhmf.nhmf_profile_enable(prob.ctx, 1)
+    for a, b in ev:
+        flush.add_(1.0)
+        a.record(st)
+        prob.apply(du, v, prec, strat)
+        b.record(st)
+    torch.cuda.synchronize()
+    nhmf.nhmf_profile_enable(prob.ctx, 0)
+    kms, launches = nhmf.nhmf_profile_read(prob.ctx, nhmf.NHMF_KIND_APPLY)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return step_ms, kms / steps, launches
+
+
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2505_15535_gb300 import nhmf
+
+    dev = torch.device("cuda", local)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    strategy = args.strategy
+    strat = nhmf.NHMF_CACHED if strategy == "cached" else nhmf.NHMF_ON_THE_FLY
+
+    w = inp.WORKLOADS[MAIN]
+    u, du = inp.draw_u(w), inp.draw_du(w)
+    prob = nhmf.Problem.from_workload(w)
+    ut = torch.from_numpy(u).to(dev)
+    t0 = time.perf_counter()
+    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    torch.cuda.synchronize()
+    cache_build_s = time.perf_counter() - t0
+    dut = torch.from_numpy(du).to(dev)
+    v = torch.empty_like(dut)
+    for _ in range(args.warmup):
+        prob.apply(dut, v, nhmf.NHMF_FP64, strat)
+
+    # ---- timed region: exactly K steps
+    barrier()
+    with ClockSampler(local) as clk:
+        step_ms, kernel_ms, launches = time_applies(torch, prob, nhmf, dut, v, nhmf.NHMF_FP64, strat,
+                                                    args.steps, flush)
+        barrier()
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([step_ms, kernel_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, kernel_ms = t.tolist()
+    value = world * w.n_dofs / (step_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers
+    du_h = torch.from_numpy(du).pin_memory()
+    v_h = torch.empty(du_h.shape, dtype=torch.float64).pin_memory()
+    d_in = torch.empty_like(dut)
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        d_in.copy_(du_h, non_blocking=True); prob.apply(d_in, v, nhmf.NHMF_FP64, strat); v_h.copy_(v, non_blocking=True)
+    barrier()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(e2e_steps):
+        d_in.copy_(du_h, non_blocking=True)
+        prob.apply(d_in, v, nhmf.NHMF_FP64, strat)
+        v_h.copy_(v, non_blocking=True)
+    b.record(st)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    e2e = {"value": world * w.n_dofs / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
+           "h2d_bytes_per_step": int(du_h.numel() * 8), "d2h_bytes_per_step": int(v_h.numel() * 8)}
+
+    # ---- roofline of the apply kernel (FP64 pipe)
+    flops = canonical_flops(w, strategy)
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": f"k_apply<2,double,{strategy}> (8 colour launches per apply)",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz (FMA loop measured 1.20)",
+                "flops_per_apply": flops}
+
+    # ---- variants (not the headline): both strategies, both precisions, both C2 meshes
+    variants = {}
+    if not args.no_variants:
+        vs = max(5, min(args.steps, 30))
+        for name in (MAIN, COMPANION):
+            wv = inp.WORKLOADS[name]
+            if name == MAIN:
+                pv, dv = prob, dut
+            else:
+                pv = nhmf.Problem.from_workload(wv)
+                pv.set_linearization(torch.from_numpy(inp.draw_u(wv)).to(dev),
+                                     nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+                dv = torch.from_numpy(inp.draw_du(wv)).to(dev)
+            for prec_name, prec, dt in (("fp64", nhmf.NHMF_FP64, torch.float64), ("fp32", nhmf.NHMF_FP32, torch.float32)):
+                x = dv.to(dt)
+                y = torch.empty_like(x)
+                for sname, sid in (("otf", nhmf.NHMF_ON_THE_FLY), ("cached", nhmf.NHMF_CACHED)):
+                    for _ in range(3):
+                        pv.apply(x, y, prec, sid)
+                    sm, km, _ = time_applies(torch, pv, nhmf, x, y, prec, sid, vs, flush)
+                    fl = canonical_flops(wv, sname)
+                    peak = FP64_PEAK_TFLOPS if prec_name == "fp64" else FP32_PEAK_TFLOPS
+                    bts = compulsory_bytes(wv, sname, 8 if prec_name == "fp64" else 4)
+                    variants[f"{name}/{prec_name}/{sname}"] = {
+                        "gdofs": wv.n_dofs / (sm * 1e-3) / 1e9, "ms": sm, "kernel_ms": km,
+                        "tflops": fl / (km * 1e-3) / 1e12, "alu_frac": fl / (km * 1e-3) / 1e12 / peak,
+                        "hbm_gbs": bts / (km * 1e-3) / 1e9}
+            if pv is not prob:
+                pv.close()
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        gd, ne, spent = oracle_sample(w, u, du, budget_s=args.cpu_seconds, max_elems=65536)
+        cpu = {"value": gd, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ne} of {w.n_elements} elements in {spent:.1f} s (FP64 NumPy oracle, explicit L "
+                         "per point, single thread), scaled to the full DoF count"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{MAIN}: " + describe(w) + f"; FP64 tangent apply, {strategy} strategy",
+                       "l2": "flushed between timed steps (256 MB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches + args.steps),   # 8 colour launches + 1 Dirichlet fix per step
+            "clocks": clocks, "cache_build_s": cache_build_s, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--strategy", choices=["cached", "otf"], default="cached")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,123 @@
+/*
+ * nhmf -- matrix-free compressible neo-Hookean finite-strain elasticity on structured
+ * Q_p hexahedral meshes of the unit cube, for one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow the paper's statement of the problem (arXiv 2505.15535):
+ *   - energy Psi = mu/2 (tr C - 3 - 2 ln J) + lambda (ln J)^2          (Eq. hypref)
+ *   - residual R(u)_i = int P(F) : Grad phi_i dV, P = dPsi/dF          (Eq. F)
+ *   - tangent  W_i = K(u; du, phi_i) = int Grad du : L : Grad phi_i dV (Eq. DF, Eq. L;
+ *     Algorithm 1 "Given u, du / Return W")
+ *   - Q_p elements with (p+1)^3 Gauss points per element               (Section 2.2, 2.4)
+ *   - operator diagonal (used by Jacobi / Chebyshev smoothing)         (Section 2.3)
+ *
+ * Discretisation readings fixed by this library:
+ *   mesh      Omega = [0,1]^3 split into N^3 cubes of side h = 1/N; Q_p on GLL nodes;
+ *             M = pN + 1 nodes per direction; (p+1)-point Gauss-Legendre rule.
+ *   vectors   caller-owned DEVICE arrays of 3*M^3 entries, component-major:
+ *             entry c*M^3 + i + M*(j + M*k) is component c at node (i, j, k), x fastest.
+ *   Dirichlet the constrained operator is A du = P_f K(u) P_f du + P_D du (identity rows and
+ *             columns on the constrained set D); residual rows on D are zero.
+ *             Presets: NHMF_BC_NONE (raw operator), NHMF_BC_CLAMP_X0 (all components on
+ *             x = 0), NHMF_BC_COMPRESSION (all components on z = 0, u_z on z = 1).
+ *
+ * Asynchrony: every call enqueues its kernels on `stream` (a cudaStream_t passed as void*;
+ * NULL = legacy default stream) and returns without waiting, unless its comment says it
+ * synchronises.  One context must not be used from two host threads at the same time.
+ *
+ * Errors: calls return an nhmf_status; no call aborts the process or traps on the device.
+ * Kernels that meet det F <= 0 or a non-finite value record it in a device status word that
+ * nhmf_check_status() (and every synchronising call) turns into NHMF_ERR_NONPOS_J /
+ * NHMF_ERR_NONFINITE.  nhmf_last_error() returns a text description of the last failure.
+ */
+#ifndef NHMF_H
+#define NHMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NHMF_OK = 0,
+  NHMF_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad enum) */
+  NHMF_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  NHMF_ERR_OOM = 3,           /* device allocation failed */
+  NHMF_ERR_NONPOS_J = 4,      /* det F <= 0 at some quadrature point */
+  NHMF_ERR_NONFINITE = 5,     /* NaN or Inf met */
+  NHMF_ERR_BREAKDOWN = 6,     /* Krylov breakdown (p^T A p <= 0) */
+  NHMF_ERR_NOT_CONVERGED = 7, /* iteration limit reached */
+  NHMF_ERR_STATE = 8          /* call out of order (e.g. apply before set_linearization) */
+} nhmf_status;
+
+enum { NHMF_FP64 = 0, NHMF_FP32 = 1 };                     /* arithmetic of an apply */
+enum { NHMF_ON_THE_FLY = 0, NHMF_CACHED = 1 };             /* the paper's two strategies */
+enum { NHMF_BC_NONE = 0, NHMF_BC_CLAMP_X0 = 1, NHMF_BC_COMPRESSION = 2 };
+enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2 };         /* bit mask for set_linearization */
+
+typedef struct nhmf_ctx nhmf_ctx;
+
+typedef struct {
+  int n_el;       /* N, elements per direction, >= 1 */
+  int degree;     /* p, 1..4 */
+  double mu;      /* shear modulus, > 0 (Eq. hypref) */
+  double lambda;  /* Lame constant, >= 0 (Eq. hypref; the energy uses lambda (ln J)^2) */
+  int bc;         /* NHMF_BC_* preset */
+  double top_uz;  /* prescribed u_z on z = 1 for NHMF_BC_COMPRESSION (solver only) */
+} nhmf_params;
+
+/* Create a context for one mesh/material on the current CUDA device.  Allocates the
+ * context's own device buffers (linearisation copy, status word).  Synchronous. */
+nhmf_status nhmf_create(const nhmf_params* params, nhmf_ctx** out);
+
+/* Free the context and every device buffer it owns.  Synchronises the device. */
+void nhmf_destroy(nhmf_ctx* ctx);
+
+/* Number of DoFs, 3*(p*N+1)^3. */
+size_t nhmf_num_dofs(const nhmf_ctx* ctx);
+
+/* Text of the last error on this context (static storage owned by the context). */
+const char* nhmf_last_error(const nhmf_ctx* ctx);
+
+/* Fix the linearisation point u (device, FP64, 3*M^3; read only, may be freed after the
+ * call) for later tangent/diagonal calls: copies u into the context and, for each bit of
+ * `cache_mask`, builds the per-quadrature-point cache of the cached strategy (Section 3.2
+ * "partial assembly"): F^-1 (9 values) and ln J (1 value) per point, computed in FP64 and
+ * stored in FP64 (NHMF_CACHE_FP64) and/or FP32 (NHMF_CACHE_FP32); 10*E*(p+1)^3 values
+ * each, layout [10][E*(p+1)^3] with elements in colour-major order.  Synchronises and
+ * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
+nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
+
+/* v = A(u) du with u the current linearisation point (Algorithm 1 for NHMF_ON_THE_FLY, the
+ * cached variant for NHMF_CACHED).  `precision` NHMF_FP64: du, v are double*; NHMF_FP32: du,
+ * v are float* and all arithmetic after the cache build runs in FP32 with FP32 accumulation.
+ * du and v are device arrays of 3*M^3 entries and must not overlap.  Asynchronous.
+ * NHMF_ERR_STATE if no linearisation point (or no cache of that precision) is set. */
+nhmf_status nhmf_tangent_apply(nhmf_ctx* ctx, int precision, int strategy, const void* du,
+                               void* v, void* stream);
+
+/* r = R(u) (Eq. F, no traction) in FP64 for the device vector u; rows on D are zero.
+ * Synchronises and returns NHMF_ERR_NONPOS_J / NHMF_ERR_NONFINITE on failure. */
+nhmf_status nhmf_residual(nhmf_ctx* ctx, const double* u, double* r, void* stream);
+
+/* d = diag(A(u)) in FP64 at the current linearisation point (1 on D).  Asynchronous. */
+nhmf_status nhmf_diagonal(nhmf_ctx* ctx, double* d, void* stream);
+
+/* Synchronise `stream`, read and clear the device status word.  Returns NHMF_OK,
+ * NHMF_ERR_NONPOS_J or NHMF_ERR_NONFINITE. */
+nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
+
+/* Kernel timing.  While enabled, every operator call records a CUDA event pair on its
+ * stream around its element kernels (the eight colour launches, not the vector memset or
+ * the Dirichlet-row fix).  nhmf_profile_read() synchronises those events, returns the summed
+ * elapsed milliseconds and the number of element-kernel launches recorded for one operator
+ * kind (NHMF_KIND_*), and clears that kind's record. */
+enum { NHMF_KIND_APPLY = 0, NHMF_KIND_CACHE = 1, NHMF_KIND_RESIDUAL = 2, NHMF_KIND_DIAGONAL = 3 };
+nhmf_status nhmf_profile_enable(nhmf_ctx* ctx, int enable);
+nhmf_status nhmf_profile_read(nhmf_ctx* ctx, int kind, double* elapsed_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NHMF_H */

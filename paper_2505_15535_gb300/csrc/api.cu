@@ -1,0 +1,190 @@
+// C ABI of the library (declarations and contracts in include/nhmf.h).
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace nhmf {
+
+nhmf_status fail(nhmf_ctx* c, nhmf_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+nhmf_status cuda_check(nhmf_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return NHMF_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? NHMF_ERR_OOM : NHMF_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static void build_geometry(const nhmf_params& p, Geometry* g) {
+  g->N = p.n_el;
+  g->p = p.degree;
+  g->n = p.degree + 1;
+  g->M = p.degree * p.n_el + 1;
+  g->M3 = (long long)g->M * g->M * g->M;
+  g->E = (long long)p.n_el * p.n_el * p.n_el;
+  g->nq = g->E * g->n * g->n * g->n;
+  g->h = 1.0 / p.n_el;
+  long long slot = 0;
+  for (int k = 0; k < 8; ++k) {
+    Colour& c = g->colour[k];
+    c.cx = k & 1;
+    c.cy = (k >> 1) & 1;
+    c.cz = (k >> 2) & 1;
+    c.nx = (p.n_el - c.cx + 1) / 2;
+    c.ny = (p.n_el - c.cy + 1) / 2;
+    c.nz = (p.n_el - c.cz + 1) / 2;
+    c.count = c.nx * c.ny * c.nz;
+    c.slot0 = slot;
+    slot += c.count;
+  }
+}
+
+static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace nhmf
+
+using namespace nhmf;
+
+extern "C" {
+
+nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
+  if (!prm || !out) return NHMF_ERR_ARG;
+  *out = nullptr;
+  if (prm->n_el < 1 || prm->n_el > 4096 || prm->degree < 1 || prm->degree > 4 || !(prm->mu > 0.0) ||
+      !(prm->lambda >= 0.0) || prm->bc < NHMF_BC_NONE || prm->bc > NHMF_BC_COMPRESSION)
+    return NHMF_ERR_ARG;
+  nhmf_ctx* c = new (std::nothrow) nhmf_ctx();
+  if (!c) return NHMF_ERR_OOM;
+  c->prm = *prm;
+  build_geometry(*prm, &c->g);
+  build_tables(prm->degree, &c->tab);
+  cudaGetDevice(&c->device);
+  nhmf_status st = cuda_check(c, cudaMalloc(&c->status, sizeof(unsigned)), "status alloc");
+  if (st == NHMF_OK) st = cuda_check(c, cudaMemset(c->status, 0, sizeof(unsigned)), "status clear");
+  if (st == NHMF_OK) st = cuda_check(c, cudaMalloc(&c->ubar, sizeof(double) * 3 * c->g.M3), "ubar alloc");
+  if (st == NHMF_OK) st = cuda_check(c, cudaMalloc(&c->ubar32, sizeof(float) * 3 * c->g.M3), "ubar32 alloc");
+  if (st != NHMF_OK) {
+    nhmf_destroy(c);
+    return st;
+  }
+  *out = c;
+  return NHMF_OK;
+}
+
+void nhmf_destroy(nhmf_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cudaFree(c->status);
+  cudaFree(c->ubar);
+  cudaFree(c->ubar32);
+  cudaFree(c->cache64);
+  cudaFree(c->cache32);
+  delete c;
+}
+
+size_t nhmf_num_dofs(const nhmf_ctx* c) { return c ? (size_t)(3 * c->g.M3) : 0; }
+
+const char* nhmf_last_error(const nhmf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  unsigned h = 0;
+  cudaStream_t s = as_stream(stream);
+  nhmf_status st = cuda_check(c, cudaMemcpyAsync(&h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status read");
+  if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "status sync");
+  if (st == NHMF_OK) st = cuda_check(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), s), "status clear");
+  if (st != NHMF_OK) return st;
+  if (h & kStatusNonPosJ) return fail(c, NHMF_ERR_NONPOS_J, "det F <= 0 at a quadrature point");
+  if (h & kStatusNonFinite) return fail(c, NHMF_ERR_NONFINITE, "non-finite value");
+  return NHMF_OK;
+}
+
+nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void* stream) {
+  if (!c || !u || mask < 0 || mask > 3) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
+  cudaStream_t s = as_stream(stream);
+  const size_t n = 3 * c->g.M3;
+  c->have_lin = false;
+  nhmf_status st = cuda_check(c, cudaMemcpyAsync(c->ubar, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "ubar copy");
+  if (st != NHMF_OK) return st;
+  if ((st = launch_to_fp32(c->ubar, c->ubar32, (long long)n, s)) != NHMF_OK)
+    return fail(c, st, "ubar fp32 copy");
+  const size_t cache_elems = 10 * (size_t)c->g.nq;
+  if ((mask & NHMF_CACHE_FP64) && !c->cache64)
+    if ((st = cuda_check(c, cudaMalloc(&c->cache64, cache_elems * sizeof(double)), "cache64 alloc")) != NHMF_OK) return st;
+  if ((mask & NHMF_CACHE_FP32) && !c->cache32)
+    if ((st = cuda_check(c, cudaMalloc(&c->cache32, cache_elems * sizeof(float)), "cache32 alloc")) != NHMF_OK) return st;
+  if (!(mask & NHMF_CACHE_FP64) && c->cache64) { cudaFree(c->cache64); c->cache64 = nullptr; }
+  if (!(mask & NHMF_CACHE_FP32) && c->cache32) { cudaFree(c->cache32); c->cache32 = nullptr; }
+  if (mask) {
+    if ((st = launch_cache_build(c, s)) != NHMF_OK) return st;
+  }
+  if ((st = nhmf_check_status(c, stream)) != NHMF_OK) return st;
+  c->have_lin = true;
+  return NHMF_OK;
+}
+
+nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!du || !v || du == v || (precision != NHMF_FP64 && precision != NHMF_FP32) ||
+      (strategy != NHMF_ON_THE_FLY && strategy != NHMF_CACHED))
+    return fail(c, NHMF_ERR_ARG, "tangent_apply: bad argument");
+  if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "tangent_apply: no linearisation point set");
+  if (strategy == NHMF_CACHED && ((precision == NHMF_FP64 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32)))
+    return fail(c, NHMF_ERR_STATE, "tangent_apply: no point cache of this precision");
+  return launch_apply(c, precision, strategy, du, v, as_stream(stream));
+}
+
+nhmf_status nhmf_residual(nhmf_ctx* c, const double* u, double* r, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!u || !r || (const void*)u == (void*)r) return fail(c, NHMF_ERR_ARG, "residual: bad argument");
+  nhmf_status st = launch_residual(c, u, r, as_stream(stream));
+  if (st != NHMF_OK) return st;
+  return nhmf_check_status(c, stream);
+}
+
+nhmf_status nhmf_diagonal(nhmf_ctx* c, double* d, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!d) return fail(c, NHMF_ERR_ARG, "diagonal: bad argument");
+  if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "diagonal: no linearisation point set");
+  return launch_diagonal(c, d, as_stream(stream));
+}
+
+nhmf_status nhmf_profile_enable(nhmf_ctx* c, int enable) {
+  if (!c) return NHMF_ERR_ARG;
+  c->profiling = enable != 0;
+  return NHMF_OK;
+}
+
+nhmf_status nhmf_profile_read(nhmf_ctx* c, int kind, double* ms, long long* launches) {
+  if (!c || !ms || !launches) return fail(c, NHMF_ERR_ARG, "profile_read: bad argument");
+  double total = 0.0;
+  long long n = 0;
+  std::vector<nhmf_ctx::Rec> keep;
+  for (auto& r : c->prof) {
+    if (r.kind != kind) {
+      keep.push_back(r);
+      continue;
+    }
+    float t = 0.f;
+    nhmf_status st = cuda_check(c, cudaEventSynchronize(r.b), "profile sync");
+    if (st == NHMF_OK) st = cuda_check(c, cudaEventElapsedTime(&t, r.a, r.b), "profile elapsed");
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+    if (st != NHMF_OK) return st;
+    total += t;
+    n += r.launches;
+  }
+  c->prof.swap(keep);
+  *ms = total;
+  *launches = n;
+  return NHMF_OK;
+}
+
+}  // extern "C"

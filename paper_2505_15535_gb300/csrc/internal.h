@@ -1,0 +1,78 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nhmf.h"
+
+namespace nhmf {
+
+constexpr int kMaxN = 5;  // p + 1 for p <= 4
+
+// 1D tables of the Q_p element on [0, 1] (Section 2.2, 2.4), FP64.
+//   B[q][i]  = l_i(x_q): GLL Lagrange basis at the Gauss points
+//   Dc[q][r] = derivative of the Lagrange basis on the Gauss points, at Gauss point q
+//              (collocation derivative: exact for polynomials of degree <= p)
+//   D[q][i]  = l_i'(x_q) = sum_r Dc[q][r] B[r][i]
+//   w[q]     = Gauss weights on [0, 1]
+struct Tables1D {
+  int n;
+  double nodes[kMaxN], xq[kMaxN], w[kMaxN];
+  double B[kMaxN][kMaxN], Dc[kMaxN][kMaxN], D[kMaxN][kMaxN];
+};
+void build_tables(int p, Tables1D* t);
+
+// Geometry of one element colour class: elements (cx + 2 ix, cy + 2 iy, cz + 2 iz).
+struct Colour {
+  int cx, cy, cz;
+  int nx, ny, nz;
+  int count;        // nx * ny * nz
+  long long slot0;  // first colour-major element slot of this class
+};
+
+struct Geometry {
+  int N, p, n, M;
+  long long M3;      // nodes
+  long long E;       // elements
+  long long nq;      // quadrature points, E * n^3
+  double h;
+  Colour colour[8];
+};
+
+}  // namespace nhmf
+
+struct nhmf_ctx {
+  nhmf_params prm;
+  nhmf::Geometry g;
+  nhmf::Tables1D tab;
+  int device = 0;
+  double* ubar = nullptr;     // linearisation point, FP64
+  float* ubar32 = nullptr;    // its FP32 copy (FP32 on-the-fly apply)
+  double* cache64 = nullptr;  // [10][nq]
+  float* cache32 = nullptr;   // [10][nq]
+  unsigned* status = nullptr; // device status word: bit 0 det F <= 0, bit 1 non-finite
+  bool have_lin = false;
+  std::string err;
+  // kernel timing (nhmf_profile_enable): event pairs per operator kind
+  bool profiling = false;
+  struct Rec { int kind; int launches; cudaEvent_t a, b; };
+  std::vector<Rec> prof;
+};
+
+namespace nhmf {
+
+enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u };
+
+nhmf_status launch_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v,
+                         cudaStream_t s);
+nhmf_status launch_cache_build(nhmf_ctx* c, cudaStream_t s);
+nhmf_status launch_residual(nhmf_ctx* c, const double* u, double* r, cudaStream_t s);
+nhmf_status launch_diagonal(nhmf_ctx* c, double* d, cudaStream_t s);
+nhmf_status launch_to_fp32(const double* x, float* y, long long n, cudaStream_t s);
+
+nhmf_status fail(nhmf_ctx* c, nhmf_status st, const std::string& msg);
+nhmf_status cuda_check(nhmf_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace nhmf

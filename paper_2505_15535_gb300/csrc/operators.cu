@@ -1,0 +1,532 @@
+// Matrix-free operators of compressible neo-Hookean elasticity on the GPU:
+//   k_apply     tangent application, on the fly (Algorithm 1) or from the point cache
+//   k_cache     point cache {F^-1, ln J} at the linearisation point (partial assembly, Section 3.2)
+//   k_residual  residual R(u) (Eq. F)
+//   k_diagonal  operator diagonal (Section 2.3)
+// Each block processes NE elements of one colour class; elements of a class share no node,
+// so the read-modify-write scatter of a launch is race-free and deterministic.  The eight
+// classes run as eight launches in a fixed order.
+#include <algorithm>
+
+#include "sumfact.cuh"
+
+namespace nhmf {
+namespace {
+
+constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128;  // B, Dc, D tables + n^3 weights (+pad)
+
+template <int P, typename T>
+__device__ __forceinline__ void load_tables(const OpArgs& a, T* sB, T* sDc, T* sD, T* sW, double wscale) {
+  constexpr int n = P + 1;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    sB[i] = T(a.B[i]);
+    sDc[i] = T(a.Dc[i]);
+    sD[i] = T(a.D[i]);
+  }
+  for (int q = threadIdx.x; q < n * n * n; q += blockDim.x)
+    sW[q] = T(a.w[q % n] * a.w[(q / n) % n] * a.w[q / (n * n)] * wscale);
+}
+
+// Gather three components of a global vector into dst[c][t] for the block's elements,
+// optionally zeroing constrained DoFs; items of absent elements are zero.
+template <int P, int NI, typename TS, typename T>
+__device__ __forceinline__ void gather(const OpArgs& a, const TS* __restrict__ src, long long e0,
+                                       int nvalid, bool mask, T* dst) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1);
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    const int e = t / n3;
+    if (e < nvalid) {
+      int gi, gj, gk;
+      item_node<P>(a, e0 + e, t % n3, gi, gj, gk);
+      const long long node = gi + (long long)a.M * (gj + (long long)a.M * gk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T val = T(src[c * a.M3 + node]);
+        if (mask && is_constrained(a.bc, c, gi, gk, a.M)) val = T(0);
+        dst[c * NI + t] = val;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dst[c * NI + t] = T(0);
+    }
+  }
+}
+
+template <int P, int NI, typename T>
+__device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long long e0, int nvalid,
+                                            T* __restrict__ out) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1);
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    const int e = t / n3;
+    if (e >= nvalid) continue;
+    int gi, gj, gk;
+    item_node<P>(a, e0 + e, t % n3, gi, gj, gk);
+    const long long node = gi + (long long)a.M * (gj + (long long)a.M * gk);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * a.M3 + node] += src[c * NI + t];
+  }
+}
+
+// Forward interpolation of three components to the points: in -> out (tmp is clobbered).
+template <int n, int NI, typename T>
+__device__ __forceinline__ void to_points(const T* sB, T* in, T* tmp, T* out) {
+  sf_pass<n, NI, 3, 0, false, false>(sB, in, tmp);
+  __syncthreads();
+  sf_pass<n, NI, 3, 1, false, false>(sB, tmp, in);
+  __syncthreads();
+  sf_pass<n, NI, 3, 2, false, false>(sB, in, out);
+  __syncthreads();
+}
+
+// Transposed integration of the nine point fluxes G[3c+d] to nodal values in `out`
+// (`tmp` clobbered; G's first three slots are reused).
+template <int n, int NI, typename T>
+__device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* tmp, T* out) {
+  colloc_grad_T<n, NI>(sDc, G, tmp);
+  __syncthreads();
+  sf_pass<n, NI, 3, 0, true, false>(sB, tmp, G);
+  __syncthreads();
+  sf_pass<n, NI, 3, 1, true, false>(sB, G, tmp);
+  __syncthreads();
+  sf_pass<n, NI, 3, 2, true, false>(sB, tmp, out);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ tangent application
+template <int P, typename T, int STRAT>
+__global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
+  constexpr int n = P + 1, n3 = n * n * n, NE = Cfg<P, T>::NE, NI = NE * n3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sB = reinterpret_cast<T*>(smem_raw);
+  T* sDc = sB + kMaxN * kMaxN;
+  T* sD = sDc + kMaxN * kMaxN;
+  T* sW = sD + kMaxN * kMaxN;
+  T* U = sB + kTabSlots;                        // [3][NI] ubar at the points (on the fly)
+  T* Vq = U + (STRAT == NHMF_ON_THE_FLY ? 3 * NI : 0);  // [3][NI] du at the points
+  T* G = Vq + 3 * NI;                           // [9][NI] fluxes; G[0..2] doubles as gather buffer
+
+  load_tables<P>(a, sB, sDc, sD, sW, a.h);
+  const long long e0 = (long long)blockIdx.x * NE;
+  const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
+  const T invh = T(1.0 / a.h);
+
+  if (STRAT == NHMF_ON_THE_FLY) {
+    if (sizeof(T) == 8)
+      gather<P, NI>(a, a.u64, e0, nvalid, false, G);
+    else
+      gather<P, NI>(a, a.u32, e0, nvalid, false, G);
+    __syncthreads();
+    to_points<n, NI>(sB, G, Vq, U);
+  }
+  gather<P, NI>(a, static_cast<const T*>(a.du), e0, nvalid, true, G);
+  __syncthreads();
+  to_points<n, NI>(sB, G, Vq + 0, Vq);  // in-place target is fine: passes ping-pong via G
+  // (to_points(in=G, tmp=Vq, out=Vq): x: G->Vq, y: Vq->G, z: G->Vq)
+
+  const T mu = T(a.mu), lam = T(a.lam);
+  const T* cache = static_cast<const T*>(a.cache);
+  const long long cbase = (a.col.slot0 + e0) * n3;
+  bool bad = false;
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    T Fi[9], lnJ;
+    if (STRAT == NHMF_ON_THE_FLY) {
+      T H[9];
+      colloc_grad<n, NI>(sDc, U, t, H);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) H[k] *= invh;
+      const T Jm1 = kinematics(H, Fi, lnJ);
+      bad |= !(Jm1 > T(-1));
+    } else {
+      if (t / n3 < nvalid) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fi[k] = cache[k * a.nq + cbase + t];
+        lnJ = cache[9 * a.nq + cbase + t];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fi[k] = (k % 4 == 0) ? T(1) : T(0);
+        lnJ = T(0);
+      }
+    }
+    T dH[9], g[9];
+    colloc_grad<n, NI>(sDc, Vq, t, dH);
+    linearised_stress(Fi, lnJ, dH, mu, lam, sW[t % n3], g);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
+  }
+  if (bad) atomicOr(a.status, kStatusNonPosJ);
+  __syncthreads();
+  from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
+  scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<T*>(a.v));
+}
+
+// ------------------------------------------------------------------ point cache
+template <int P>
+__global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs a) {
+  using T = double;
+  constexpr int n = P + 1, n3 = n * n * n, NE = Cfg<P, T>::NE, NI = NE * n3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sB = reinterpret_cast<T*>(smem_raw);
+  T* sDc = sB + kMaxN * kMaxN;
+  T* sD = sDc + kMaxN * kMaxN;
+  T* sW = sD + kMaxN * kMaxN;
+  T* A = sB + kTabSlots;  // [3][NI]
+  T* Vq = A + 3 * NI;     // [3][NI]
+  load_tables<P>(a, sB, sDc, sD, sW, 1.0);
+  const long long e0 = (long long)blockIdx.x * NE;
+  const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
+  gather<P, NI>(a, a.u64, e0, nvalid, false, A);
+  __syncthreads();
+  to_points<n, NI>(sB, A, Vq, Vq);
+  const double invh = 1.0 / a.h;
+  const long long cbase = (a.col.slot0 + e0) * n3;
+  bool bad = false;
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    if (t / n3 >= nvalid) continue;
+    double H[9], Fi[9], lnJ;
+    colloc_grad<n, NI>(sDc, Vq, t, H);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) H[k] *= invh;
+    const double Jm1 = kinematics(H, Fi, lnJ);
+    bad |= !(Jm1 > -1.0);
+    if (a.cache64_out) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a.cache64_out[k * a.nq + cbase + t] = Fi[k];
+      a.cache64_out[9 * a.nq + cbase + t] = lnJ;
+    }
+    if (a.cache32_out) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a.cache32_out[k * a.nq + cbase + t] = float(Fi[k]);
+      a.cache32_out[9 * a.nq + cbase + t] = float(lnJ);
+    }
+  }
+  if (bad) atomicOr(a.status, kStatusNonPosJ);
+}
+
+// ------------------------------------------------------------------ residual
+template <int P>
+__global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_residual(const OpArgs a) {
+  using T = double;
+  constexpr int n = P + 1, n3 = n * n * n, NE = Cfg<P, T>::NE, NI = NE * n3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sB = reinterpret_cast<T*>(smem_raw);
+  T* sDc = sB + kMaxN * kMaxN;
+  T* sD = sDc + kMaxN * kMaxN;
+  T* sW = sD + kMaxN * kMaxN;
+  T* Vq = sB + kTabSlots;  // [3][NI]
+  T* G = Vq + 3 * NI;      // [9][NI]
+  load_tables<P>(a, sB, sDc, sD, sW, a.h * a.h);
+  const long long e0 = (long long)blockIdx.x * NE;
+  const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
+  gather<P, NI>(a, a.u64, e0, nvalid, false, G);
+  __syncthreads();
+  to_points<n, NI>(sB, G, Vq, Vq);
+  const double invh = 1.0 / a.h;
+  unsigned flags = 0;
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    double H[9], Fi[9], lnJ;
+    colloc_grad<n, NI>(sDc, Vq, t, H);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) H[k] *= invh;
+    const double Jm1 = kinematics(H, Fi, lnJ);
+    if (!(Jm1 > -1.0)) flags |= kStatusNonPosJ;
+    const double s = sW[t % n3];
+    const double c2 = 2.0 * a.lam * lnJ - a.mu;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // P = mu F + (2 lambda ln J - mu) F^-T
+        const double F = (i == j ? 1.0 : 0.0) + H[3 * i + j];
+        const double Pij = fma(a.mu, F, c2 * Fi[3 * j + i]);
+        if (!isfinite(Pij)) flags |= kStatusNonFinite;
+        G[(3 * i + j) * NI + t] = s * Pij;
+      }
+  }
+  if (flags) atomicOr(a.status, flags);
+  __syncthreads();
+  from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
+  scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<double*>(a.v));
+}
+
+// ------------------------------------------------------------------ diagonal
+// diag(K)_{c,I} = sum_q sum_{d,l} L_{cdcl} dphi_I/dX_d dphi_I/dX_l w_q h^3 with
+// L_{cdcl} = mu delta_dl + (mu + 2 lambda (1 - ln J)) Finv[d][c] Finv[l][c].  The products
+// of 1D factors are separable, so each (d, l) pair is three transposed passes with the
+// elementwise-product tables BB, BD, DD.
+template <int P> struct DiagCfg { static constexpr int NE = Cfg<P, double>::NE / 2 > 0 ? Cfg<P, double>::NE / 2 : 1; };
+
+template <int P>
+__global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpArgs a) {
+  using T = double;
+  constexpr int n = P + 1, n3 = n * n * n, NE = DiagCfg<P>::NE, NI = NE * n3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sB = reinterpret_cast<T*>(smem_raw);
+  T* sDc = sB + kMaxN * kMaxN;
+  T* sD = sDc + kMaxN * kMaxN;
+  T* sW = sD + kMaxN * kMaxN;
+  T* sBB = sB + kTabSlots;  // 3 product tables, n*n each
+  T* sBD = sBB + kMaxN * kMaxN;
+  T* sDD = sBD + kMaxN * kMaxN;
+  T* Cq = sDD + kMaxN * kMaxN + 1;  // [10][NI]: Finv (9) and ln J at the points
+  T* S = Cq + 10 * NI;              // [3][NI]
+  T* tmp = S + 3 * NI;              // [3][NI]
+  T* R = tmp + 3 * NI;              // [3][NI]
+  load_tables<P>(a, sB, sDc, sD, sW, a.h);
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int q = i / n, k = i % n;
+    sBB[i] = a.B[q * n + k] * a.B[q * n + k];
+    sBD[i] = a.B[q * n + k] * a.D[q * n + k];
+    sDD[i] = a.D[q * n + k] * a.D[q * n + k];
+  }
+  const long long e0 = (long long)blockIdx.x * NE;
+  const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
+  gather<P, NI>(a, a.u64, e0, nvalid, false, S);
+  __syncthreads();
+  to_points<n, NI>(sB, S, tmp, tmp);
+  const double invh = 1.0 / a.h;
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    double H[9], Fi[9], lnJ;
+    colloc_grad<n, NI>(sDc, tmp, t, H);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) H[k] *= invh;
+    kinematics(H, Fi, lnJ);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Cq[k * NI + t] = Fi[k];
+    Cq[9 * NI + t] = lnJ;
+    for (int c = 0; c < 3; ++c) R[c * NI + t] = 0.0;
+  }
+  __syncthreads();
+  for (int d = 0; d < 3; ++d)
+    for (int l = d; l < 3; ++l) {
+      for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+        const double s = sW[t % n3] * (d == l ? 1.0 : 2.0);
+        const double kap = a.mu + 2.0 * a.lam * (1.0 - Cq[9 * NI + t]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double L = (d == l ? a.mu : 0.0) + kap * Cq[(3 * d + c) * NI + t] * Cq[(3 * l + c) * NI + t];
+          S[c * NI + t] = s * L;
+        }
+      }
+      __syncthreads();
+      // direction x uses DD if d == l == 0, BD if exactly one of d, l is 0, else BB
+      const T* mx = (d == 0 && l == 0) ? sDD : ((d == 0 || l == 0) ? sBD : sBB);
+      const T* my = (d == 1 && l == 1) ? sDD : ((d == 1 || l == 1) ? sBD : sBB);
+      const T* mz = (d == 2 && l == 2) ? sDD : ((d == 2 || l == 2) ? sBD : sBB);
+      sf_pass<n, NI, 3, 0, true, false>(mx, S, tmp);
+      __syncthreads();
+      sf_pass<n, NI, 3, 1, true, false>(my, tmp, S);
+      __syncthreads();
+      sf_pass<n, NI, 3, 2, true, true>(mz, S, R);
+      __syncthreads();
+    }
+  scatter_add<P, NI>(a, R, e0, nvalid, static_cast<double*>(a.v));
+}
+
+// ------------------------------------------------------------------ Dirichlet rows
+// mode 0: out[d] = src[d]; mode 1: out[d] = value, on every constrained DoF.
+template <typename T>
+__global__ void k_fix_constrained(int bc, int M, long long M3, const T* src, T* out, int mode, T value) {
+  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long M2 = (long long)M * M;
+  if (f >= M2) return;
+  const int x = int(f % M), y = int(f / M);
+  auto fix = [&](int c, long long node) {
+    const long long d = c * M3 + node;
+    out[d] = mode == 0 ? src[d] : value;
+  };
+  if (bc == NHMF_BC_CLAMP_X0) {
+    const long long node = (long long)M * (x + (long long)M * y);  // (0, x, y)
+    for (int c = 0; c < 3; ++c) fix(c, node);
+  } else if (bc == NHMF_BC_COMPRESSION) {
+    const long long bottom = x + (long long)M * y;
+    const long long top = bottom + M2 * (M - 1);
+    for (int c = 0; c < 3; ++c) fix(c, bottom);
+    fix(2, top);
+  }
+}
+
+__global__ void k_to_fp32(const double* x, float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = float(x[i]);
+}
+
+// ------------------------------------------------------------------ host side
+OpArgs base_args(nhmf_ctx* c) {
+  OpArgs a{};
+  a.N = c->g.N;
+  a.M = c->g.M;
+  a.bc = c->prm.bc;
+  a.M3 = c->g.M3;
+  a.nq = c->g.nq;
+  a.h = c->g.h;
+  a.mu = c->prm.mu;
+  a.lam = c->prm.lambda;
+  const int n = c->g.n;
+  for (int q = 0; q < n; ++q) {
+    a.w[q] = c->tab.w[q];
+    for (int i = 0; i < n; ++i) {
+      a.B[q * n + i] = c->tab.B[q][i];
+      a.Dc[q * n + i] = c->tab.Dc[q][i];
+      a.D[q * n + i] = c->tab.D[q][i];
+    }
+  }
+  a.status = c->status;
+  return a;
+}
+
+template <typename KernelT>
+cudaError_t prepare(KernelT kernel, size_t smem) {
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+// Runs `kernel` once per colour class with NE elements per block.
+template <typename KernelT>
+nhmf_status run_colours(nhmf_ctx* c, KernelT kernel, OpArgs a, int NE, int threads, size_t smem,
+                        cudaStream_t s, const char* what, int kind) {
+  if (cudaError_t e = prepare(kernel, smem); e != cudaSuccess) return cuda_check(c, e, what);
+  nhmf_ctx::Rec rec{kind, 0, nullptr, nullptr};
+  if (c->profiling) {
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, s);
+  }
+  for (int k = 0; k < 8; ++k) {
+    const Colour& col = c->g.colour[k];
+    if (col.count == 0) continue;
+    a.col = col;
+    const int blocks = (col.count + NE - 1) / NE;
+    kernel<<<blocks, threads, smem, s>>>(a);
+    ++rec.launches;
+  }
+  if (c->profiling) {
+    cudaEventRecord(rec.b, s);
+    c->prof.push_back(rec);
+  }
+  return cuda_check(c, cudaGetLastError(), what);
+}
+
+template <typename T>
+nhmf_status fix_rows(nhmf_ctx* c, const T* src, T* out, int mode, T value, cudaStream_t s) {
+  if (c->prm.bc == NHMF_BC_NONE) return NHMF_OK;
+  const long long M2 = (long long)c->g.M * c->g.M;
+  k_fix_constrained<T><<<(unsigned)((M2 + 255) / 256), 256, 0, s>>>(c->prm.bc, c->g.M, c->g.M3, src, out, mode, value);
+  return cuda_check(c, cudaGetLastError(), "dirichlet rows");
+}
+
+template <int P, typename T, int STRAT>
+nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, cudaStream_t s) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, T>::NE, NI = NE * n3;
+  OpArgs a = base_args(c);
+  a.u64 = c->ubar;
+  a.u32 = c->ubar32;
+  a.du = du;
+  a.v = v;
+  a.cache = sizeof(T) == 8 ? (const void*)c->cache64 : (const void*)c->cache32;
+  const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;
+  const size_t smem = slots * sizeof(T);
+  if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(T) * 3 * c->g.M3, s); e != cudaSuccess)
+    return cuda_check(c, e, "apply memset");
+  nhmf_status st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
+  if (st != NHMF_OK) return st;
+  return fix_rows<T>(c, static_cast<const T*>(du), static_cast<T*>(v), 0, T(0), s);
+}
+
+template <int P>
+nhmf_status apply_dispatch_p(nhmf_ctx* c, int prec, int strat, const void* du, void* v, cudaStream_t s) {
+  if (prec == NHMF_FP64)
+    return strat == NHMF_CACHED ? apply_p<P, double, NHMF_CACHED>(c, du, v, s)
+                                : apply_p<P, double, NHMF_ON_THE_FLY>(c, du, v, s);
+  return strat == NHMF_CACHED ? apply_p<P, float, NHMF_CACHED>(c, du, v, s)
+                              : apply_p<P, float, NHMF_ON_THE_FLY>(c, du, v, s);
+}
+
+template <int P>
+nhmf_status cache_p(nhmf_ctx* c, cudaStream_t s) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, double>::NE, NI = NE * n3;
+  OpArgs a = base_args(c);
+  a.u64 = c->ubar;
+  a.cache64_out = c->cache64;
+  a.cache32_out = c->cache32;
+  const size_t smem = (kTabSlots + 6 * (size_t)NI) * sizeof(double);
+  return run_colours(c, k_cache<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "cache build", NHMF_KIND_CACHE);
+}
+
+template <int P>
+nhmf_status residual_p(nhmf_ctx* c, const double* u, double* r, cudaStream_t s) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, double>::NE, NI = NE * n3;
+  OpArgs a = base_args(c);
+  a.u64 = u;
+  a.v = r;
+  const size_t smem = (kTabSlots + 12 * (size_t)NI) * sizeof(double);
+  if (cudaError_t e = cudaMemsetAsync(r, 0, sizeof(double) * 3 * c->g.M3, s); e != cudaSuccess)
+    return cuda_check(c, e, "residual memset");
+  nhmf_status st = run_colours(c, k_residual<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "residual", NHMF_KIND_RESIDUAL);
+  if (st != NHMF_OK) return st;
+  return fix_rows<double>(c, nullptr, r, 1, 0.0, s);
+}
+
+template <int P>
+nhmf_status diagonal_p(nhmf_ctx* c, double* d, cudaStream_t s) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = DiagCfg<P>::NE, NI = NE * n3;
+  OpArgs a = base_args(c);
+  a.u64 = c->ubar;
+  a.v = d;
+  const size_t smem = (kTabSlots + 3 * kMaxN * kMaxN + 1 + 19 * (size_t)NI) * sizeof(double);
+  if (cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double) * 3 * c->g.M3, s); e != cudaSuccess)
+    return cuda_check(c, e, "diagonal memset");
+  nhmf_status st = run_colours(c, k_diagonal<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "diagonal", NHMF_KIND_DIAGONAL);
+  if (st != NHMF_OK) return st;
+  return fix_rows<double>(c, nullptr, d, 1, 1.0, s);
+}
+
+}  // namespace
+
+nhmf_status launch_apply(nhmf_ctx* c, int prec, int strat, const void* du, void* v, cudaStream_t s) {
+  switch (c->g.p) {
+    case 1: return apply_dispatch_p<1>(c, prec, strat, du, v, s);
+    case 2: return apply_dispatch_p<2>(c, prec, strat, du, v, s);
+    case 3: return apply_dispatch_p<3>(c, prec, strat, du, v, s);
+    case 4: return apply_dispatch_p<4>(c, prec, strat, du, v, s);
+  }
+  return fail(c, NHMF_ERR_ARG, "degree out of range");
+}
+
+nhmf_status launch_cache_build(nhmf_ctx* c, cudaStream_t s) {
+  switch (c->g.p) {
+    case 1: return cache_p<1>(c, s);
+    case 2: return cache_p<2>(c, s);
+    case 3: return cache_p<3>(c, s);
+    case 4: return cache_p<4>(c, s);
+  }
+  return fail(c, NHMF_ERR_ARG, "degree out of range");
+}
+
+nhmf_status launch_residual(nhmf_ctx* c, const double* u, double* r, cudaStream_t s) {
+  switch (c->g.p) {
+    case 1: return residual_p<1>(c, u, r, s);
+    case 2: return residual_p<2>(c, u, r, s);
+    case 3: return residual_p<3>(c, u, r, s);
+    case 4: return residual_p<4>(c, u, r, s);
+  }
+  return fail(c, NHMF_ERR_ARG, "degree out of range");
+}
+
+nhmf_status launch_diagonal(nhmf_ctx* c, double* d, cudaStream_t s) {
+  switch (c->g.p) {
+    case 1: return diagonal_p<1>(c, d, s);
+    case 2: return diagonal_p<2>(c, d, s);
+    case 3: return diagonal_p<3>(c, d, s);
+    case 4: return diagonal_p<4>(c, d, s);
+  }
+  return fail(c, NHMF_ERR_ARG, "degree out of range");
+}
+
+nhmf_status launch_to_fp32(const double* x, float* y, long long n, cudaStream_t s) {
+  k_to_fp32<<<1216, 256, 0, s>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? NHMF_OK : NHMF_ERR_CUDA;
+}
+
+}  // namespace nhmf

@@ -1,0 +1,201 @@
+// Device building blocks of the matrix-free operators: launch shapes, shared-memory sum
+// factorisation passes and the neo-Hookean point code.
+//
+// Sum factorisation (Section 2.4): values of a Q_p field at the (p+1)^3 Gauss points of an
+// element are three 1D passes with B[q][i] = l_i(x_q), one per direction; reference-cell
+// gradients at the points are then one collocation pass Dc per direction.  The transposed
+// contraction with the test-function gradients is one combined Dc^T pass followed by three
+// B^T passes.  Every pass maps an [n][n][n] block (x fastest) to another, with n = p + 1.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace nhmf {
+
+// Elements per thread block and threads per block for each degree and precision.  Chosen so
+// that NE * (p+1)^3 work items fill whole warps and the shared-memory footprint allows
+// several blocks per SM.
+template <int P, typename T> struct Cfg;
+template <> struct Cfg<1, double> { static constexpr int NE = 32, THREADS = 256; };
+template <> struct Cfg<2, double> { static constexpr int NE = 32, THREADS = 288; };
+template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; };
+template <> struct Cfg<4, double> { static constexpr int NE = 8, THREADS = 256; };
+template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; };
+template <> struct Cfg<2, float> { static constexpr int NE = 32, THREADS = 288; };
+template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
+template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
+
+// Kernel arguments (by value; lives in the constant bank).
+struct OpArgs {
+  int N, M, bc;
+  long long M3, nq;
+  double h, mu, lam;
+  Colour col;
+  double B[kMaxN * kMaxN], Dc[kMaxN * kMaxN], D[kMaxN * kMaxN], w[kMaxN];
+  const double* u64;
+  const float* u32;
+  const void* du;
+  void* v;
+  const void* cache;
+  double* cache64_out;
+  float* cache32_out;
+  unsigned* status;
+};
+
+__device__ __forceinline__ bool is_constrained(int bc, int c, int gi, int gk, int M) {
+  if (bc == NHMF_BC_CLAMP_X0) return gi == 0;
+  if (bc == NHMF_BC_COMPRESSION) return gk == 0 || (c == 2 && gk == M - 1);
+  return false;
+}
+
+// Global node of work item t (element t / n^3 of this block, local point/node t % n^3).
+template <int P>
+__device__ __forceinline__ void item_node(const OpArgs& a, long long e_in_colour, int q, int& gi,
+                                          int& gj, int& gk) {
+  constexpr int n = P + 1;
+  const Colour& c = a.col;
+  const int ix = int(e_in_colour % c.nx);
+  const int iy = int((e_in_colour / c.nx) % c.ny);
+  const int iz = int(e_in_colour / ((long long)c.nx * c.ny));
+  gi = P * (c.cx + 2 * ix) + q % n;
+  gj = P * (c.cy + 2 * iy) + (q / n) % n;
+  gk = P * (c.cz + 2 * iz) + q / (n * n);
+}
+
+// One 1D pass along direction DIR over NC arrays of NI items:
+//   out[c][t] (+)= sum_m Mat(r, m) in[c][t with coordinate r along DIR replaced by m]
+// with Mat(r, m) = mat[r][m] (TR = false) or mat[m][r] (TR = true).
+template <int n, int NI, int NC, int DIR, bool TR, bool ACC, typename T>
+__device__ __forceinline__ void sf_pass(const T* __restrict__ mat, const T* in, T* out) {
+  constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n);
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    const int r = (t / s) % n;
+    const int base = t - r * s;
+    T acc[NC];
+    {
+      const T c0 = TR ? mat[r] : mat[r * n];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = c0 * in[c * NI + base];
+    }
+#pragma unroll
+    for (int m = 1; m < n; ++m) {
+      const T cm = TR ? mat[m * n + r] : mat[r * n + m];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = fma(cm, in[c * NI + base + m * s], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (ACC)
+        out[c * NI + t] += acc[c];
+      else
+        out[c * NI + t] = acc[c];
+    }
+  }
+}
+
+// Reference-cell gradient of NC fields at item t from their point values (collocation).
+//   g[c][d] = sum_m Dc[r_d][m] val[c][t with coordinate d replaced by m]
+template <int n, int NI, typename T>
+__device__ __forceinline__ void colloc_grad(const T* __restrict__ Dc, const T* val, int t, T g[9]) {
+  const int rx = t % n, ry = (t / n) % n, rz = (t / (n * n)) % n;
+  const int bx = t - rx, by = t - ry * n, bz = t - rz * n * n;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* vc = val + c * NI;
+    T gx = Dc[rx * n] * vc[bx];
+    T gy = Dc[ry * n] * vc[by];
+    T gz = Dc[rz * n] * vc[bz];
+#pragma unroll
+    for (int m = 1; m < n; ++m) {
+      gx = fma(Dc[rx * n + m], vc[bx + m], gx);
+      gy = fma(Dc[ry * n + m], vc[by + m * n], gy);
+      gz = fma(Dc[rz * n + m], vc[bz + m * n * n], gz);
+    }
+    g[c * 3 + 0] = gx;
+    g[c * 3 + 1] = gy;
+    g[c * 3 + 2] = gz;
+  }
+}
+
+// Combined transposed collocation pass: y[c][t] = sum_d sum_m Dc[m][r_d] G[3c+d][t_d(m)].
+template <int n, int NI, typename T>
+__device__ __forceinline__ void colloc_grad_T(const T* __restrict__ Dc, const T* G, T* y) {
+  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    const int rx = t % n, ry = (t / n) % n, rz = (t / (n * n)) % n;
+    const int bx = t - rx, by = t - ry * n, bz = t - rz * n * n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* gx = G + (3 * c + 0) * NI;
+      const T* gy = G + (3 * c + 1) * NI;
+      const T* gz = G + (3 * c + 2) * NI;
+      T acc = Dc[rx] * gx[bx];
+      acc = fma(Dc[ry], gy[by], acc);
+      acc = fma(Dc[rz], gz[bz], acc);
+#pragma unroll
+      for (int m = 1; m < n; ++m) {
+        acc = fma(Dc[m * n + rx], gx[bx + m], acc);
+        acc = fma(Dc[m * n + ry], gy[by + m * n], acc);
+        acc = fma(Dc[m * n + rz], gz[bz + m * n * n], acc);
+      }
+      y[c * NI + t] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ point code
+// Kinematics at a point from the physical displacement gradient H (row-major H[3c+d]):
+// J - 1 from the invariants of H (no cancellation near J = 1),
+//   J - 1 = tr H + ((tr H)^2 - tr(H^2))/2 + det H,
+// F^-1 = cof(F)^T / J, ln J = log1p(J - 1).  Returns J - 1.
+template <typename T>
+__device__ __forceinline__ T kinematics(const T H[9], T Fi[9], T& lnJ) {
+  const T trH = H[0] + H[4] + H[8];
+  const T trH2 = H[0] * H[0] + H[4] * H[4] + H[8] * H[8] +
+                 T(2) * (H[1] * H[3] + H[2] * H[6] + H[5] * H[7]);
+  const T detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                 H[2] * (H[3] * H[7] - H[4] * H[6]);
+  const T Jm1 = trH + T(0.5) * (trH * trH - trH2) + detH;
+  const T F0 = T(1) + H[0], F4 = T(1) + H[4], F8 = T(1) + H[8];
+  const T F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
+  const T invJ = T(1) / (T(1) + Jm1);
+  Fi[0] = (F4 * F8 - F5 * F7) * invJ;
+  Fi[1] = (F2 * F7 - F1 * F8) * invJ;
+  Fi[2] = (F1 * F5 - F2 * F4) * invJ;
+  Fi[3] = (F5 * F6 - F3 * F8) * invJ;
+  Fi[4] = (F0 * F8 - F2 * F6) * invJ;
+  Fi[5] = (F2 * F3 - F0 * F5) * invJ;
+  Fi[6] = (F3 * F7 - F4 * F6) * invJ;
+  Fi[7] = (F1 * F6 - F0 * F7) * invJ;
+  Fi[8] = (F0 * F4 - F1 * F3) * invJ;
+  lnJ = log1p(Jm1);
+  return Jm1;
+}
+
+// Linearised first Piola stress at a point, scaled by s (Eq. LG: G = L : Grad du):
+//   dP = mu dH + (mu - 2 lambda ln J) F^-T dH^T F^-T + 2 lambda tr(F^-1 dH) F^-T
+// with K = F^-1 dH and Q = K F^-1 (so F^-T dH^T F^-T = Q^T).  Written into g[3i+J].
+template <typename T>
+__device__ __forceinline__ void linearised_stress(const T Fi[9], T lnJ, const T dH[9], T mu,
+                                                  T lam, T s, T g[9]) {
+  T K[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      K[3 * i + j] = fma(Fi[3 * i + 0], dH[j], fma(Fi[3 * i + 1], dH[3 + j], Fi[3 * i + 2] * dH[6 + j]));
+  const T trK = K[0] + K[4] + K[8];
+  const T smu = s * mu;
+  const T sc1 = s * (mu - T(2) * lam * lnJ);
+  const T sc2 = s * (T(2) * lam * trK);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // Q[j][i] = sum_c K[j][c] Fi[c][i]
+      const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
+      g[3 * i + j] = fma(smu, dH[3 * i + j], fma(sc1, Qji, sc2 * Fi[3 * j + i]));
+    }
+}
+
+}  // namespace nhmf

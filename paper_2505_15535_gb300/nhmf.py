@@ -1,0 +1,179 @@
+"""ctypes binding of libnhmf.so: the C entry points under the same names, plus `Problem`.
+
+Arguments are marshalled only: tensors become device pointers (`data_ptr()`), the stream is
+torch's current CUDA stream.  Every computation runs in the library's CUDA kernels; if the
+library is missing the import of a function raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnhmf.so")
+
+NHMF_OK = 0
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPOS_J",
+                5: "ERR_NONFINITE", 6: "ERR_BREAKDOWN", 7: "ERR_NOT_CONVERGED", 8: "ERR_STATE"}
+NHMF_FP64, NHMF_FP32 = 0, 1
+NHMF_ON_THE_FLY, NHMF_CACHED = 0, 1
+NHMF_BC_NONE, NHMF_BC_CLAMP_X0, NHMF_BC_COMPRESSION = 0, 1, 2
+NHMF_CACHE_FP64, NHMF_CACHE_FP32 = 1, 2
+NHMF_KIND_APPLY, NHMF_KIND_CACHE, NHMF_KIND_RESIDUAL, NHMF_KIND_DIAGONAL = 0, 1, 2, 3
+
+
+class NhmfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nhmf_params(ctypes.Structure):
+    _fields_ = [("n_el", ctypes.c_int), ("degree", ctypes.c_int), ("mu", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("bc", ctypes.c_int), ("top_uz", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SIGS = {
+    "nhmf_create": (ctypes.c_int, [ctypes.POINTER(nhmf_params), ctypes.POINTER(_P)]),
+    "nhmf_destroy": (None, [_P]),
+    "nhmf_num_dofs": (ctypes.c_size_t, [_P]),
+    "nhmf_last_error": (ctypes.c_char_p, [_P]),
+    "nhmf_set_linearization": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "nhmf_tangent_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "nhmf_residual": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nhmf_diagonal": (ctypes.c_int, [_P, _P, _P]),
+    "nhmf_check_status": (ctypes.c_int, [_P, _P]),
+    "nhmf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "nhmf_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(ctx, st):
+    if st != NHMF_OK:
+        raise NhmfError(st, lib().nhmf_last_error(ctx).decode())
+
+
+# ---- the C entry points, same names ---------------------------------------------------
+def nhmf_create(n_el, degree, mu, lam, bc, top_uz=0.0):
+    prm = nhmf_params(n_el, degree, mu, lam, bc, top_uz)
+    ctx = _P()
+    st = lib().nhmf_create(ctypes.byref(prm), ctypes.byref(ctx))
+    if st != NHMF_OK:
+        raise NhmfError(st, "nhmf_create failed")
+    return ctx
+
+
+def nhmf_destroy(ctx):
+    lib().nhmf_destroy(ctx)
+
+
+def nhmf_num_dofs(ctx):
+    return lib().nhmf_num_dofs(ctx)
+
+
+def nhmf_last_error(ctx):
+    return lib().nhmf_last_error(ctx).decode()
+
+
+def nhmf_set_linearization(ctx, u, cache_mask=0, stream=None):
+    _check(ctx, lib().nhmf_set_linearization(ctx, _ptr(u), cache_mask, _stream(stream)))
+
+
+def nhmf_tangent_apply(ctx, precision, strategy, du, v, stream=None):
+    _check(ctx, lib().nhmf_tangent_apply(ctx, precision, strategy, _ptr(du), _ptr(v), _stream(stream)))
+
+
+def nhmf_residual(ctx, u, r, stream=None):
+    _check(ctx, lib().nhmf_residual(ctx, _ptr(u), _ptr(r), _stream(stream)))
+
+
+def nhmf_diagonal(ctx, d, stream=None):
+    _check(ctx, lib().nhmf_diagonal(ctx, _ptr(d), _stream(stream)))
+
+
+def nhmf_check_status(ctx, stream=None):
+    _check(ctx, lib().nhmf_check_status(ctx, _stream(stream)))
+
+
+def nhmf_profile_enable(ctx, enable):
+    _check(ctx, lib().nhmf_profile_enable(ctx, int(bool(enable))))
+
+
+def nhmf_profile_read(ctx, kind):
+    """(elapsed_ms, launches) of the element kernels of one operator kind since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(ctx, lib().nhmf_profile_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+class Problem:
+    """One mesh + material on the current CUDA device (owns an nhmf context)."""
+
+    def __init__(self, n_el, degree, mu, lam, bc, top_uz=0.0):
+        self.n_el, self.degree, self.mu, self.lam, self.bc = n_el, degree, mu, lam, bc
+        self.ctx = nhmf_create(n_el, degree, mu, lam, bc, top_uz)
+        self.n_dofs = nhmf_num_dofs(self.ctx)
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.n_el, w.degree, w.mu, w.lam, w.bc)
+
+    def close(self):
+        if self.ctx is not None:
+            nhmf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_linearization(self, u, cache_mask=0):
+        nhmf_set_linearization(self.ctx, u, cache_mask)
+
+    def apply(self, du, v, precision=NHMF_FP64, strategy=NHMF_ON_THE_FLY):
+        nhmf_tangent_apply(self.ctx, precision, strategy, du, v)
+        return v
+
+    def residual(self, u, r):
+        nhmf_residual(self.ctx, u, r)
+        return r
+
+    def diagonal(self, d):
+        nhmf_diagonal(self.ctx, d)
+        return d

@@ -1,0 +1,161 @@
+"""Parity of the CUDA tangent application, residual and diagonal with the FP64 oracle
+(Eq. F, Eq. DF, Algorithm 1, Section 2.3).  Bar: FP64 relative l2 <= 1e-12; FP32 results
+report their error and must stay within 1e-5 (FP32 sum factorisation with FP32 accumulation
+over at most (p+1)^3-term contractions and one conditioning factor of the operator)."""
+import numpy as np
+import pytest
+
+import nhmf_inputs as inp
+from oracle.fem import Operator
+from oracle.mesh import Mesh
+from tests.gpu_util import cuda, host, lib_or_fail, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def case(n_el, p, bc, lam=1.5, seed=0, amp=0.05):
+    w = inp.Workload(f"t{n_el}_{p}_{bc}", n_el, p, 1.0, lam, bc, "scaled", amp, "normal", 1.0,
+                     3000 + seed + 10 * p + 100 * n_el, 4000 + seed + 10 * p + 100 * n_el)
+    return w, inp.draw_u(w), inp.draw_du(w)
+
+
+@pytest.fixture(scope="module")
+def nhmf():
+    return lib_or_fail()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("n_el", [1, 3, 5])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_fp64_apply_both_strategies(nhmf, p, n_el, bc):
+    w, u, du = case(n_el, p, bc)
+    op = Operator(Mesh(n_el, p), w.mu, w.lam, bc)
+    ref = op.apply(u, du)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    dut = cuda(du)
+    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+        v = cuda(np.zeros_like(u))
+        prob.apply(dut, v, nhmf.NHMF_FP64, strat)
+        assert rel_l2(host(v), ref) <= FP64_TOL, (strat, rel_l2(host(v), ref))
+    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+        v32 = cuda(np.zeros(u.size, dtype=np.float32))
+        prob.apply(cuda(du.astype(np.float32)), v32, nhmf.NHMF_FP32, strat)
+        assert rel_l2(host(v32), ref) <= FP32_TOL, (strat, rel_l2(host(v32), ref))
+    prob.close()
+
+
+def test_q1_8_clamp_workload(nhmf):
+    w = inp.WORKLOADS["q1_8_clamp"]
+    u, du = inp.draw_u(w), inp.draw_du(w)
+    ref = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc).apply(u, du)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u))
+    v = cuda(np.zeros_like(u))
+    prob.apply(cuda(du), v, nhmf.NHMF_FP64, nhmf.NHMF_ON_THE_FLY)
+    assert rel_l2(host(v), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_fp64_residual(nhmf, p, bc):
+    w, u, _ = case(4, p, bc)
+    ref = Operator(Mesh(4, p), w.mu, w.lam, bc).residual(u)
+    prob = nhmf.Problem.from_workload(w)
+    r = cuda(np.zeros_like(u))
+    prob.residual(cuda(u), r)
+    assert rel_l2(host(r), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc", [0, 2])
+def test_fp64_diagonal(nhmf, p, bc):
+    w, u, _ = case(3, p, bc)
+    ref = Operator(Mesh(3, p), w.mu, w.lam, bc).diagonal(u)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u))
+    d = cuda(np.zeros_like(u))
+    prob.diagonal(d)
+    assert rel_l2(host(d), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("n_el,p", [(1, 1), (2, 1), (1, 2), (2, 2), (3, 1), (1, 3), (1, 4)])
+def test_columns_match_assembled_matrix(nhmf, n_el, p):
+    import torch
+    w, u, _ = case(n_el, p, 1)
+    op = Operator(Mesh(n_el, p), w.mu, w.lam, 1)
+    K = op.assemble(u)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64)
+    n = u.size
+    cols = np.arange(n) if n <= 400 else np.random.default_rng(1).choice(n, 400, replace=False)
+    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+        for j in cols:
+            e = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+            e[j] = 1.0
+            v = torch.empty_like(e)
+            prob.apply(e, v, nhmf.NHMF_FP64, strat)
+            col = host(v)
+            assert np.abs(col - K[:, j]).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_bitwise_determinism(nhmf):
+    import torch
+    w, u, du = case(6, 2, 1)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    for prec, dt in ((nhmf.NHMF_FP64, np.float64), (nhmf.NHMF_FP32, np.float32)):
+        for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+            dut = cuda(du.astype(dt))
+            outs = []
+            for _ in range(10):
+                v = torch.empty_like(dut)
+                prob.apply(dut, v, prec, strat)
+                outs.append(v.clone())
+            for o in outs[1:]:
+                assert torch.equal(o, outs[0])
+
+
+def test_strategies_agree(nhmf):
+    w, u, du = case(5, 3, 2, lam=49.0)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64)
+    a = cuda(np.zeros_like(u)); b = cuda(np.zeros_like(u))
+    prob.apply(cuda(du), a, nhmf.NHMF_FP64, nhmf.NHMF_ON_THE_FLY)
+    prob.apply(cuda(du), b, nhmf.NHMF_FP64, nhmf.NHMF_CACHED)
+    assert rel_l2(host(a), host(b)) <= 1e-13
+
+
+def test_nonpositive_jacobian_is_reported(nhmf):
+    w, u, _ = case(3, 2, 0)
+    prob = nhmf.Problem.from_workload(w)
+    bad = u.copy()
+    bad[: bad.size // 3] *= -3000.0       # folds elements: det F <= 0 somewhere
+    with pytest.raises(nhmf.NhmfError) as ei:
+        prob.set_linearization(cuda(bad), nhmf.NHMF_CACHE_FP64)
+    assert ei.value.status == 4
+    r = cuda(np.zeros_like(u))
+    with pytest.raises(nhmf.NhmfError) as ei:
+        prob.residual(cuda(bad), r)
+    assert ei.value.status == 4
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64)  # the context stays usable
+
+
+def test_call_order_and_argument_errors(nhmf):
+    w, u, du = case(2, 1, 1)
+    prob = nhmf.Problem.from_workload(w)
+    v = cuda(np.zeros_like(u))
+    with pytest.raises(nhmf.NhmfError) as ei:
+        prob.apply(cuda(du), v)
+    assert ei.value.status == 8
+    prob.set_linearization(cuda(u), 0)
+    with pytest.raises(nhmf.NhmfError) as ei:
+        prob.apply(cuda(du), v, nhmf.NHMF_FP64, nhmf.NHMF_CACHED)
+    assert ei.value.status == 8
+    with pytest.raises(nhmf.NhmfError):
+        nhmf.nhmf_create(0, 2, 1.0, 1.5, 0)
+    with pytest.raises(nhmf.NhmfError):
+        nhmf.nhmf_create(4, 5, 1.0, 1.5, 0)
