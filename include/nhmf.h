@@ -107,6 +107,72 @@ nhmf_status nhmf_diagonal(nhmf_ctx* ctx, double* d, void* stream);
  * NHMF_ERR_NONPOS_J or NHMF_ERR_NONFINITE. */
 nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
 
+/* ------------------------------------------------------------------ solvers
+ * Newton's method with load steps (Section 2.1-2.3): at Newton iterate u, solve
+ * A(u) du = b with b = -R(u) on free rows and b = g - u on constrained rows (g the
+ * prescribed values of the current load step; the Dirichlet increment is lifted through
+ * the unconstrained operator, b_f -= K(u) (g - u)_D), then u += theta du with theta halved
+ * while det F <= 0 is met.  A load step converges when ||b|| <= newton_rtol * ||b_0||, b_0
+ * the right-hand side of its first iteration.
+ * Linear solvers (all on the device; scalars stay on the device and the host reads the
+ * residual norm every `check_every` iterations):
+ *   NHMF_SOLVER_JACOBI_CG  FP64 CG preconditioned by the inverse operator diagonal
+ *                          (the plain baseline);
+ *   NHMF_SOLVER_MIXED_FCG  FP64 flexible CG whose preconditioner is an FP32 Jacobi-CG on the
+ *                          FP32 apply (FP64 residuals, dot products and updates outside);
+ *   NHMF_SOLVER_LEARNED_FCG FP64 flexible CG preconditioned by the trained U-Net, falling
+ *                          back to Jacobi-CG from the current iterate on stagnation. */
+enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2 };
+#define NHMF_MAX_STEPS 64
+
+typedef struct {
+  int solver;           /* NHMF_SOLVER_* */
+  int strategy;         /* NHMF_ON_THE_FLY or NHMF_CACHED for every apply of the solve */
+  int load_steps;       /* S >= 1 */
+  int first_step;       /* 1-based first load step to run (resume), default 1 */
+  int last_step;        /* last load step to run, default S */
+  double compression;   /* compression preset: u_z = -compression * s / S on z = 1 */
+  double newton_rtol;   /* default 1e-8 */
+  int newton_max_iter;  /* per load step, default 20 */
+  int max_backtracks;   /* halvings of the Newton step on det F <= 0, default 8 */
+  double linear_rtol;   /* default 1e-6 (relative to ||b||) */
+  int linear_max_iter;  /* default 20000 */
+  double inner_rtol;    /* mixed: FP32 inner CG relative tolerance, default 1e-2 */
+  int inner_max_iter;   /* mixed: FP32 inner CG iteration cap, default 200 */
+  int check_every;      /* iterations between host convergence reads, default 10 */
+} nhmf_solve_opts;
+
+typedef struct {
+  int steps_done;
+  int newton_iters[NHMF_MAX_STEPS];
+  long long linear_iters[NHMF_MAX_STEPS];  /* outer Krylov iterations (FP64 applies) */
+  long long inner_iters[NHMF_MAX_STEPS];   /* FP32 inner iterations (mixed) */
+  int fallbacks[NHMF_MAX_STEPS];           /* learned: linear solves that fell back */
+  double rel_residual[NHMF_MAX_STEPS];     /* final ||b|| / ||b_0|| of each step */
+  double seconds[NHMF_MAX_STEPS];
+  long long total_linear_iters, total_inner_iters;
+  double total_seconds;
+} nhmf_solve_stats;
+
+/* Fill `opts` with the defaults listed above (solver JACOBI_CG, strategy CACHED, S = 1). */
+void nhmf_solve_opts_default(nhmf_solve_opts* opts);
+
+/* Run load steps first_step..last_step of Newton's method on the context's problem.  u
+ * (device, FP64, 3*M^3) holds the initial state (the converged state of step first_step-1)
+ * and receives the result; the linearisation point ends at the final u.  Allocates the
+ * solver's work vectors in the context on first use.  Synchronises.  Returns
+ * NHMF_ERR_NOT_CONVERGED if a load step misses its tolerance, NHMF_ERR_NONPOS_J if
+ * backtracking cannot keep det F > 0, NHMF_ERR_BREAKDOWN on p^T A p <= 0. */
+nhmf_status nhmf_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, double* u, nhmf_solve_stats* stats,
+                       void* stream);
+
+/* Solve A(u) x = b at the current linearisation point with opts->solver, from x = 0, to
+ * ||b - A x|| <= opts->linear_rtol ||b||.  b, x: device FP64, 3*M^3.  `iters` receives the
+ * outer iterations, `inner_iters` the FP32 inner ones, `rel_res` the final relative
+ * residual (recomputed with an FP64 apply).  Synchronises. */
+nhmf_status nhmf_linear_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, const double* b, double* x,
+                              long long* iters, long long* inner_iters, double* rel_res, void* stream);
+
 /* Kernel timing.  While enabled, every operator call records a CUDA event pair on its
  * stream around its element kernels (the eight colour launches, not the vector memset or
  * the Dirichlet-row fix).  nhmf_profile_read() synchronises those events, returns the summed

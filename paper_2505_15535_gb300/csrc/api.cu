@@ -86,6 +86,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->ubar32);
   cudaFree(c->cache64);
   cudaFree(c->cache32);
+  free_work(c);
   delete c;
 }
 
@@ -103,6 +104,7 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
   if (st != NHMF_OK) return st;
   if (h & kStatusNonPosJ) return fail(c, NHMF_ERR_NONPOS_J, "det F <= 0 at a quadrature point");
   if (h & kStatusNonFinite) return fail(c, NHMF_ERR_NONFINITE, "non-finite value");
+  if (h & kStatusBreakdown) return fail(c, NHMF_ERR_BREAKDOWN, "Krylov breakdown: p^T A p <= 0");
   return NHMF_OK;
 }
 

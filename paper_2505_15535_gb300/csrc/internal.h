@@ -43,6 +43,20 @@ struct Geometry {
 
 }  // namespace nhmf
 
+namespace nhmf {
+// Work vectors of the solvers, allocated on first use.
+struct SolverWork {
+  long long n = 0;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *qprev = nullptr, *x = nullptr;
+  double *b = nullptr, *R = nullptr, *d = nullptr, *t = nullptr, *du = nullptr, *utry = nullptr;
+  double *diag = nullptr, *dinv = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
+  double* sc = nullptr;        // device scalars
+  double* partials = nullptr;  // reduction scratch
+  double* host = nullptr;      // pinned host scalar
+};
+}  // namespace nhmf
+
 struct nhmf_ctx {
   nhmf_params prm;
   nhmf::Geometry g;
@@ -59,14 +73,19 @@ struct nhmf_ctx {
   bool profiling = false;
   struct Rec { int kind; int launches; cudaEvent_t a, b; };
   std::vector<Rec> prof;
+  nhmf::SolverWork* work = nullptr;
 };
 
 namespace nhmf {
 
-enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u };
+enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u };
+void free_work(nhmf_ctx* c);
 
+// raw = true applies the unconstrained operator K (no Dirichlet masking or identity rows).
 nhmf_status launch_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v,
-                         cudaStream_t s);
+                         cudaStream_t s, bool raw = false);
+// On every constrained DoF: out = src (mode 0) or out = value (mode 1).
+nhmf_status fix_rows64(nhmf_ctx* c, const double* src, double* out, int mode, double value, cudaStream_t s);
 nhmf_status launch_cache_build(nhmf_ctx* c, cudaStream_t s);
 nhmf_status launch_residual(nhmf_ctx* c, const double* u, double* r, cudaStream_t s);
 nhmf_status launch_diagonal(nhmf_ctx* c, double* d, cudaStream_t s);

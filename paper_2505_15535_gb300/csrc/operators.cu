@@ -417,9 +417,10 @@ nhmf_status fix_rows(nhmf_ctx* c, const T* src, T* out, int mode, T value, cudaS
 }
 
 template <int P, typename T, int STRAT>
-nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, cudaStream_t s) {
+nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t s) {
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, T>::NE, NI = NE * n3;
   OpArgs a = base_args(c);
+  if (raw) a.bc = NHMF_BC_NONE;  // unconstrained operator K: no masking, no identity rows
   a.u64 = c->ubar;
   a.u32 = c->ubar32;
   a.du = du;
@@ -430,17 +431,17 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, cudaStream_t s) {
   if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(T) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "apply memset");
   nhmf_status st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
-  if (st != NHMF_OK) return st;
+  if (st != NHMF_OK || raw) return st;
   return fix_rows<T>(c, static_cast<const T*>(du), static_cast<T*>(v), 0, T(0), s);
 }
 
 template <int P>
-nhmf_status apply_dispatch_p(nhmf_ctx* c, int prec, int strat, const void* du, void* v, cudaStream_t s) {
+nhmf_status apply_dispatch_p(nhmf_ctx* c, int prec, int strat, const void* du, void* v, bool raw, cudaStream_t s) {
   if (prec == NHMF_FP64)
-    return strat == NHMF_CACHED ? apply_p<P, double, NHMF_CACHED>(c, du, v, s)
-                                : apply_p<P, double, NHMF_ON_THE_FLY>(c, du, v, s);
-  return strat == NHMF_CACHED ? apply_p<P, float, NHMF_CACHED>(c, du, v, s)
-                              : apply_p<P, float, NHMF_ON_THE_FLY>(c, du, v, s);
+    return strat == NHMF_CACHED ? apply_p<P, double, NHMF_CACHED>(c, du, v, raw, s)
+                                : apply_p<P, double, NHMF_ON_THE_FLY>(c, du, v, raw, s);
+  return strat == NHMF_CACHED ? apply_p<P, float, NHMF_CACHED>(c, du, v, raw, s)
+                              : apply_p<P, float, NHMF_ON_THE_FLY>(c, du, v, raw, s);
 }
 
 template <int P>
@@ -484,12 +485,12 @@ nhmf_status diagonal_p(nhmf_ctx* c, double* d, cudaStream_t s) {
 
 }  // namespace
 
-nhmf_status launch_apply(nhmf_ctx* c, int prec, int strat, const void* du, void* v, cudaStream_t s) {
+nhmf_status launch_apply(nhmf_ctx* c, int prec, int strat, const void* du, void* v, cudaStream_t s, bool raw) {
   switch (c->g.p) {
-    case 1: return apply_dispatch_p<1>(c, prec, strat, du, v, s);
-    case 2: return apply_dispatch_p<2>(c, prec, strat, du, v, s);
-    case 3: return apply_dispatch_p<3>(c, prec, strat, du, v, s);
-    case 4: return apply_dispatch_p<4>(c, prec, strat, du, v, s);
+    case 1: return apply_dispatch_p<1>(c, prec, strat, du, v, raw, s);
+    case 2: return apply_dispatch_p<2>(c, prec, strat, du, v, raw, s);
+    case 3: return apply_dispatch_p<3>(c, prec, strat, du, v, raw, s);
+    case 4: return apply_dispatch_p<4>(c, prec, strat, du, v, raw, s);
   }
   return fail(c, NHMF_ERR_ARG, "degree out of range");
 }
@@ -522,6 +523,10 @@ nhmf_status launch_diagonal(nhmf_ctx* c, double* d, cudaStream_t s) {
     case 4: return diagonal_p<4>(c, d, s);
   }
   return fail(c, NHMF_ERR_ARG, "degree out of range");
+}
+
+nhmf_status fix_rows64(nhmf_ctx* c, const double* src, double* out, int mode, double value, cudaStream_t s) {
+  return fix_rows<double>(c, src, out, mode, value, s);
 }
 
 nhmf_status launch_to_fp32(const double* x, float* y, long long n, cudaStream_t s) {

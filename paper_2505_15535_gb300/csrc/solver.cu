@@ -1,0 +1,371 @@
+// Newton's method with load steps and the Krylov solvers on the matrix-free operator
+// (Sections 2.1-2.3).  Host code drives device kernels; every vector operation, reduction
+// and scalar of the iterations lives on the device, and the host reads the residual norm
+// only every `check_every` iterations.
+#include <chrono>
+#include <cmath>
+
+#include "blas.h"
+#include "internal.h"
+
+namespace nhmf {
+namespace {
+
+// Dirichlet data of a load step: mode 0 writes d = g - u on constrained DoFs (0 elsewhere
+// is the caller's memset); mode 1 sets u = g there.  g = top_uz for u_z on z = 1 of the
+// compression preset, 0 elsewhere.
+__global__ void k_bc(int bc, int M, long long M3, double top_uz, double* u, double* d, int mode) {
+  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long M2 = (long long)M * M;
+  if (f >= M2) return;
+  const int x = int(f % M), y = int(f / M);
+  auto set = [&](int c, long long node, double g) {
+    const long long i = c * M3 + node;
+    if (mode == 0)
+      d[i] = g - u[i];
+    else
+      u[i] = g;
+  };
+  if (bc == NHMF_BC_CLAMP_X0) {
+    const long long node = (long long)M * (x + (long long)M * y);
+    for (int c = 0; c < 3; ++c) set(c, node, 0.0);
+  } else if (bc == NHMF_BC_COMPRESSION) {
+    const long long bottom = x + (long long)M * y;
+    for (int c = 0; c < 3; ++c) set(c, bottom, 0.0);
+    set(2, bottom + M2 * (M - 1), top_uz);
+  }
+}
+
+enum Slot { RZ0 = 0, RZ1 = 1, PQ = 2, RR = 3, BN = 4, ALPHA = 5, BETA = 6, ZQ = 7, PR = 8, PQPREV = 9,
+            RNORM = 10, TMP = 11, IN_RZ0 = 16, IN_RZ1 = 17, IN_PQ = 18, IN_RR = 19, IN_BN = 20 };
+
+struct Ctx {
+  nhmf_ctx* c;
+  cudaStream_t s;
+  long long n;
+  SolverWork& w;
+};
+
+nhmf_status ensure_work(nhmf_ctx* c) {
+  const long long n = 3 * c->g.M3;
+  if (c->work && c->work->n == n) return NHMF_OK;
+  free_work(c);
+  c->work = new SolverWork();
+  SolverWork& w = *c->work;
+  w.n = n;
+  double** d64[] = {&w.r, &w.z, &w.p, &w.q, &w.qprev, &w.x, &w.b, &w.R, &w.d, &w.t, &w.du, &w.utry, &w.diag, &w.dinv};
+  for (double** p : d64)
+    if (cudaMalloc(p, n * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "solver work alloc");
+  float** d32[] = {&w.r32, &w.z32, &w.p32, &w.q32, &w.x32, &w.b32, &w.dinv32};
+  for (float** p : d32)
+    if (cudaMalloc(p, n * sizeof(float)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "solver work alloc");
+  if (cudaMalloc(&w.sc, 64 * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "solver scalars");
+  if (cudaMalloc(&w.partials, kPartialSlots * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "partials");
+  if (cudaMallocHost(&w.host, 8 * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "pinned scalar");
+  cudaMemset(w.sc, 0, 64 * sizeof(double));
+  return NHMF_OK;
+}
+
+nhmf_status read_scalar(Ctx& x, const double* dev, double* out) {
+  nhmf_status st = cuda_check(x.c, cudaMemcpyAsync(x.w.host, dev, sizeof(double), cudaMemcpyDeviceToHost, x.s), "scalar read");
+  if (st == NHMF_OK) st = cuda_check(x.c, cudaStreamSynchronize(x.s), "scalar sync");
+  *out = x.w.host[0];
+  return st;
+}
+
+nhmf_status norm(Ctx& x, const double* v, int slot, double* out) {
+  norm2(x.n, v, x.w.sc + slot, x.w.partials, x.s);
+  return read_scalar(x, x.w.sc + slot, out);
+}
+
+template <typename T> struct Prec;
+template <> struct Prec<double> { static constexpr int id = NHMF_FP64; };
+template <> struct Prec<float> { static constexpr int id = NHMF_FP32; };
+
+// Jacobi-preconditioned CG from x = 0 on A in precision T.  Scalars use slots base..base+4.
+template <typename T>
+nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z, T* p, T* q, double rtol,
+                int maxit, int check_every, int base, long long* iters, double* relres) {
+  nhmf_ctx* c = x.c;
+  double* sc = x.w.sc;
+  double* rz[2] = {sc + base + 0, sc + base + 1};
+  double* pq = sc + base + 2;
+  double* rr = sc + base + 3;
+  double* bn = sc + base + 4;
+  norm2(x.n, b, bn, x.w.partials, x.s);
+  double bnh;
+  nhmf_status st = read_scalar(x, bn, &bnh);
+  if (st != NHMF_OK) return st;
+  cudaMemsetAsync(sol, 0, x.n * sizeof(T), x.s);
+  *iters = 0;
+  *relres = 0.0;
+  if (!(bnh > 0.0)) return bnh == 0.0 ? NHMF_OK : fail(c, NHMF_ERR_NONFINITE, "pcg: non-finite right-hand side");
+  cudaMemcpyAsync(r, b, x.n * sizeof(T), cudaMemcpyDeviceToDevice, x.s);
+  jacobi<T>(x.n, r, dinv, z, rz[0], rr, x.w.partials, x.s);
+  pcg_direction<T>(x.n, rz[0], nullptr, z, p, x.s);
+  long long k = 0;
+  double rrh = bnh * bnh;
+  while (k < maxit) {
+    if ((st = launch_apply(c, Prec<T>::id, strat, p, q, x.s)) != NHMF_OK) return st;
+    dot(x.n, p, q, pq, x.w.partials, x.s);
+    pcg_update<T>(x.n, rz[k & 1], pq, sol, r, p, q, dinv, z, rz[(k + 1) & 1], rr, x.w.partials, c->status, x.s);
+    pcg_direction<T>(x.n, rz[(k + 1) & 1], rz[k & 1], z, p, x.s);
+    ++k;
+    if (k % check_every == 0 || k == maxit) {
+      if ((st = read_scalar(x, rr, &rrh)) != NHMF_OK) return st;
+      if (!std::isfinite(rrh)) return fail(c, NHMF_ERR_NONFINITE, "pcg: non-finite residual");
+      if (std::sqrt(rrh) <= rtol * bnh) break;
+    }
+  }
+  *iters = k;
+  *relres = std::sqrt(rrh) / bnh;
+  return nhmf_check_status(c, x.s);
+}
+
+// Flexible CG (Notay's FCG with one-term A-orthogonalisation) in FP64 from x = 0:
+//   z = M(r); p = z - (z.q_prev / p_prev.q_prev) p_prev; alpha = p.r / p.q.
+template <class Precond>
+nhmf_status fcg(Ctx& x, int strat, const double* b, double* sol, double rtol, int maxit, Precond&& precond,
+                long long* iters, double* relres) {
+  nhmf_ctx* c = x.c;
+  SolverWork& w = x.w;
+  double* sc = w.sc;
+  double bnh;
+  nhmf_status st = norm(x, b, BN, &bnh);
+  if (st != NHMF_OK) return st;
+  cudaMemsetAsync(sol, 0, x.n * sizeof(double), x.s);
+  *iters = 0;
+  *relres = 0.0;
+  if (!(bnh > 0.0)) return bnh == 0.0 ? NHMF_OK : fail(c, NHMF_ERR_NONFINITE, "fcg: non-finite right-hand side");
+  cudaMemcpyAsync(w.r, b, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+  double* q = w.q;
+  double* qprev = w.qprev;
+  double rn = bnh;
+  long long k = 0;
+  for (; k < maxit;) {
+    if ((st = precond(w.r, w.z)) != NHMF_OK) return st;
+    if (k == 0) {
+      cudaMemcpyAsync(w.p, w.z, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+    } else {
+      dot(x.n, w.z, qprev, sc + ZQ, w.partials, x.s);
+      ratio(sc + ZQ, sc + PQPREV, -1.0, sc + BETA, x.s);
+      axpby(x.n, 1.0, nullptr, w.z, 1.0, sc + BETA, w.p, x.s);
+    }
+    if ((st = launch_apply(c, NHMF_FP64, strat, w.p, q, x.s)) != NHMF_OK) return st;
+    dot(x.n, w.p, q, sc + PQ, w.partials, x.s);
+    dot(x.n, w.p, w.r, sc + PR, w.partials, x.s);
+    ratio(sc + PR, sc + PQ, 1.0, sc + ALPHA, x.s);
+    axpby(x.n, 1.0, sc + ALPHA, w.p, 1.0, nullptr, sol, x.s);
+    axpby(x.n, -1.0, sc + ALPHA, q, 1.0, nullptr, w.r, x.s);
+    cudaMemcpyAsync(sc + PQPREV, sc + PQ, sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+    std::swap(q, qprev);
+    ++k;
+    double pqh;
+    if ((st = read_scalar(x, sc + PQ, &pqh)) != NHMF_OK) return st;
+    if (!(pqh > 0.0)) return fail(c, NHMF_ERR_BREAKDOWN, "fcg: p^T A p <= 0");
+    if ((st = norm(x, w.r, RNORM, &rn)) != NHMF_OK) return st;
+    if (!std::isfinite(rn)) return fail(c, NHMF_ERR_NONFINITE, "fcg: non-finite residual");
+    if (rn <= rtol * bnh) break;
+  }
+  *iters = k;
+  *relres = rn / bnh;
+  return NHMF_OK;
+}
+
+nhmf_status update_diagonal(Ctx& x) {
+  nhmf_status st = launch_diagonal(x.c, x.w.diag, x.s);
+  if (st != NHMF_OK) return st;
+  reciprocal(x.n, x.w.diag, x.w.dinv, x.w.dinv32, x.s);
+  return cuda_check(x.c, cudaGetLastError(), "diagonal inverse");
+}
+
+// One linear solve A(ubar) sol = b with the chosen solver; the diagonal must be current.
+nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* sol, long long* outer,
+                   long long* inner, double* relres) {
+  SolverWork& w = x.w;
+  *inner = 0;
+  if (o.solver == NHMF_SOLVER_JACOBI_CG)
+    return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
+                       o.check_every, RZ0, outer, relres);
+  if (o.solver == NHMF_SOLVER_MIXED_FCG) {
+    auto precond = [&](const double* r, double* z) -> nhmf_status {
+      // z = ||r|| * A32^{-1}(r / ||r||) approximately, by FP32 Jacobi-CG
+      norm2(x.n, r, w.sc + TMP, w.partials, x.s);
+      to_fp32_scaled(x.n, r, w.sc + TMP, true, w.b32, x.s);
+      long long it = 0;
+      double rel = 0.0;
+      nhmf_status st = pcg<float>(x, o.strategy, w.b32, w.x32, w.dinv32, w.r32, w.z32, w.p32, w.q32, o.inner_rtol,
+                                  o.inner_max_iter, o.check_every, IN_RZ0, &it, &rel);
+      *inner += it;
+      if (st != NHMF_OK) return st;
+      to_fp64_scaled(x.n, w.x32, w.sc + TMP, z, x.s);
+      return cuda_check(x.c, cudaGetLastError(), "mixed preconditioner");
+    };
+    return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+  }
+  return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no trained network in this context");
+}
+
+int cache_mask(const nhmf_solve_opts& o) {
+  if (o.strategy != NHMF_CACHED) return 0;
+  return o.solver == NHMF_SOLVER_MIXED_FCG ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32) : NHMF_CACHE_FP64;
+}
+
+nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
+  if (!o || o->solver < 0 || o->solver > 2 || (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED) ||
+      o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
+      o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)
+    return fail(c, NHMF_ERR_ARG, "solve: bad options");
+  return NHMF_OK;
+}
+
+}  // namespace
+
+void free_work(nhmf_ctx* c) {
+  if (!c->work) return;
+  SolverWork& w = *c->work;
+  void* ptrs[] = {w.r, w.z, w.p, w.q, w.qprev, w.x, w.b, w.R, w.d, w.t, w.du, w.utry, w.diag, w.dinv,
+                  w.r32, w.z32, w.p32, w.q32, w.x32, w.b32, w.dinv32, w.sc, w.partials};
+  for (void* p : ptrs) cudaFree(p);
+  if (w.host) cudaFreeHost(w.host);
+  delete c->work;
+  c->work = nullptr;
+}
+
+}  // namespace nhmf
+
+using namespace nhmf;
+
+extern "C" {
+
+void nhmf_solve_opts_default(nhmf_solve_opts* o) {
+  if (!o) return;
+  o->solver = NHMF_SOLVER_JACOBI_CG;
+  o->strategy = NHMF_CACHED;
+  o->load_steps = 1;
+  o->first_step = 1;
+  o->last_step = 0;
+  o->compression = 0.0;
+  o->newton_rtol = 1e-8;
+  o->newton_max_iter = 20;
+  o->max_backtracks = 8;
+  o->linear_rtol = 1e-6;
+  o->linear_max_iter = 20000;
+  o->inner_rtol = 1e-2;
+  o->inner_max_iter = 200;
+  o->check_every = 10;
+}
+
+nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const double* b, double* xsol, long long* iters,
+                              long long* inner_iters, double* rel_res, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!b || !xsol || !iters || !inner_iters || !rel_res) return fail(c, NHMF_ERR_ARG, "linear_solve: bad argument");
+  nhmf_status st = check_opts(c, o);
+  if (st != NHMF_OK) return st;
+  if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "linear_solve: no linearisation point set");
+  if (o->strategy == NHMF_CACHED && (!c->cache64 || (o->solver == NHMF_SOLVER_MIXED_FCG && !c->cache32)))
+    return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
+  if ((st = ensure_work(c)) != NHMF_OK) return st;
+  Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
+  if ((st = update_diagonal(x)) != NHMF_OK) return st;
+  double rel = 0.0;
+  if ((st = linear(x, *o, b, xsol, iters, inner_iters, &rel)) != NHMF_OK) return st;
+  // true residual with an FP64 apply
+  if ((st = launch_apply(c, NHMF_FP64, o->strategy, xsol, x.w.t, x.s)) != NHMF_OK) return st;
+  axpby(x.n, 1.0, nullptr, b, -1.0, nullptr, x.w.t, x.s);
+  double rn, bn;
+  if ((st = norm(x, x.w.t, TMP, &rn)) != NHMF_OK) return st;
+  if ((st = norm(x, b, TMP, &bn)) != NHMF_OK) return st;
+  *rel_res = bn > 0 ? rn / bn : 0.0;
+  return NHMF_OK;
+}
+
+nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_solve_stats* stats, void* stream) {
+  using clk = std::chrono::steady_clock;
+  if (!c) return NHMF_ERR_ARG;
+  nhmf_status st = check_opts(c, o);
+  if (st != NHMF_OK) return st;
+  if (!u || !stats) return fail(c, NHMF_ERR_ARG, "solve: bad argument");
+  const int S = o->load_steps;
+  const int first = o->first_step > 0 ? o->first_step : 1;
+  const int last = o->last_step > 0 ? o->last_step : S;
+  if (first > last || last > S || last - first + 1 > NHMF_MAX_STEPS) return fail(c, NHMF_ERR_ARG, "solve: bad step range");
+  if ((st = ensure_work(c)) != NHMF_OK) return st;
+  *stats = nhmf_solve_stats{};
+  Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
+  SolverWork& w = x.w;
+  const long long M2 = (long long)c->g.M * c->g.M;
+  const unsigned bc_blocks = (unsigned)((M2 + 255) / 256);
+  const auto t_all = clk::now();
+  for (int step = first; step <= last; ++step) {
+    const int k = step - first;
+    const auto t0 = clk::now();
+    const double top = c->prm.bc == NHMF_BC_COMPRESSION ? -o->compression * step / S : 0.0;
+    double ref = -1.0, bnh = 0.0;
+    bool converged = false;
+    int it = 0;
+    for (; it <= o->newton_max_iter; ++it) {
+      if ((st = launch_residual(c, u, w.R, x.s)) != NHMF_OK) return st;
+      if ((st = nhmf_check_status(c, x.s)) != NHMF_OK) return st;
+      cudaMemsetAsync(w.d, 0, x.n * sizeof(double), x.s);
+      if (c->prm.bc != NHMF_BC_NONE) k_bc<<<bc_blocks, 256, 0, x.s>>>(c->prm.bc, c->g.M, c->g.M3, top, u, w.d, 0);
+      double dn;
+      if ((st = norm(x, w.d, TMP, &dn)) != NHMF_OK) return st;
+      if ((st = nhmf_set_linearization(c, u, cache_mask(*o), x.s)) != NHMF_OK) return st;
+      axpby(x.n, -1.0, nullptr, w.R, 0.0, nullptr, w.b, x.s);          // b = -R
+      if (dn > 0.0) {
+        if ((st = launch_apply(c, NHMF_FP64, o->strategy, w.d, w.t, x.s, true)) != NHMF_OK) return st;
+        axpby(x.n, -1.0, nullptr, w.t, 1.0, nullptr, w.b, x.s);        // b -= K d
+      }
+      if ((st = fix_rows64(c, w.d, w.b, 0, 0.0, x.s)) != NHMF_OK) return st;  // b_D = d_D
+      if ((st = norm(x, w.b, TMP, &bnh)) != NHMF_OK) return st;
+      if (ref < 0.0) ref = bnh;
+      if (dn == 0.0 && (bnh <= o->newton_rtol * ref || bnh == 0.0)) {
+        converged = true;
+        break;
+      }
+      if (it == o->newton_max_iter) break;
+      if ((st = update_diagonal(x)) != NHMF_OK) return st;
+      long long outer = 0, inner = 0;
+      double rel = 0.0;
+      if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel)) != NHMF_OK) return st;
+      stats->linear_iters[k] += outer;
+      stats->inner_iters[k] += inner;
+      // backtracking: halve the step while det F <= 0 somewhere
+      double theta = 1.0;
+      bool ok = false;
+      for (int bt = 0; bt <= o->max_backtracks; ++bt) {
+        cudaMemcpyAsync(w.utry, u, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+        axpby(x.n, theta, nullptr, w.du, 1.0, nullptr, w.utry, x.s);
+        st = launch_residual(c, w.utry, w.R, x.s);
+        if (st != NHMF_OK) return st;
+        st = nhmf_check_status(c, x.s);
+        if (st == NHMF_OK) {
+          ok = true;
+          break;
+        }
+        if (st != NHMF_ERR_NONPOS_J) return st;
+        theta *= 0.5;
+      }
+      if (!ok) return fail(c, NHMF_ERR_NONPOS_J, "Newton: backtracking could not keep det F > 0");
+      cudaMemcpyAsync(u, w.utry, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+      if (theta == 1.0 && c->prm.bc != NHMF_BC_NONE)
+        k_bc<<<bc_blocks, 256, 0, x.s>>>(c->prm.bc, c->g.M, c->g.M3, top, u, nullptr, 1);  // u_D = g exactly
+    }
+    cudaStreamSynchronize(x.s);
+    stats->newton_iters[k] = it;
+    stats->rel_residual[k] = ref > 0.0 ? bnh / ref : 0.0;
+    stats->seconds[k] = std::chrono::duration<double>(clk::now() - t0).count();
+    stats->total_linear_iters += stats->linear_iters[k];
+    stats->total_inner_iters += stats->inner_iters[k];
+    stats->steps_done = k + 1;
+    if (!converged) {
+      stats->total_seconds = std::chrono::duration<double>(clk::now() - t_all).count();
+      return fail(c, NHMF_ERR_NOT_CONVERGED, "Newton: load step " + std::to_string(step) + " did not converge");
+    }
+  }
+  stats->total_seconds = std::chrono::duration<double>(clk::now() - t_all).count();
+  return NHMF_OK;
+}
+
+}  // extern "C"

@@ -33,6 +33,38 @@ class nhmf_params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("bc", ctypes.c_int), ("top_uz", ctypes.c_double)]
 
 
+NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG = 0, 1, 2
+NHMF_MAX_STEPS = 64
+
+
+class nhmf_solve_opts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("strategy", ctypes.c_int), ("load_steps", ctypes.c_int),
+                ("first_step", ctypes.c_int), ("last_step", ctypes.c_int), ("compression", ctypes.c_double),
+                ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
+                ("max_backtracks", ctypes.c_int), ("linear_rtol", ctypes.c_double),
+                ("linear_max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("inner_max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class nhmf_solve_stats(ctypes.Structure):
+    _fields_ = [("steps_done", ctypes.c_int), ("newton_iters", ctypes.c_int * NHMF_MAX_STEPS),
+                ("linear_iters", ctypes.c_longlong * NHMF_MAX_STEPS),
+                ("inner_iters", ctypes.c_longlong * NHMF_MAX_STEPS),
+                ("fallbacks", ctypes.c_int * NHMF_MAX_STEPS),
+                ("rel_residual", ctypes.c_double * NHMF_MAX_STEPS),
+                ("seconds", ctypes.c_double * NHMF_MAX_STEPS),
+                ("total_linear_iters", ctypes.c_longlong), ("total_inner_iters", ctypes.c_longlong),
+                ("total_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        k = self.steps_done
+        return {"steps_done": k, "newton_iters": list(self.newton_iters[:k]),
+                "linear_iters": list(self.linear_iters[:k]), "inner_iters": list(self.inner_iters[:k]),
+                "fallbacks": list(self.fallbacks[:k]), "rel_residual": list(self.rel_residual[:k]),
+                "seconds": list(self.seconds[:k]), "total_linear_iters": self.total_linear_iters,
+                "total_inner_iters": self.total_inner_iters, "total_seconds": self.total_seconds}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _SIGS = {
@@ -46,6 +78,11 @@ _SIGS = {
     "nhmf_diagonal": (ctypes.c_int, [_P, _P, _P]),
     "nhmf_check_status": (ctypes.c_int, [_P, _P]),
     "nhmf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "nhmf_solve_opts_default": (None, [ctypes.POINTER(nhmf_solve_opts)]),
+    "nhmf_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, ctypes.POINTER(nhmf_solve_stats), _P]),
+    "nhmf_linear_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, _P,
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_double), _P]),
     "nhmf_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]),
 }
@@ -140,6 +177,36 @@ def nhmf_profile_read(ctx, kind):
     return ms.value, n.value
 
 
+def nhmf_solve_opts_default(**overrides):
+    o = nhmf_solve_opts()
+    lib().nhmf_solve_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def nhmf_solve(ctx, opts, u, stream=None):
+    """Run the Newton load steps; returns the stats (raises NhmfError on failure, with the
+    partial stats attached as `.stats`)."""
+    stats = nhmf_solve_stats()
+    st = lib().nhmf_solve(ctx, ctypes.byref(opts), _ptr(u), ctypes.byref(stats), _stream(stream))
+    if st != NHMF_OK:
+        err = NhmfError(st, lib().nhmf_last_error(ctx).decode())
+        err.stats = stats.as_dict()
+        raise err
+    return stats.as_dict()
+
+
+def nhmf_linear_solve(ctx, opts, b, x, stream=None):
+    """(outer iterations, inner iterations, true relative residual)."""
+    it, inner, rel = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, lib().nhmf_linear_solve(ctx, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(it),
+                                        ctypes.byref(inner), ctypes.byref(rel), _stream(stream)))
+    return it.value, inner.value, rel.value
+
+
 class Problem:
     """One mesh + material on the current CUDA device (owns an nhmf context)."""
 
@@ -177,3 +244,9 @@ class Problem:
     def diagonal(self, d):
         nhmf_diagonal(self.ctx, d)
         return d
+
+    def solve(self, u, **opts):
+        return nhmf_solve(self.ctx, nhmf_solve_opts_default(**opts), u)
+
+    def linear_solve(self, b, x, **opts):
+        return nhmf_linear_solve(self.ctx, nhmf_solve_opts_default(**opts), b, x)
