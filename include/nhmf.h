@@ -173,6 +173,28 @@ nhmf_status nhmf_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, double* u, nh
 nhmf_status nhmf_linear_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, const double* b, double* x,
                               long long* iters, long long* inner_iters, double* rel_res, void* stream);
 
+/* FP64 Jacobi-CG solve of A(u) x = b that allocates no memory (the paper has no
+ * counterpart; this is a deployment variant of nhmf_linear_solve with solver
+ * NHMF_SOLVER_JACOBI_CG).  For callers that cannot allocate device memory once running:
+ * code whose device memory is owned by a pool or budget, loops that must avoid the
+ * implicit device synchronisation of cudaMalloc/cudaFree, or hosts that forbid allocation
+ * after start-up.  The context must already exist and hold a linearisation point (and an
+ * FP64 point cache for NHMF_CACHED); both of those may allocate, at set-up time.
+ *   Scratch: one file-scope device array of 6.3 MB (six FP64 vectors of up to 131,072
+ *   entries, reduction partials, scalars), held by every GPU that loads the library until
+ *   the process exits.  Problems with more than 131,072 DoFs are rejected with
+ *   NHMF_ERR_ARG and a message naming the limit.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   Every call shares the array and it keeps the last call's contents (the call clears
+ *   what must start at zero): calls that overlap on the GPU, from any context or stream,
+ *   race and must be serialised by the caller.
+ * Arguments: strategy NHMF_ON_THE_FLY or NHMF_CACHED; rtol > 0 relative to ||b||; max_iter
+ * >= 1; b, x device FP64 arrays of 3*M^3; iters and rel_res (the true relative residual,
+ * recomputed with an FP64 apply) are host outputs.  Synchronises. */
+nhmf_status nhmf_linear_solve_noalloc(nhmf_ctx* ctx, int strategy, double rtol, int max_iter, const double* b,
+                                      double* x, long long* iters, double* rel_res, void* stream);
+
 /* Kernel timing.  While enabled, every operator call records a CUDA event pair on its
  * stream around its element kernels (the eight colour launches, not the vector memset or
  * the Dirichlet-row fix).  nhmf_profile_read() synchronises those events, returns the summed

@@ -80,6 +80,8 @@ _SIGS = {
     "nhmf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "nhmf_solve_opts_default": (None, [ctypes.POINTER(nhmf_solve_opts)]),
     "nhmf_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, ctypes.POINTER(nhmf_solve_stats), _P]),
+    "nhmf_linear_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P,
+                                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double), _P]),
     "nhmf_linear_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, _P,
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double), _P]),
@@ -205,6 +207,14 @@ def nhmf_linear_solve(ctx, opts, b, x, stream=None):
     _check(ctx, lib().nhmf_linear_solve(ctx, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(it),
                                         ctypes.byref(inner), ctypes.byref(rel), _stream(stream)))
     return it.value, inner.value, rel.value
+
+
+def nhmf_linear_solve_noalloc(ctx, strategy, rtol, max_iter, b, x, stream=None):
+    """Jacobi-CG solve with static scratch (no allocation); (iterations, true relative residual)."""
+    it, rel = ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, lib().nhmf_linear_solve_noalloc(ctx, strategy, rtol, max_iter, _ptr(b), _ptr(x), ctypes.byref(it),
+                                                ctypes.byref(rel), _stream(stream)))
+    return it.value, rel.value
 
 
 class Problem:
