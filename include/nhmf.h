@@ -140,6 +140,13 @@ typedef struct {
   double inner_rtol;    /* mixed: FP32 inner CG relative tolerance, default 1e-2 */
   int inner_max_iter;   /* mixed: FP32 inner CG iteration cap, default 200 */
   int check_every;      /* iterations between host convergence reads, default 10 */
+  int record_pairs;     /* JACOBI_CG with a U-Net: store training pairs (Newton (b, du) and CG
+                           (r_j, x* - x_j)) in the network's pair store, default 0 */
+  int cg_pair_every;    /* CG pairs at iterations j = k, 4k, 16k (k = this), default 8 */
+  double learned_jacobi_weight; /* LEARNED_FCG: z = N(r) + w D^-1 r, default 0 */
+  int learned_stall_window;     /* LEARNED_FCG: fall back to Jacobi-CG when the residual */
+  double learned_stall_factor;  /* drops by less than this factor over this many iterations
+                                   (defaults 10 and 0.9), or after linear_max_iter/4 iterations */
 } nhmf_solve_opts;
 
 typedef struct {
@@ -194,6 +201,39 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, const 
  * recomputed with an FP64 apply) are host outputs.  Synchronises. */
 nhmf_status nhmf_linear_solve_noalloc(nhmf_ctx* ctx, int strategy, double rtol, int max_iter, const double* b,
                                       double* x, long long* iters, double* rel_res, void* stream);
+
+/* ------------------------------------------------------------------ learned preconditioner
+ * A 3-level convolutional U-Net on the nodal grid (16 channels, 3x3x3 convolutions, ReLU,
+ * stride-2 down and transposed-convolution up paths with additive skips; 3 input and 3
+ * output channels = the displacement components), BF16 weights and activations with FP32
+ * accumulation on the tensor cores, FP32 master weights trained by Adam.  It maps a
+ * residual r (scaled to unit RMS) to a correction; as a preconditioner z = N(r) scaled back
+ * and zeroed on constrained DoFs.  Requires p*N divisible by 4.
+ * Parameters: a flat FP32 array, layer by layer (in, e0, d1, e1, d2, m2, u1, t1, u0, t0,
+ * out), each weight tensor then its bias; conv/down weights W[out][in][3][3][3], up
+ * weights U[in][out][3][3][3] (taps ordered dz, dy, dx from -1).
+ * Pair store: each pair is the normalised input and target, FP32 [2][3][M^3]. */
+nhmf_status nhmf_unet_create(nhmf_ctx* ctx, int pair_capacity);           /* allocates; sync */
+size_t nhmf_unet_num_params(const nhmf_ctx* ctx);
+int nhmf_unet_num_pairs(const nhmf_ctx* ctx);
+/* Copy the flat parameters from / to host memory (n must equal num_params); set resets
+ * the Adam moments.  Synchronous. */
+nhmf_status nhmf_unet_set_params(nhmf_ctx* ctx, const float* host_params, size_t n);
+nhmf_status nhmf_unet_get_params(nhmf_ctx* ctx, float* host_params, size_t n);
+/* y = N(x) for device FP32 planar x, y of 3*M^3 (no scaling, no masking).  Asynchronous. */
+nhmf_status nhmf_unet_forward(nhmf_ctx* ctx, const float* x, float* y, void* stream);
+/* Loss ||f (N(x) - e)||^2 / ||f e||^2 (f = 1 on free DoFs) and its gradient with respect to
+ * the parameters (copied to grads_host if not null).  Synchronises. */
+nhmf_status nhmf_unet_loss_grad(nhmf_ctx* ctx, const float* x, const float* e, double* loss, float* grads_host,
+                                void* stream);
+/* z = preconditioner(r) for device FP64 r, z (3*M^3).  Asynchronous. */
+nhmf_status nhmf_unet_precondition(nhmf_ctx* ctx, const double* r, double* z, void* stream);
+/* Append the pair (r / rms(r), e / rms(e)) to the pair store (dropped when full). */
+nhmf_status nhmf_unet_record_pair(nhmf_ctx* ctx, const double* r, const double* e, void* stream);
+/* `epochs` passes of Adam (learning rate lr) over the stored pairs in order, one pair per
+ * step; returns the mean loss of the first and of the last epoch.  Synchronises. */
+nhmf_status nhmf_unet_train(nhmf_ctx* ctx, int epochs, double lr, double* loss_first, double* loss_last,
+                            void* stream);
 
 /* Kernel timing.  While enabled, every operator call records a CUDA event pair on its
  * stream around its element kernels (the eight colour launches, not the vector memset or

@@ -87,6 +87,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->cache64);
   cudaFree(c->cache32);
   free_work(c);
+  unet_free(c);
   delete c;
 }
 

@@ -134,6 +134,11 @@ __global__ void k_reciprocal(long long n, const double* d, double* dinv64, float
   }
 }
 
+__global__ void k_mul(long long n, const double* d, double* x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= d[i];
+}
+
 __global__ void k_sqrt(double* x) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *x = sqrt(*x);
 }
@@ -195,6 +200,9 @@ void to_fp32_scaled(long long n, const double* x, const double* scale, bool inve
 }
 void to_fp64_scaled(long long n, const float* x, const double* scale, double* y, cudaStream_t s) {
   k_scale_convert<float, double><<<kEwBlocks, kEwThreads, 0, s>>>(n, x, scale, false, y);
+}
+void jacobi_apply(long long n, const double* dinv, double* x, cudaStream_t s) {
+  k_mul<<<kEwBlocks, kEwThreads, 0, s>>>(n, dinv, x);
 }
 void reciprocal(long long n, const double* d, double* dinv64, float* dinv32, cudaStream_t s) {
   k_reciprocal<<<kEwBlocks, kEwThreads, 0, s>>>(n, d, dinv64, dinv32);

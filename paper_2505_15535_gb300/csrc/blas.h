@@ -23,6 +23,8 @@ void axpby(long long n, double a, const double* pa, const double* x, double b, c
 void ratio(const double* num, const double* den, double sign, double* out, cudaStream_t s);
 void to_fp32_scaled(long long n, const double* x, const double* scale, bool invert, float* y, cudaStream_t s);
 void to_fp64_scaled(long long n, const float* x, const double* scale, double* y, cudaStream_t s);
+// x *= dinv (element-wise)
+void jacobi_apply(long long n, const double* dinv, double* x, cudaStream_t s);
 void reciprocal(long long n, const double* d, double* dinv64, float* dinv32, cudaStream_t s);
 
 }  // namespace nhmf

@@ -44,6 +44,7 @@ struct Geometry {
 }  // namespace nhmf
 
 namespace nhmf {
+struct UNet;
 // Work vectors of the solvers, allocated on first use.
 struct SolverWork {
   long long n = 0;
@@ -74,12 +75,28 @@ struct nhmf_ctx {
   struct Rec { int kind; int launches; cudaEvent_t a, b; };
   std::vector<Rec> prof;
   nhmf::SolverWork* work = nullptr;
+  nhmf::UNet* unet = nullptr;
 };
 
 namespace nhmf {
 
 enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u };
 void free_work(nhmf_ctx* c);
+nhmf_status ensure_work(nhmf_ctx* c);
+
+// U-Net preconditioner (unet.cu)
+nhmf_status unet_alloc(nhmf_ctx* c, int pair_capacity);
+void unet_free(nhmf_ctx* c);
+void unet_refresh_weights(UNet& u, cudaStream_t s);
+void unet_forward(UNet& u, cudaStream_t s);
+void unet_backward(UNet& u, cudaStream_t s);
+void unet_input_planar32(UNet& u, const float* x, cudaStream_t s);
+void unet_loss_and_grad(nhmf_ctx* c, const float* target, bool accumulate, cudaStream_t s);
+void unet_adam(UNet& u, float lr, cudaStream_t s);
+void unet_precondition(nhmf_ctx* c, const double* r, double* z, cudaStream_t s);
+nhmf_status unet_record(nhmf_ctx* c, const double* r, const double* e, cudaStream_t s);
+int unet_snapshot_begin(nhmf_ctx* c, const double* r, const double* xj, cudaStream_t s);
+void unet_snapshot_finish(nhmf_ctx* c, int slot, const double* xstar, cudaStream_t s);
 
 // raw = true applies the unconstrained operator K (no Dirichlet masking or identity rows).
 nhmf_status launch_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v,

@@ -4,9 +4,11 @@
 // only every `check_every` iterations.
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 #include "blas.h"
 #include "internal.h"
+#include "unet.h"
 
 namespace nhmf {
 namespace {
@@ -46,6 +48,8 @@ struct Ctx {
   SolverWork& w;
 };
 
+}  // namespace
+
 nhmf_status ensure_work(nhmf_ctx* c) {
   const long long n = 3 * c->g.M3;
   if (c->work && c->work->n == n) return NHMF_OK;
@@ -66,6 +70,8 @@ nhmf_status ensure_work(nhmf_ctx* c) {
   return NHMF_OK;
 }
 
+namespace {
+
 nhmf_status read_scalar(Ctx& x, const double* dev, double* out) {
   nhmf_status st = cuda_check(x.c, cudaMemcpyAsync(x.w.host, dev, sizeof(double), cudaMemcpyDeviceToHost, x.s), "scalar read");
   if (st == NHMF_OK) st = cuda_check(x.c, cudaStreamSynchronize(x.s), "scalar sync");
@@ -83,9 +89,13 @@ template <> struct Prec<double> { static constexpr int id = NHMF_FP64; };
 template <> struct Prec<float> { static constexpr int id = NHMF_FP32; };
 
 // Jacobi-preconditioned CG from x = 0 on A in precision T.  Scalars use slots base..base+4.
-template <typename T>
+struct NoSnap {
+  void operator()(long long, const void*, const void*) const {}
+};
+
+template <typename T, class Snap = NoSnap>
 nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z, T* p, T* q, double rtol,
-                int maxit, int check_every, int base, long long* iters, double* relres) {
+                int maxit, int check_every, int base, long long* iters, double* relres, Snap snap = Snap()) {
   nhmf_ctx* c = x.c;
   double* sc = x.w.sc;
   double* rz[2] = {sc + base + 0, sc + base + 1};
@@ -111,6 +121,7 @@ nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z
     pcg_update<T>(x.n, rz[k & 1], pq, sol, r, p, q, dinv, z, rz[(k + 1) & 1], rr, x.w.partials, c->status, x.s);
     pcg_direction<T>(x.n, rz[(k + 1) & 1], rz[k & 1], z, p, x.s);
     ++k;
+    snap(k, r, sol);
     if (k % check_every == 0 || k == maxit) {
       if ((st = read_scalar(x, rr, &rrh)) != NHMF_OK) return st;
       if (!std::isfinite(rrh)) return fail(c, NHMF_ERR_NONFINITE, "pcg: non-finite residual");
@@ -124,9 +135,11 @@ nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z
 
 // Flexible CG (Notay's FCG with one-term A-orthogonalisation) in FP64 from x = 0:
 //   z = M(r); p = z - (z.q_prev / p_prev.q_prev) p_prev; alpha = p.r / p.q.
+// Returns NHMF_ERR_NOT_CONVERGED (with sol, w.r the current iterate and residual) when the
+// residual drops by less than stall_factor over stall_window iterations or maxit is reached.
 template <class Precond>
 nhmf_status fcg(Ctx& x, int strat, const double* b, double* sol, double rtol, int maxit, Precond&& precond,
-                long long* iters, double* relres) {
+                long long* iters, double* relres, int stall_window = 0, double stall_factor = 1.0) {
   nhmf_ctx* c = x.c;
   SolverWork& w = x.w;
   double* sc = w.sc;
@@ -142,6 +155,8 @@ nhmf_status fcg(Ctx& x, int strat, const double* b, double* sol, double rtol, in
   double* qprev = w.qprev;
   double rn = bnh;
   long long k = 0;
+  std::vector<double> hist;
+  hist.push_back(bnh);
   for (; k < maxit;) {
     if ((st = precond(w.r, w.z)) != NHMF_OK) return st;
     if (k == 0) {
@@ -165,11 +180,18 @@ nhmf_status fcg(Ctx& x, int strat, const double* b, double* sol, double rtol, in
     if (!(pqh > 0.0)) return fail(c, NHMF_ERR_BREAKDOWN, "fcg: p^T A p <= 0");
     if ((st = norm(x, w.r, RNORM, &rn)) != NHMF_OK) return st;
     if (!std::isfinite(rn)) return fail(c, NHMF_ERR_NONFINITE, "fcg: non-finite residual");
+    hist.push_back(rn);
     if (rn <= rtol * bnh) break;
+    if (stall_window > 0 && (long long)hist.size() > stall_window &&
+        rn > stall_factor * hist[hist.size() - 1 - stall_window]) {
+      *iters = k;
+      *relres = rn / bnh;
+      return NHMF_ERR_NOT_CONVERGED;
+    }
   }
   *iters = k;
   *relres = rn / bnh;
-  return NHMF_OK;
+  return rn <= rtol * bnh ? NHMF_OK : NHMF_ERR_NOT_CONVERGED;
 }
 
 nhmf_status update_diagonal(Ctx& x) {
@@ -181,12 +203,62 @@ nhmf_status update_diagonal(Ctx& x) {
 
 // One linear solve A(ubar) sol = b with the chosen solver; the diagonal must be current.
 nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* sol, long long* outer,
-                   long long* inner, double* relres) {
+                   long long* inner, double* relres, int* fallbacks) {
   SolverWork& w = x.w;
   *inner = 0;
-  if (o.solver == NHMF_SOLVER_JACOBI_CG)
-    return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
-                       o.check_every, RZ0, outer, relres);
+  if (o.solver == NHMF_SOLVER_JACOBI_CG) {
+    UNet* u = x.c->unet;
+    if (!(o.record_pairs && u && u->npairs < u->cap))
+      return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
+                         o.check_every, RZ0, outer, relres);
+    // record CG pairs (r_j, x* - x_j) at j = k, 4k, 16k
+    std::vector<int> slots;
+    const long long every = o.cg_pair_every > 0 ? o.cg_pair_every : 8;
+    auto snap = [&](long long j, const void* r, const void* xj) {
+      if (j == every || j == 4 * every || j == 16 * every) {
+        const int slot = unet_snapshot_begin(x.c, static_cast<const double*>(r), static_cast<const double*>(xj), x.s);
+        if (slot >= 0) slots.push_back(slot);
+      }
+    };
+    nhmf_status st = pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol,
+                                 o.linear_max_iter, o.check_every, RZ0, outer, relres, snap);
+    if (st != NHMF_OK) return st;
+    for (int slot : slots) unet_snapshot_finish(x.c, slot, sol, x.s);
+    return cuda_check(x.c, cudaGetLastError(), "pair recording");
+  }
+  if (o.solver == NHMF_SOLVER_LEARNED_FCG) {
+    if (!x.c->unet) return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no network in this context");
+    auto precond = [&](const double* r, double* z) -> nhmf_status {
+      unet_precondition(x.c, r, z, x.s);
+      if (o.learned_jacobi_weight != 0.0) {
+        cudaMemcpyAsync(w.t, r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+        jacobi_apply(x.n, w.dinv, w.t, x.s);
+        axpby(x.n, o.learned_jacobi_weight, nullptr, w.t, 1.0, nullptr, z, x.s);
+      }
+      return cuda_check(x.c, cudaGetLastError(), "learned preconditioner");
+    };
+    const int cap = std::max(1, o.linear_max_iter / 4);
+    nhmf_status st = fcg(x, o.strategy, b, sol, o.linear_rtol, cap, precond, outer, relres,
+                         o.learned_stall_window, o.learned_stall_factor);
+    if (st == NHMF_OK) return st;
+    if (st != NHMF_ERR_NOT_CONVERGED) return st;
+    // fall back to Jacobi-CG on the remaining residual: A d = r, sol += d
+    *fallbacks += 1;
+    double bnh, rnh;
+    if ((st = norm(x, b, TMP, &bnh)) != NHMF_OK) return st;
+    if ((st = norm(x, w.r, TMP, &rnh)) != NHMF_OK) return st;
+    cudaMemcpyAsync(w.t, w.r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+    long long it2 = 0;
+    double rel2 = 0.0;
+    const double rtol2 = rnh > 0.0 ? std::min(1.0, o.linear_rtol * bnh / rnh) : 1.0;
+    st = pcg<double>(x, o.strategy, w.t, w.utry, w.dinv, w.r, w.z, w.p, w.q, rtol2, o.linear_max_iter,
+                     o.check_every, RZ0, &it2, &rel2);
+    if (st != NHMF_OK) return st;
+    axpby(x.n, 1.0, nullptr, w.utry, 1.0, nullptr, sol, x.s);
+    *outer += it2;
+    *relres = rel2 * rnh / bnh;
+    return cuda_check(x.c, cudaGetLastError(), "fallback");
+  }
   if (o.solver == NHMF_SOLVER_MIXED_FCG) {
     auto precond = [&](const double* r, double* z) -> nhmf_status {
       // z = ||r|| * A32^{-1}(r / ||r||) approximately, by FP32 Jacobi-CG
@@ -203,7 +275,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     };
     return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
   }
-  return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no trained network in this context");
+  return fail(x.c, NHMF_ERR_ARG, "unknown solver");
 }
 
 int cache_mask(const nhmf_solve_opts& o) {
@@ -254,6 +326,11 @@ void nhmf_solve_opts_default(nhmf_solve_opts* o) {
   o->inner_rtol = 1e-2;
   o->inner_max_iter = 200;
   o->check_every = 10;
+  o->record_pairs = 0;
+  o->cg_pair_every = 8;
+  o->learned_jacobi_weight = 0.0;
+  o->learned_stall_window = 10;
+  o->learned_stall_factor = 0.9;
 }
 
 nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const double* b, double* xsol, long long* iters,
@@ -269,7 +346,8 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
   if ((st = update_diagonal(x)) != NHMF_OK) return st;
   double rel = 0.0;
-  if ((st = linear(x, *o, b, xsol, iters, inner_iters, &rel)) != NHMF_OK) return st;
+  int fb = 0;
+  if ((st = linear(x, *o, b, xsol, iters, inner_iters, &rel, &fb)) != NHMF_OK) return st;
   // true residual with an FP64 apply
   if ((st = launch_apply(c, NHMF_FP64, o->strategy, xsol, x.w.t, x.s)) != NHMF_OK) return st;
   axpby(x.n, 1.0, nullptr, b, -1.0, nullptr, x.w.t, x.s);
@@ -328,7 +406,9 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
       if ((st = update_diagonal(x)) != NHMF_OK) return st;
       long long outer = 0, inner = 0;
       double rel = 0.0;
-      if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel)) != NHMF_OK) return st;
+      if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel, &stats->fallbacks[k])) != NHMF_OK) return st;
+      if (o->record_pairs && o->solver == NHMF_SOLVER_JACOBI_CG && c->unet)
+        if ((st = unet_record(c, w.b, w.du, x.s)) != NHMF_OK) return st;   // Newton pair (b, du)
       stats->linear_iters[k] += outer;
       stats->inner_iters[k] += inner;
       // backtracking: halve the step while det F <= 0 somewhere

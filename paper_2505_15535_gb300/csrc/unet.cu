@@ -1,0 +1,755 @@
+// Learned preconditioner: a 3-level convolutional U-Net on the nodal grid, with BF16 weights
+// and activations, FP32 accumulation and FP32 master weights trained by Adam.
+//
+// Network (channels C = 16, ReLU r; grids M0 = M, M1 = (M0-1)/2+1, M2 = (M1-1)/2+1):
+//   a0 = r(conv(x)) 3->C;  s0 = r(conv(a0));  d1 = r(down(s0));  s1 = r(conv(d1));
+//   d2 = r(down(s1));  m2 = r(conv(d2));  u1 = r(up(m2) + s1);  t1 = r(conv(u1));
+//   u0 = r(up(t1) + s0);  t0 = r(conv(u0));  y = conv(t0) C->3
+// with 3x3x3 zero-padded cross-correlations: conv (stride 1), down (stride 2) and up (the
+// transposed stride-2 convolution).  Activations are channels-last [voxel][16] BF16 (32 B
+// per voxel, one DRAM sector); inputs and outputs with 3 channels are padded to 16 with
+// zero weights.  Every convolution - forward, backward-data and the weight gradient - is an
+// implicit GEMM on the tensor cores with mma.sync m16n8k16 BF16 -> FP32:
+//   forward/backward-data: rows = 16 output voxels, K = 16 input channels per tap, N = 16
+//   output channels (two n8 tiles), 27 taps accumulated in registers;
+//   weight gradient: rows = 16 channels of the per-voxel operand, K = 16 voxels, N = 16
+//   channels of the gathered operand; partial sums per block, reduced in a fixed order.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "blas.h"
+#include "internal.h"
+#include "unet.h"
+
+namespace nhmf {
+namespace {
+
+constexpr int kC = 16;
+enum Gather { S1 = 0, DOWN2 = 1, UP2 = 2 };
+enum Kind { CONV = 0, DOWN = 1, UP = 2 };
+constexpr int kConvBlocks = 1216;  // 8 per SM
+constexpr int kWgBlocks = 608;     // weight-gradient partial blocks (4 per SM)
+
+__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Source coordinate of output coordinate o for tap offset d (-1, 0, 1), or -1 if outside.
+template <int G>
+__device__ __forceinline__ int src1(int o, int d, int m_in) {
+  int s;
+  if (G == S1) {
+    s = o + d;
+  } else if (G == DOWN2) {
+    s = 2 * o + d;
+  } else {
+    const int t = o - d;
+    if (t & 1) return -1;
+    s = t >> 1;
+  }
+  return (s >= 0 && s < m_in) ? s : -1;
+}
+
+template <int G>
+__device__ __forceinline__ long long src_voxel(int i, int j, int k, int dx, int dy, int dz, int m_in) {
+  const int x = src1<G>(i, dx, m_in), y = src1<G>(j, dy, m_in), z = src1<G>(k, dz, m_in);
+  if (x < 0 || y < 0 || z < 0) return -1;
+  return x + (long long)m_in * (y + (long long)m_in * z);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+struct ConvArgs {
+  const __nv_bfloat16* in;
+  int m_in;
+  const __nv_bfloat16* w;      // [27][16 co][16 ci]
+  const float* bias;           // [16] or null (zero beyond cout)
+  const __nv_bfloat16* add;    // [m_out^3][16] or null, added before the ReLU
+  const __nv_bfloat16* mask;   // [m_out^3][16] or null, output zeroed where mask <= 0
+  int relu;
+  __nv_bfloat16* out;          // [m_out^3][16]
+  float* out_planar;           // or [3][m_out^3] FP32 (channels 0..2)
+  int m_out;
+};
+
+template <int G>
+__global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
+  __shared__ uint32_t sw[27 * 16 * 12];  // rows of 8 u32 (16 ci) padded to 12: conflict-free B loads
+  const uint32_t* wg = reinterpret_cast<const uint32_t*>(a.w);
+  for (int idx = threadIdx.x; idx < 27 * 16 * 8; idx += blockDim.x) sw[(idx >> 3) * 12 + (idx & 7)] = wg[idx];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const long long mo = a.m_out, nvox = mo * mo * mo, ntiles = (nvox + 15) / 16;
+  const uint32_t* in32 = reinterpret_cast<const uint32_t*>(a.in);
+  for (long long tile = (long long)blockIdx.x * 8 + warp; tile < ntiles; tile += (long long)gridDim.x * 8) {
+    const long long v0 = tile * 16 + g, v1 = v0 + 8;
+    const bool ok0 = v0 < nvox, ok1 = v1 < nvox;
+    const int i0 = int(v0 % mo), j0 = int((v0 / mo) % mo), k0 = int(v0 / (mo * mo));
+    const int i1 = int(v1 % mo), j1 = int((v1 / mo) % mo), k1 = int(v1 / (mo * mo));
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 3
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+      const long long s0 = ok0 ? src_voxel<G>(i0, j0, k0, dx, dy, dz, a.m_in) : -1;
+      const long long s1 = ok1 ? src_voxel<G>(i1, j1, k1, dx, dy, dz, a.m_in) : -1;
+      const uint32_t A0 = s0 >= 0 ? __ldg(in32 + s0 * 8 + t) : 0u;
+      const uint32_t A1 = s1 >= 0 ? __ldg(in32 + s1 * 8 + t) : 0u;
+      const uint32_t A2 = s0 >= 0 ? __ldg(in32 + s0 * 8 + 4 + t) : 0u;
+      const uint32_t A3 = s1 >= 0 ? __ldg(in32 + s1 * 8 + 4 + t) : 0u;
+      const uint32_t* w0 = sw + (tap * 16 + g) * 12;
+      const uint32_t* w1 = sw + (tap * 16 + 8 + g) * 12;
+      mma16816(acc0, A0, A1, A2, A3, w0[t], w0[4 + t]);
+      mma16816(acc1, A0, A1, A2, A3, w1[t], w1[4 + t]);
+    }
+    auto emit = [&](long long v, int ch, float x0, float x1) {
+      if (a.bias) {
+        x0 += a.bias[ch];
+        x1 += a.bias[ch + 1];
+      }
+      if (a.add) {
+        const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(a.add + v * kC + ch);
+        x0 += __low2float(ad);
+        x1 += __high2float(ad);
+      }
+      if (a.relu) {
+        x0 = fmaxf(x0, 0.f);
+        x1 = fmaxf(x1, 0.f);
+      }
+      if (a.mask) {
+        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kC + ch);
+        x0 = __low2float(mk) > 0.f ? x0 : 0.f;
+        x1 = __high2float(mk) > 0.f ? x1 : 0.f;
+      }
+      if (a.out_planar) {
+        if (ch < 3) a.out_planar[ch * nvox + v] = x0;
+        if (ch + 1 < 3) a.out_planar[(ch + 1) * nvox + v] = x1;
+      } else {
+        *reinterpret_cast<__nv_bfloat162*>(a.out + v * kC + ch) = __floats2bfloat162_rn(x0, x1);
+      }
+    };
+    if (ok0) {
+      emit(v0, 2 * t, acc0[0], acc0[1]);
+      emit(v0, 8 + 2 * t, acc1[0], acc1[1]);
+    }
+    if (ok1) {
+      emit(v1, 2 * t, acc0[2], acc0[3]);
+      emit(v1, 8 + 2 * t, acc1[2], acc1[3]);
+    }
+  }
+}
+
+// Weight gradient G[tap][a][b] = sum_v P[v][a] Q[src(v, tap)][b] over the P grid, for the
+// gathers S1 and DOWN2; 9 warps, warp w owns taps 3w..3w+2; per-block partials.
+template <int G>
+__global__ void __launch_bounds__(288) k_wgrad(const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
+                                               float* partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const long long m = mp, nvox = m * m * m, nks = (nvox + 15) / 16;
+  float acc[3][2][4] = {};
+  for (long long ks = blockIdx.x; ks < nks; ks += gridDim.x) {
+    const long long kb = ks * 16;
+    const long long vv[4] = {kb + 2 * t, kb + 2 * t + 1, kb + 8 + 2 * t, kb + 9 + 2 * t};
+    int ci[4], cj[4], ck[4];
+    bool ok[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ok[q] = vv[q] < nvox;
+      ci[q] = int(vv[q] % m);
+      cj[q] = int((vv[q] / m) % m);
+      ck[q] = int(vv[q] / (m * m));
+    }
+    const __nv_bfloat16 z = __float2bfloat16(0.f);
+    auto p = [&](int q, int ch) { return ok[q] ? P[vv[q] * kC + ch] : z; };
+    const uint32_t A0 = pack_bf16(p(0, g), p(1, g)), A1 = pack_bf16(p(0, g + 8), p(1, g + 8));
+    const uint32_t A2 = pack_bf16(p(2, g), p(3, g)), A3 = pack_bf16(p(2, g + 8), p(3, g + 8));
+#pragma unroll
+    for (int jt = 0; jt < 3; ++jt) {
+      const int tap = 3 * warp + jt;
+      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+      long long s[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] = ok[q] ? src_voxel<G>(ci[q], cj[q], ck[q], dx, dy, dz, mq) : -1;
+      auto qv = [&](int q, int ch) { return s[q] >= 0 ? Q[s[q] * kC + ch] : z; };
+      mma16816(acc[jt][0], A0, A1, A2, A3, pack_bf16(qv(0, g), qv(1, g)), pack_bf16(qv(2, g), qv(3, g)));
+      mma16816(acc[jt][1], A0, A1, A2, A3, pack_bf16(qv(0, g + 8), qv(1, g + 8)),
+               pack_bf16(qv(2, g + 8), qv(3, g + 8)));
+    }
+  }
+  float* out = partial + (long long)blockIdx.x * 27 * 256;
+#pragma unroll
+  for (int jt = 0; jt < 3; ++jt) {
+    const int tap = 3 * warp + jt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = 8 * h + 2 * t;
+      out[tap * 256 + g * 16 + b] = acc[jt][h][0];
+      out[tap * 256 + g * 16 + b + 1] = acc[jt][h][1];
+      out[tap * 256 + (g + 8) * 16 + b] = acc[jt][h][2];
+      out[tap * 256 + (g + 8) * 16 + b + 1] = acc[jt][h][3];
+    }
+  }
+}
+
+// Sum the partials in block order and write the layer's weight gradient in the flat layout:
+// conv/down W[o][c][tap] (a = o, b = c); up U[c][o][tap] (a = c, b = o).
+__global__ void k_wgrad_reduce(const float* partial, int nblocks, float* grad_w, int kind, int cin, int cout) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 27 * 256) return;
+  const int tap = idx / 256, aa = (idx / 16) % 16, bb = idx % 16;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * 27 * 256 + idx];
+  if (kind == UP) {
+    if (aa < cin && bb < cout) grad_w[((long long)aa * cout + bb) * 27 + tap] = s;
+  } else {
+    if (aa < cout && bb < cin) grad_w[((long long)aa * cin + bb) * 27 + tap] = s;
+  }
+}
+
+// Bias gradient: per-block channel sums of P, then a fixed-order reduction.
+__global__ void __launch_bounds__(256) k_bgrad_partial(const __nv_bfloat16* P, long long nvox, float* partial) {
+  const int ch = threadIdx.x & 15, lanegrp = threadIdx.x >> 4;  // 16 voxel lanes x 16 channels
+  float s = 0.f;
+  for (long long v = (long long)blockIdx.x * 16 + lanegrp; v < nvox; v += (long long)gridDim.x * 16)
+    s += __bfloat162float(P[v * kC + ch]);
+  __shared__ float sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    float r = 0.f;
+    for (int l = 0; l < 16; ++l) r += sh[l * 16 + threadIdx.x];
+    partial[blockIdx.x * 16 + threadIdx.x] = r;
+  }
+}
+
+__global__ void k_bgrad_reduce(const float* partial, int nblocks, float* grad_b, int cout) {
+  const int ch = threadIdx.x;
+  if (ch >= cout) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += partial[b * 16 + ch];
+  grad_b[ch] = s;
+}
+
+// Forward and backward-data BF16 weights of one layer from the FP32 master weights.
+__global__ void k_layer_weights(const float* w, int kind, int cin, int cout, __nv_bfloat16* wf, __nv_bfloat16* wb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 27 * 256) return;
+  const int tap = idx / 256, co = (idx / 16) % 16, ci = idx % 16;
+  float f = 0.f, b = 0.f;
+  if (kind == UP) {
+    // forward: co = o, ci = c: U[c][o][tap];  backward-data (DOWN2 gather): co = c, ci = o
+    if (ci < cin && co < cout) f = w[((long long)ci * cout + co) * 27 + tap];
+    if (co < cin && ci < cout) b = w[((long long)co * cout + ci) * 27 + tap];
+  } else {
+    // forward: W[o = co][c = ci][tap]; backward-data: co = c, ci = o, taps flipped for conv
+    if (co < cout && ci < cin) f = w[((long long)co * cin + ci) * 27 + tap];
+    const int tb = kind == CONV ? 26 - tap : tap;
+    if (ci < cout && co < cin) b = w[((long long)ci * cin + co) * 27 + tb];
+  }
+  wf[idx] = __float2bfloat16(f);
+  wb[idx] = __float2bfloat16(b);
+}
+
+__global__ void k_adam(long long n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                       float eps, float bc1, float bc2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+__device__ __forceinline__ bool constrained_dof(int bc, int c, long long v, int M) {
+  const int i = int(v % M), k = int(v / ((long long)M * M));
+  if (bc == NHMF_BC_CLAMP_X0) return i == 0;
+  if (bc == NHMF_BC_COMPRESSION) return k == 0 || (c == 2 && k == M - 1);
+  return false;
+}
+
+// Network input: x16[v][c] = scale * src[c][v] (c < 3), 0 for c >= 3; scale = mul / (*den)
+// when den is given, else mul.
+template <typename TS>
+__global__ void k_input(const TS* src, long long n, const double* den, double mul, __nv_bfloat16* x16) {
+  const float s = float(den ? mul / *den : mul);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    uint32_t w[8];
+    w[0] = pack_bf16(__float2bfloat16(float(src[v]) * s), __float2bfloat16(float(src[n + v]) * s));
+    w[1] = pack_bf16(__float2bfloat16(float(src[2 * n + v]) * s), __float2bfloat16(0.f));
+    for (int q = 2; q < 8; ++q) w[q] = 0u;
+    uint4* dst = reinterpret_cast<uint4*>(x16 + v * kC);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+}
+
+// Masked loss sums: partials of ||f (y - e)||^2 and ||f e||^2.
+__global__ void __launch_bounds__(kRedThreads) k_loss_partials(const float* y, const float* e, long long n, int bc,
+                                                               int M, double* partials) {
+  double num = 0.0, den = 0.0;
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < 3 * n; i += (long long)kRedBlocks * kRedThreads) {
+    const int c = int(i / n);
+    if (constrained_dof(bc, c, i % n, M)) continue;
+    const double d = double(y[i]) - double(e[i]);
+    num += d * d;
+    den += double(e[i]) * double(e[i]);
+  }
+  __shared__ double sh[2][kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, o);
+    den += __shfl_down_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = num;
+    sh[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) {
+      a += sh[0][w];
+      b += sh[1][w];
+    }
+    partials[blockIdx.x] = a;
+    partials[kRedBlocks + blockIdx.x] = b;
+  }
+}
+
+__global__ void k_loss_final(const double* partials, double* num, double* den, double* loss_acc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < kRedBlocks; ++i) {
+    a += partials[i];
+    b += partials[kRedBlocks + i];
+  }
+  *num = a;
+  *den = b;
+  if (loss_acc) *loss_acc += b > 0.0 ? a / b : 0.0;
+}
+
+// dy16[v][c] = 2 f (y - e) / den for c < 3, 0 otherwise.
+__global__ void k_loss_grad(const float* y, const float* e, long long n, int bc, int M, const double* den,
+                            __nv_bfloat16* dy16) {
+  const float s = float(2.0 / *den);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    float d[3];
+    for (int c = 0; c < 3; ++c)
+      d[c] = constrained_dof(bc, c, v, M) ? 0.f : s * (y[c * n + v] - e[c * n + v]);
+    uint4* dst = reinterpret_cast<uint4*>(dy16 + v * kC);
+    dst[0] = make_uint4(pack_bf16(__float2bfloat16(d[0]), __float2bfloat16(d[1])),
+                        pack_bf16(__float2bfloat16(d[2]), __float2bfloat16(0.f)), 0u, 0u);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// z = mask(y) * mul * (*scale) as FP64 (the preconditioner output); z_D = 0.
+__global__ void k_output(const float* y, long long n, int bc, int M, const double* scale, double mul, double* z) {
+  const double s = scale ? mul * *scale : mul;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i / n);
+    z[i] = constrained_dof(bc, c, i % n, M) ? 0.0 : s * double(y[i]);
+  }
+}
+
+// pair slot <- (src * mul / *den) as FP32
+__global__ void k_store_scaled(const double* src, long long n3, const double* den, double mul, float* dst) {
+  const double s = mul / *den;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = float(src[i] * s);
+}
+
+const int kLayerKind[11] = {CONV, CONV, DOWN, CONV, DOWN, CONV, UP, CONV, UP, CONV, CONV};
+const int kLayerCin[11] = {3, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
+const int kLayerCout[11] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 3};
+enum { L_IN = 0, L_E0, L_D1, L_E1, L_D2, L_M2, L_U1, L_T1, L_U0, L_T0, L_OUT };
+
+template <int G>
+void conv_launch(const ConvArgs& a, cudaStream_t s) {
+  k_conv<G><<<kConvBlocks, 256, 0, s>>>(a);
+}
+
+// out = act(conv_G(in; w) + bias + add) * mask
+void conv(int gather, const __nv_bfloat16* in, int m_in, const __nv_bfloat16* w, const float* bias,
+          const __nv_bfloat16* add, const __nv_bfloat16* mask, bool relu, __nv_bfloat16* out, float* out_planar,
+          int m_out, cudaStream_t s) {
+  ConvArgs a{in, m_in, w, bias, add, mask, relu ? 1 : 0, out, out_planar, m_out};
+  if (gather == S1)
+    conv_launch<S1>(a, s);
+  else if (gather == DOWN2)
+    conv_launch<DOWN2>(a, s);
+  else
+    conv_launch<UP2>(a, s);
+}
+
+void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
+           cudaStream_t s) {
+  const long long nks = ((long long)mp * mp * mp + 15) / 16;
+  const int blocks = (int)std::min<long long>(kWgBlocks, nks);
+  if (gather == S1)
+    k_wgrad<S1><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
+  else
+    k_wgrad<DOWN2><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
+  const UNetLayer& L = u.L[layer];
+  k_wgrad_reduce<<<(27 * 256 + 255) / 256, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
+}
+
+void bgrad(UNet& u, int layer, const __nv_bfloat16* P, long long nvox, cudaStream_t s) {
+  const int blocks = 256;
+  float* part = u.partial + (long long)kWgBlocks * 27 * 256;
+  k_bgrad_partial<<<blocks, 256, 0, s>>>(P, nvox, part);
+  k_bgrad_reduce<<<1, 32, 0, s>>>(part, blocks, u.grads + u.L[layer].boff, u.L[layer].cout);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host API pieces
+nhmf_status unet_alloc(nhmf_ctx* c, int cap) {
+  if ((c->g.M - 1) % 4 != 0) return fail(c, NHMF_ERR_ARG, "unet: p*N must be divisible by 4 (two stride-2 levels)");
+  if (c->unet) return fail(c, NHMF_ERR_STATE, "unet: already created");
+  UNet* u = new UNet();
+  c->unet = u;
+  u->M0 = c->g.M;
+  u->M1 = (u->M0 - 1) / 2 + 1;
+  u->M2 = (u->M1 - 1) / 2 + 1;
+  u->N0 = (long long)u->M0 * u->M0 * u->M0;
+  u->N1 = (long long)u->M1 * u->M1 * u->M1;
+  u->N2 = (long long)u->M2 * u->M2 * u->M2;
+  long long off = 0;
+  for (int l = 0; l < 11; ++l) {
+    UNetLayer& L = u->L[l];
+    L.kind = kLayerKind[l];
+    L.cin = kLayerCin[l];
+    L.cout = kLayerCout[l];
+    L.woff = off;
+    off += (long long)L.cin * L.cout * 27;
+    L.boff = off;
+    off += L.cout;
+  }
+  u->nparams = off;
+  u->cap = cap;
+  bool ok = true;
+  auto A = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+    if (ok) cudaMemset(*p, 0, bytes);
+  };
+  A((void**)&u->params, off * sizeof(float));
+  A((void**)&u->grads, off * sizeof(float));
+  A((void**)&u->adam_m, off * sizeof(float));
+  A((void**)&u->adam_v, off * sizeof(float));
+  for (int l = 0; l < 11; ++l) {
+    A((void**)&u->L[l].wf, 27 * 256 * sizeof(__nv_bfloat16));
+    A((void**)&u->L[l].wb, 27 * 256 * sizeof(__nv_bfloat16));
+  }
+  const size_t b0 = u->N0 * kC * sizeof(__nv_bfloat16), b1 = u->N1 * kC * sizeof(__nv_bfloat16),
+               b2 = u->N2 * kC * sizeof(__nv_bfloat16);
+  for (__nv_bfloat16** p : {&u->x16, &u->a0, &u->s0, &u->u0, &u->t0, &u->g0a, &u->g0b, &u->g0c}) A((void**)p, b0);
+  for (__nv_bfloat16** p : {&u->d1, &u->s1, &u->u1, &u->t1, &u->g1a, &u->g1b, &u->g1c}) A((void**)p, b1);
+  for (__nv_bfloat16** p : {&u->d2, &u->m2, &u->g2a, &u->g2b}) A((void**)p, b2);
+  A((void**)&u->y, 3 * u->N0 * sizeof(float));
+  A((void**)&u->partial, ((size_t)kWgBlocks * 27 * 256 + 256 * 16) * sizeof(float));
+  A((void**)&u->sc, 16 * sizeof(double));
+  if (cap > 0) A((void**)&u->pairs, (size_t)cap * 2 * 3 * u->N0 * sizeof(float));
+  if (!ok) return fail(c, NHMF_ERR_OOM, "unet: device allocation failed");
+  return NHMF_OK;
+}
+
+void unet_free(nhmf_ctx* c) {
+  UNet* u = c->unet;
+  if (!u) return;
+  void* ptrs[] = {u->params, u->grads, u->adam_m, u->adam_v, u->x16, u->a0, u->s0, u->d1, u->s1, u->d2, u->m2,
+                  u->u1, u->t1, u->u0, u->t0, u->g0a, u->g0b, u->g0c, u->g1a, u->g1b, u->g1c, u->g2a, u->g2b,
+                  u->y, u->partial, u->sc, u->pairs};
+  for (void* p : ptrs) cudaFree(p);
+  for (int l = 0; l < 11; ++l) {
+    cudaFree(u->L[l].wf);
+    cudaFree(u->L[l].wb);
+  }
+  delete u;
+  c->unet = nullptr;
+}
+
+void unet_refresh_weights(UNet& u, cudaStream_t s) {
+  for (int l = 0; l < 11; ++l) {
+    const UNetLayer& L = u.L[l];
+    k_layer_weights<<<(27 * 256 + 255) / 256, 256, 0, s>>>(u.params + L.woff, L.kind, L.cin, L.cout, L.wf, L.wb);
+  }
+}
+
+// Forward pass from u.x16 to u.y (FP32 planar).
+void unet_forward(UNet& u, cudaStream_t s) {
+  const float* P = u.params;
+  auto B = [&](int l) { return P + u.L[l].boff; };
+  const int M0 = u.M0, M1 = u.M1, M2 = u.M2;
+  conv(S1, u.x16, M0, u.L[L_IN].wf, B(L_IN), nullptr, nullptr, true, u.a0, nullptr, M0, s);
+  conv(S1, u.a0, M0, u.L[L_E0].wf, B(L_E0), nullptr, nullptr, true, u.s0, nullptr, M0, s);
+  conv(DOWN2, u.s0, M0, u.L[L_D1].wf, B(L_D1), nullptr, nullptr, true, u.d1, nullptr, M1, s);
+  conv(S1, u.d1, M1, u.L[L_E1].wf, B(L_E1), nullptr, nullptr, true, u.s1, nullptr, M1, s);
+  conv(DOWN2, u.s1, M1, u.L[L_D2].wf, B(L_D2), nullptr, nullptr, true, u.d2, nullptr, M2, s);
+  conv(S1, u.d2, M2, u.L[L_M2].wf, B(L_M2), nullptr, nullptr, true, u.m2, nullptr, M2, s);
+  conv(UP2, u.m2, M2, u.L[L_U1].wf, B(L_U1), u.s1, nullptr, true, u.u1, nullptr, M1, s);
+  conv(S1, u.u1, M1, u.L[L_T1].wf, B(L_T1), nullptr, nullptr, true, u.t1, nullptr, M1, s);
+  conv(UP2, u.t1, M1, u.L[L_U0].wf, B(L_U0), u.s0, nullptr, true, u.u0, nullptr, M0, s);
+  conv(S1, u.u0, M0, u.L[L_T0].wf, B(L_T0), nullptr, nullptr, true, u.t0, nullptr, M0, s);
+  conv(S1, u.t0, M0, u.L[L_OUT].wf, B(L_OUT), nullptr, nullptr, false, nullptr, u.y, M0, s);
+}
+
+// Backward pass from dy16 (in u.g0a) to u.grads (after unet_forward on the same input).
+void unet_backward(UNet& u, cudaStream_t s) {
+  const int M0 = u.M0, M1 = u.M1, M2 = u.M2;
+  __nv_bfloat16 *dy = u.g0a, *dt0 = u.g0b, *du0 = u.g0c, *ds0 = u.g0a;
+  __nv_bfloat16 *dt1 = u.g1a, *du1 = u.g1b, *ds1 = u.g1c, *dd1 = u.g1a;
+  __nv_bfloat16 *dm2 = u.g2a, *dd2 = u.g2b;
+  wgrad(u, L_OUT, S1, dy, M0, u.t0, M0, s);
+  bgrad(u, L_OUT, dy, u.N0, s);
+  conv(S1, dy, M0, u.L[L_OUT].wb, nullptr, nullptr, u.t0, false, dt0, nullptr, M0, s);
+  wgrad(u, L_T0, S1, dt0, M0, u.u0, M0, s);
+  bgrad(u, L_T0, dt0, u.N0, s);
+  conv(S1, dt0, M0, u.L[L_T0].wb, nullptr, nullptr, u.u0, false, du0, nullptr, M0, s);
+  wgrad(u, L_U0, DOWN2, u.t1, M1, du0, M0, s);  // dU[c][o] = sum t1[c] du0[o](2v'+d)
+  bgrad(u, L_U0, du0, u.N0, s);
+  conv(DOWN2, du0, M0, u.L[L_U0].wb, nullptr, nullptr, u.t1, false, dt1, nullptr, M1, s);
+  wgrad(u, L_T1, S1, dt1, M1, u.u1, M1, s);
+  bgrad(u, L_T1, dt1, u.N1, s);
+  conv(S1, dt1, M1, u.L[L_T1].wb, nullptr, nullptr, u.u1, false, du1, nullptr, M1, s);
+  wgrad(u, L_U1, DOWN2, u.m2, M2, du1, M1, s);
+  bgrad(u, L_U1, du1, u.N1, s);
+  conv(DOWN2, du1, M1, u.L[L_U1].wb, nullptr, nullptr, u.m2, false, dm2, nullptr, M2, s);
+  wgrad(u, L_M2, S1, dm2, M2, u.d2, M2, s);
+  bgrad(u, L_M2, dm2, u.N2, s);
+  conv(S1, dm2, M2, u.L[L_M2].wb, nullptr, nullptr, u.d2, false, dd2, nullptr, M2, s);
+  wgrad(u, L_D2, DOWN2, dd2, M2, u.s1, M1, s);
+  bgrad(u, L_D2, dd2, u.N2, s);
+  conv(UP2, dd2, M2, u.L[L_D2].wb, nullptr, du1, u.s1, false, ds1, nullptr, M1, s);  // + skip grad, ReLU mask
+  wgrad(u, L_E1, S1, ds1, M1, u.d1, M1, s);
+  bgrad(u, L_E1, ds1, u.N1, s);
+  conv(S1, ds1, M1, u.L[L_E1].wb, nullptr, nullptr, u.d1, false, dd1, nullptr, M1, s);
+  wgrad(u, L_D1, DOWN2, dd1, M1, u.s0, M0, s);
+  bgrad(u, L_D1, dd1, u.N1, s);
+  conv(UP2, dd1, M1, u.L[L_D1].wb, nullptr, du0, u.s0, false, ds0, nullptr, M0, s);
+  wgrad(u, L_E0, S1, ds0, M0, u.a0, M0, s);
+  bgrad(u, L_E0, ds0, u.N0, s);
+  conv(S1, ds0, M0, u.L[L_E0].wb, nullptr, nullptr, u.a0, false, dt0, nullptr, M0, s);  // da0 in dt0's buffer
+  wgrad(u, L_IN, S1, dt0, M0, u.x16, M0, s);
+  bgrad(u, L_IN, dt0, u.N0, s);
+}
+
+// x16 from an FP64 planar vector scaled to unit RMS.
+void unet_input_from(nhmf_ctx* c, const double* r, cudaStream_t s) {
+  UNet& u = *c->unet;
+  norm2(3 * u.N0, r, u.sc + 0, c->work ? c->work->partials : nullptr, s);
+  k_input<double><<<kConvBlocks, 256, 0, s>>>(r, u.N0, u.sc + 0, std::sqrt(3.0 * u.N0), u.x16);
+}
+
+void unet_input_planar32(UNet& u, const float* x, cudaStream_t s) {
+  k_input<float><<<kConvBlocks, 256, 0, s>>>(x, u.N0, nullptr, 1.0, u.x16);
+}
+
+// Loss of u.y against the FP32 planar target; writes dy16 into u.g0a; adds the loss to
+// sc[3] when accumulate is set.  Uses the solver's reduction scratch.
+void unet_loss_and_grad(nhmf_ctx* c, const float* target, bool accumulate, cudaStream_t s) {
+  UNet& u = *c->unet;
+  double* partials = c->work->partials;
+  k_loss_partials<<<kRedBlocks, kRedThreads, 0, s>>>(u.y, target, u.N0, c->prm.bc, u.M0, partials);
+  k_loss_final<<<1, 32, 0, s>>>(partials, u.sc + 1, u.sc + 2, accumulate ? u.sc + 3 : nullptr);
+  k_loss_grad<<<kConvBlocks, 256, 0, s>>>(u.y, target, u.N0, c->prm.bc, u.M0, u.sc + 2, u.g0a);
+}
+
+void unet_adam(UNet& u, float lr, cudaStream_t s) {
+  u.step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.f - std::pow(b1, (float)u.step), bc2 = 1.f - std::pow(b2, (float)u.step);
+  k_adam<<<256, 256, 0, s>>>(u.nparams, u.params, u.grads, u.adam_m, u.adam_v, lr, b1, b2, 1e-8f, bc1, bc2);
+  unet_refresh_weights(u, s);
+}
+
+// z = preconditioner(r): network on r scaled to unit RMS, output scaled back by ||r|| / sqrt(3N),
+// zero on constrained DoFs.
+void unet_precondition(nhmf_ctx* c, const double* r, double* z, cudaStream_t s) {
+  UNet& u = *c->unet;
+  unet_input_from(c, r, s);
+  unet_forward(u, s);
+  k_output<<<kConvBlocks, 256, 0, s>>>(u.y, u.N0, c->prm.bc, u.M0, u.sc + 0, 1.0 / std::sqrt(3.0 * u.N0), z);
+}
+
+nhmf_status unet_record(nhmf_ctx* c, const double* r, const double* e, cudaStream_t s) {
+  UNet& u = *c->unet;
+  if (u.npairs >= u.cap) return NHMF_OK;  // store full: later pairs are dropped
+  float* slot = u.pairs + (size_t)u.npairs * 2 * 3 * u.N0;
+  const double mul = std::sqrt(3.0 * u.N0);
+  norm2(3 * u.N0, r, u.sc + 4, c->work->partials, s);
+  k_store_scaled<<<kConvBlocks, 256, 0, s>>>(r, 3 * u.N0, u.sc + 4, mul, slot);
+  norm2(3 * u.N0, e, u.sc + 5, c->work->partials, s);
+  k_store_scaled<<<kConvBlocks, 256, 0, s>>>(e, 3 * u.N0, u.sc + 5, mul, slot + 3 * u.N0);
+  u.npairs += 1;
+  return cuda_check(c, cudaGetLastError(), "unet record");
+}
+
+namespace {
+__global__ void k_store_f32(const double* src, long long n3, float* dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = float(src[i]);
+}
+// dst = (float(xstar) - dst) * mul / ||float(xstar) - dst|| in two passes
+__global__ void k_sub_from(const double* xstar, long long n3, float* dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = float(xstar[i] - double(dst[i]));
+}
+__global__ void k_scale_f32(long long n3, const double* nrm, double mul, float* dst) {
+  const float s = float(*nrm > 0.0 ? mul / *nrm : 0.0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    dst[i] *= s;
+}
+}  // namespace
+
+// CG snapshot: input slot <- r_j normalised, target slot <- x_j (finished later).
+int unet_snapshot_begin(nhmf_ctx* c, const double* r, const double* xj, cudaStream_t s) {
+  UNet& u = *c->unet;
+  if (u.npairs >= u.cap) return -1;
+  const int slot = u.npairs++;
+  float* p = u.pairs + (size_t)slot * 2 * 3 * u.N0;
+  norm2(3 * u.N0, r, u.sc + 4, c->work->partials, s);
+  k_store_scaled<<<kConvBlocks, 256, 0, s>>>(r, 3 * u.N0, u.sc + 4, std::sqrt(3.0 * u.N0), p);
+  k_store_f32<<<kConvBlocks, 256, 0, s>>>(xj, 3 * u.N0, p + 3 * u.N0);
+  return slot;
+}
+
+// target slot <- (x* - x_j) normalised to unit RMS.
+void unet_snapshot_finish(nhmf_ctx* c, int slot, const double* xstar, cudaStream_t s) {
+  UNet& u = *c->unet;
+  float* tgt = u.pairs + (size_t)slot * 2 * 3 * u.N0 + 3 * u.N0;
+  k_sub_from<<<kConvBlocks, 256, 0, s>>>(xstar, 3 * u.N0, tgt);
+  norm2(3 * u.N0, tgt, u.sc + 5, c->work->partials, s);
+  k_scale_f32<<<kConvBlocks, 256, 0, s>>>(3 * u.N0, u.sc + 5, std::sqrt(3.0 * u.N0), tgt);
+}
+
+}  // namespace nhmf
+
+// ------------------------------------------------------------------ C ABI
+using namespace nhmf;
+
+extern "C" {
+
+nhmf_status nhmf_unet_create(nhmf_ctx* c, int pair_capacity) {
+  if (!c) return NHMF_ERR_ARG;
+  if (pair_capacity < 0) return fail(c, NHMF_ERR_ARG, "unet_create: negative capacity");
+  nhmf_status st = ensure_work(c);
+  if (st != NHMF_OK) return st;
+  st = unet_alloc(c, pair_capacity);
+  if (st != NHMF_OK) {
+    unet_free(c);
+    return st;
+  }
+  return cuda_check(c, cudaDeviceSynchronize(), "unet_create");
+}
+
+size_t nhmf_unet_num_params(const nhmf_ctx* c) { return (c && c->unet) ? (size_t)c->unet->nparams : 0; }
+
+int nhmf_unet_num_pairs(const nhmf_ctx* c) { return (c && c->unet) ? c->unet->npairs : 0; }
+
+nhmf_status nhmf_unet_set_params(nhmf_ctx* c, const float* host, size_t n) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_set_params: no network");
+  UNet& u = *c->unet;
+  if (!host || n != (size_t)u.nparams) return fail(c, NHMF_ERR_ARG, "unet_set_params: size mismatch");
+  nhmf_status st = cuda_check(c, cudaMemcpy(u.params, host, n * sizeof(float), cudaMemcpyHostToDevice), "params copy");
+  if (st != NHMF_OK) return st;
+  cudaMemset(u.adam_m, 0, n * sizeof(float));
+  cudaMemset(u.adam_v, 0, n * sizeof(float));
+  u.step = 0;
+  unet_refresh_weights(u, 0);
+  return cuda_check(c, cudaDeviceSynchronize(), "unet_set_params");
+}
+
+nhmf_status nhmf_unet_get_params(nhmf_ctx* c, float* host, size_t n) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_get_params: no network");
+  if (!host || n != (size_t)c->unet->nparams) return fail(c, NHMF_ERR_ARG, "unet_get_params: size mismatch");
+  return cuda_check(c, cudaMemcpy(host, c->unet->params, n * sizeof(float), cudaMemcpyDeviceToHost), "params read");
+}
+
+nhmf_status nhmf_unet_forward(nhmf_ctx* c, const float* x, float* y, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_forward: no network");
+  if (!x || !y) return fail(c, NHMF_ERR_ARG, "unet_forward: bad argument");
+  UNet& u = *c->unet;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unet_input_planar32(u, x, s);
+  unet_forward(u, s);
+  return cuda_check(c, cudaMemcpyAsync(y, u.y, 3 * u.N0 * sizeof(float), cudaMemcpyDeviceToDevice, s), "unet_forward");
+}
+
+nhmf_status nhmf_unet_loss_grad(nhmf_ctx* c, const float* x, const float* e, double* loss, float* grads_host,
+                                void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_loss_grad: no network");
+  if (!x || !e || !loss) return fail(c, NHMF_ERR_ARG, "unet_loss_grad: bad argument");
+  UNet& u = *c->unet;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unet_input_planar32(u, x, s);
+  unet_forward(u, s);
+  unet_loss_and_grad(c, e, false, s);
+  unet_backward(u, s);
+  double nd[2];
+  nhmf_status st = cuda_check(c, cudaMemcpyAsync(nd, u.sc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "loss read");
+  if (st == NHMF_OK && grads_host)
+    st = cuda_check(c, cudaMemcpyAsync(grads_host, u.grads, u.nparams * sizeof(float), cudaMemcpyDeviceToHost, s), "grad read");
+  if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "loss_grad sync");
+  *loss = nd[1] > 0.0 ? nd[0] / nd[1] : 0.0;
+  return st;
+}
+
+nhmf_status nhmf_unet_precondition(nhmf_ctx* c, const double* r, double* z, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_precondition: no network");
+  if (!r || !z) return fail(c, NHMF_ERR_ARG, "unet_precondition: bad argument");
+  unet_precondition(c, r, z, static_cast<cudaStream_t>(stream));
+  return cuda_check(c, cudaGetLastError(), "unet_precondition");
+}
+
+nhmf_status nhmf_unet_record_pair(nhmf_ctx* c, const double* r, const double* e, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_record_pair: no network");
+  if (!r || !e) return fail(c, NHMF_ERR_ARG, "unet_record_pair: bad argument");
+  return unet_record(c, r, e, static_cast<cudaStream_t>(stream));
+}
+
+nhmf_status nhmf_unet_train(nhmf_ctx* c, int epochs, double lr, double* loss_first, double* loss_last, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!c->unet) return fail(c, NHMF_ERR_STATE, "unet_train: no network");
+  if (epochs < 1 || !(lr > 0.0) || !loss_first || !loss_last) return fail(c, NHMF_ERR_ARG, "unet_train: bad argument");
+  UNet& u = *c->unet;
+  if (u.npairs == 0) return fail(c, NHMF_ERR_STATE, "unet_train: no recorded pairs");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t pair_stride = (size_t)2 * 3 * u.N0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    cudaMemsetAsync(u.sc + 3, 0, sizeof(double), s);
+    for (int k = 0; k < u.npairs; ++k) {
+      const float* slot = u.pairs + (size_t)k * pair_stride;
+      unet_input_planar32(u, slot, s);
+      unet_forward(u, s);
+      unet_loss_and_grad(c, slot + 3 * u.N0, true, s);
+      unet_backward(u, s);
+      unet_adam(u, (float)lr, s);
+    }
+    double acc = 0.0;
+    nhmf_status st = cuda_check(c, cudaMemcpyAsync(&acc, u.sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "train loss");
+    if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "train sync");
+    if (st != NHMF_OK) return st;
+    if (!std::isfinite(acc)) return fail(c, NHMF_ERR_NONFINITE, "unet_train: non-finite loss");
+    if (ep == 0) *loss_first = acc / u.npairs;
+    *loss_last = acc / u.npairs;
+  }
+  return NHMF_OK;
+}
+
+}  // extern "C"

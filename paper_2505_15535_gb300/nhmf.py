@@ -43,7 +43,10 @@ class nhmf_solve_opts(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
                 ("max_backtracks", ctypes.c_int), ("linear_rtol", ctypes.c_double),
                 ("linear_max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("inner_max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("inner_max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("record_pairs", ctypes.c_int), ("cg_pair_every", ctypes.c_int),
+                ("learned_jacobi_weight", ctypes.c_double), ("learned_stall_window", ctypes.c_int),
+                ("learned_stall_factor", ctypes.c_double)]
 
 
 class nhmf_solve_stats(ctypes.Structure):
@@ -80,6 +83,17 @@ _SIGS = {
     "nhmf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "nhmf_solve_opts_default": (None, [ctypes.POINTER(nhmf_solve_opts)]),
     "nhmf_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, ctypes.POINTER(nhmf_solve_stats), _P]),
+    "nhmf_unet_create": (ctypes.c_int, [_P, ctypes.c_int]),
+    "nhmf_unet_num_params": (ctypes.c_size_t, [_P]),
+    "nhmf_unet_num_pairs": (ctypes.c_int, [_P]),
+    "nhmf_unet_set_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "nhmf_unet_get_params": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "nhmf_unet_forward": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nhmf_unet_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
+    "nhmf_unet_precondition": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nhmf_unet_record_pair": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nhmf_unet_train": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), _P]),
     "nhmf_linear_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _P, _P,
                                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double), _P]),
     "nhmf_linear_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, _P,
@@ -215,6 +229,66 @@ def nhmf_linear_solve_noalloc(ctx, strategy, rtol, max_iter, b, x, stream=None):
     _check(ctx, lib().nhmf_linear_solve_noalloc(ctx, strategy, rtol, max_iter, _ptr(b), _ptr(x), ctypes.byref(it),
                                                 ctypes.byref(rel), _stream(stream)))
     return it.value, rel.value
+
+
+def _host_f32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def nhmf_unet_create(ctx, pair_capacity=0):
+    _check(ctx, lib().nhmf_unet_create(ctx, int(pair_capacity)))
+
+
+def nhmf_unet_num_params(ctx):
+    return lib().nhmf_unet_num_params(ctx)
+
+
+def nhmf_unet_num_pairs(ctx):
+    return lib().nhmf_unet_num_pairs(ctx)
+
+
+def nhmf_unet_set_params(ctx, params):
+    """params: host array-like of num_params floats (flat layout, see include/nhmf.h)."""
+    a, p = _host_f32(params)
+    _check(ctx, lib().nhmf_unet_set_params(ctx, p, a.size))
+
+
+def nhmf_unet_get_params(ctx):
+    import numpy as np
+    out = np.empty(nhmf_unet_num_params(ctx), dtype=np.float32)
+    _check(ctx, lib().nhmf_unet_get_params(ctx, out.ctypes.data_as(ctypes.c_void_p), out.size))
+    return out
+
+
+def nhmf_unet_forward(ctx, x, y, stream=None):
+    _check(ctx, lib().nhmf_unet_forward(ctx, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def nhmf_unet_loss_grad(ctx, x, e, stream=None):
+    """(loss, host FP32 gradient array)."""
+    import numpy as np
+    g = np.empty(nhmf_unet_num_params(ctx), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(ctx, lib().nhmf_unet_loss_grad(ctx, _ptr(x), _ptr(e), ctypes.byref(loss),
+                                          g.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return loss.value, g
+
+
+def nhmf_unet_precondition(ctx, r, z, stream=None):
+    _check(ctx, lib().nhmf_unet_precondition(ctx, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def nhmf_unet_record_pair(ctx, r, e, stream=None):
+    _check(ctx, lib().nhmf_unet_record_pair(ctx, _ptr(r), _ptr(e), _stream(stream)))
+
+
+def nhmf_unet_train(ctx, epochs, lr, stream=None):
+    """(mean loss of the first epoch, mean loss of the last epoch)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().nhmf_unet_train(ctx, int(epochs), float(lr), ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
 
 
 class Problem:
