@@ -27,6 +27,11 @@ Layers (C = 16 channels, ReLU r):
   y  = conv(t0; out)          C -> 3,  M0   (linear)
 Loss of one pair (x, e) with Dirichlet mask f (1 on free DoFs):
   L = ||f (y - e)||^2 / ||f e||^2.
+
+With quant=True, forward and backward round to BF16 (round to nearest even) exactly where
+the GPU kernels store BF16: the weights, the input, every activation, the loss gradient and
+every activation gradient; arithmetic stays FP64.  The ReLU decisions and their masks are
+then taken in the kernels' storage precision, which the parity tests need.
 """
 from __future__ import annotations
 
@@ -109,6 +114,18 @@ def relu(z):
     return np.maximum(z, 0.0)
 
 
+def bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _quantized(params):
+    return {k: (bf16(v) if k.endswith(".w") else v) for k, v in params.items()}
+
+
 def init_params(seed_normal, m_unused=None):
     """He-normal weights from a caller-supplied N(0,1) draw function, zero biases."""
     params = {}
@@ -123,23 +140,24 @@ def init_params(seed_normal, m_unused=None):
     return params
 
 
-def forward(params, x):
+def forward(params, x, quant=False):
     """y and the cache of activations for backward."""
-    P = params
+    P = _quantized(params) if quant else params
+    q = bf16 if quant else (lambda v: v)
     M0 = x.shape[1]
     M1 = (M0 - 1) // 2 + 1
     a = {}
-    a["x"] = x
-    a["a0"] = relu(conv(x, P["in.w"], P["in.b"]))
-    a["s0"] = relu(conv(a["a0"], P["e0.w"], P["e0.b"]))
-    a["d1"] = relu(conv(a["s0"], P["d1.w"], P["d1.b"], 2))
-    a["s1"] = relu(conv(a["d1"], P["e1.w"], P["e1.b"]))
-    a["d2"] = relu(conv(a["s1"], P["d2.w"], P["d2.b"], 2))
-    a["m2"] = relu(conv(a["d2"], P["m2.w"], P["m2.b"]))
-    a["u1"] = relu(up(a["m2"], P["u1.w"], P["u1.b"], M1) + a["s1"])
-    a["t1"] = relu(conv(a["u1"], P["t1.w"], P["t1.b"]))
-    a["u0"] = relu(up(a["t1"], P["u0.w"], P["u0.b"], M0) + a["s0"])
-    a["t0"] = relu(conv(a["u0"], P["t0.w"], P["t0.b"]))
+    a["x"] = q(x)
+    a["a0"] = q(relu(conv(a["x"], P["in.w"], P["in.b"])))
+    a["s0"] = q(relu(conv(a["a0"], P["e0.w"], P["e0.b"])))
+    a["d1"] = q(relu(conv(a["s0"], P["d1.w"], P["d1.b"], 2)))
+    a["s1"] = q(relu(conv(a["d1"], P["e1.w"], P["e1.b"])))
+    a["d2"] = q(relu(conv(a["s1"], P["d2.w"], P["d2.b"], 2)))
+    a["m2"] = q(relu(conv(a["d2"], P["m2.w"], P["m2.b"])))
+    a["u1"] = q(relu(up(a["m2"], P["u1.w"], P["u1.b"], M1) + a["s1"]))
+    a["t1"] = q(relu(conv(a["u1"], P["t1.w"], P["t1.b"])))
+    a["u0"] = q(relu(up(a["t1"], P["u0.w"], P["u0.b"], M0) + a["s0"]))
+    a["t0"] = q(relu(conv(a["u0"], P["t0.w"], P["t0.b"])))
     y = conv(a["t0"], P["out.w"], P["out.b"])
     return y, a
 
@@ -149,34 +167,35 @@ def loss(y, e, free):
     return float(np.sum(d * d) / np.sum((free * e) ** 2))
 
 
-def backward(params, a, y, e, free):
+def backward(params, a, y, e, free, quant=False):
     """Gradients of the loss with respect to every parameter (dict like params)."""
-    P = params
+    P = _quantized(params) if quant else params
+    q = bf16 if quant else (lambda v: v)
     g = {}
     den = np.sum((free * e) ** 2)
-    dy = 2.0 * free * free * (y - e) / den
+    dy = q(2.0 * free * free * (y - e) / den)
     dt0, g["out.w"], g["out.b"] = conv_backward(a["t0"], P["out.w"], dy)
-    dt0 = dt0 * (a["t0"] > 0)
+    dt0 = q(dt0 * (a["t0"] > 0))
     du0, g["t0.w"], g["t0.b"] = conv_backward(a["u0"], P["t0.w"], dt0)
-    du0 = du0 * (a["u0"] > 0)                  # through the ReLU of u0 (sum of up and skip)
+    du0 = q(du0 * (a["u0"] > 0))               # through the ReLU of u0 (sum of up and skip)
     ds0 = du0.copy()
     dt1, g["u0.w"], g["u0.b"] = up_backward(a["t1"], P["u0.w"], du0)
-    dt1 = dt1 * (a["t1"] > 0)
+    dt1 = q(dt1 * (a["t1"] > 0))
     du1, g["t1.w"], g["t1.b"] = conv_backward(a["u1"], P["t1.w"], dt1)
-    du1 = du1 * (a["u1"] > 0)
+    du1 = q(du1 * (a["u1"] > 0))
     ds1 = du1.copy()
     dm2, g["u1.w"], g["u1.b"] = up_backward(a["m2"], P["u1.w"], du1)
-    dm2 = dm2 * (a["m2"] > 0)
+    dm2 = q(dm2 * (a["m2"] > 0))
     dd2, g["m2.w"], g["m2.b"] = conv_backward(a["d2"], P["m2.w"], dm2)
-    dd2 = dd2 * (a["d2"] > 0)
+    dd2 = q(dd2 * (a["d2"] > 0))
     ds1b, g["d2.w"], g["d2.b"] = conv_backward(a["s1"], P["d2.w"], dd2, 2)
-    ds1 = (ds1 + ds1b) * (a["s1"] > 0)
+    ds1 = q((ds1 + ds1b) * (a["s1"] > 0))
     dd1, g["e1.w"], g["e1.b"] = conv_backward(a["d1"], P["e1.w"], ds1)
-    dd1 = dd1 * (a["d1"] > 0)
+    dd1 = q(dd1 * (a["d1"] > 0))
     ds0b, g["d1.w"], g["d1.b"] = conv_backward(a["s0"], P["d1.w"], dd1, 2)
-    ds0 = (ds0 + ds0b) * (a["s0"] > 0)
+    ds0 = q((ds0 + ds0b) * (a["s0"] > 0))
     da0, g["e0.w"], g["e0.b"] = conv_backward(a["a0"], P["e0.w"], ds0)
-    da0 = da0 * (a["a0"] > 0)
+    da0 = q(da0 * (a["a0"] > 0))
     _, g["in.w"], g["in.b"] = conv_backward(a["x"], P["in.w"], da0)
     return g
 

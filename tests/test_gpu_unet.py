@@ -1,8 +1,10 @@
-"""The GPU U-Net against the FP64 oracle network: forward output, loss and parameter
-gradients on the same weights and inputs.  The GPU runs BF16 weights and activations with
-FP32 accumulation: with unit roundoff u = 2^-8 per stored value and about 11 layers forward
-(22 with backward), relative errors of order sqrt(layers) * u are expected, so the bars are
-2.5e-2 (forward, loss) and 6e-2 (gradients, per layer tensor)."""
+"""The GPU U-Net against the oracle network: forward output, loss and parameter gradients
+on the same weights and inputs.  The GPU stores weights, activations and activation
+gradients in BF16 and accumulates in FP32; the oracle (quant=True) rounds to BF16 at the same
+places and computes in FP64, so both take the ReLU decisions in the same precision.  What
+remains is FP32 versus FP64 accumulation (about 1e-7 relative), which now and then moves a
+stored value across a BF16 rounding boundary (one BF16 ulp, 2^-8); the bars are 2e-3 on the
+forward output and loss and 1e-2 on each gradient tensor."""
 import numpy as np
 import pytest
 
@@ -62,16 +64,16 @@ def test_forward_loss_and_gradients_match_oracle(nhmf, n_el, p, bc):
     nhmf.nhmf_unet_forward(prob.ctx, xt, y)
     xo = x.astype(np.float64).reshape(3, M, M, M)
     eo = e.astype(np.float64).reshape(3, M, M, M)
-    yo, acts = ounet.forward(params, xo)
-    assert rel_l2(host(y), yo.reshape(-1)) <= 2.5e-2
+    yo, acts = ounet.forward(params, xo, quant=True)
+    assert rel_l2(host(y), yo.reshape(-1)) <= 2e-3
     free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
     loss, g = nhmf.nhmf_unet_loss_grad(prob.ctx, xt, et)
     lo = ounet.loss(yo, eo, free)
-    assert abs(loss - lo) <= 2.5e-2 * lo
-    go = ounet.backward(params, acts, yo, eo, free)
+    assert abs(loss - lo) <= 2e-3 * lo
+    go = ounet.backward(params, acts, yo, eo, free, quant=True)
     gg = unflat(g.astype(np.float64))
-    for k in go:
-        assert rel_l2(gg[k].reshape(-1), go[k].reshape(-1)) <= 6e-2, (k, rel_l2(gg[k].reshape(-1), go[k].reshape(-1)))
+    errs = {k: rel_l2(gg[k].reshape(-1), go[k].reshape(-1)) for k in go}
+    assert max(errs.values()) <= 1e-2, errs
 
 
 def test_adam_step_matches_oracle(nhmf):
@@ -92,9 +94,9 @@ def test_adam_step_matches_oracle(nhmf):
     # oracle: the same pair normalised to unit RMS, one Adam step from the same weights
     xo = (r * np.sqrt(r.size) / np.linalg.norm(r)).reshape(3, M, M, M)
     eo = (e * np.sqrt(e.size) / np.linalg.norm(e)).reshape(3, M, M, M)
-    yo, acts = ounet.forward(params, xo)
-    assert abs(l0 - ounet.loss(yo, eo, free.reshape(3, M, M, M).astype(float))) <= 2.5e-2 * l0
-    go = ounet.backward(params, acts, yo, eo, free.reshape(3, M, M, M).astype(float))
+    yo, acts = ounet.forward(params, xo, quant=True)
+    assert abs(l0 - ounet.loss(yo, eo, free.reshape(3, M, M, M).astype(float))) <= 2e-3 * l0
+    go = ounet.backward(params, acts, yo, eo, free.reshape(3, M, M, M).astype(float), quant=True)
     st = {}
     p2 = {k: v.copy() for k, v in params.items()}
     ounet.adam_step(p2, go, st, lr=1e-3)

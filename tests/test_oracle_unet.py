@@ -119,3 +119,18 @@ def test_adam_matches_closed_form_first_step():
     unet.adam_step(p, g, st, lr=0.1)
     # first Adam step moves each weight by lr * sign(g) (up to eps)
     assert np.allclose(p["w"], [1.0 - 0.1, -2.0 + 0.1], atol=1e-7)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([RNG.standard_normal(10000) * 10.0 ** RNG.integers(-6, 6, 10000),
+                        [0.0, -0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8)]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(unet.bf16(x), ref)
+
+
+def test_quantized_network_stays_close_to_exact():
+    params, x, e, free = small_problem()
+    y, _ = unet.forward(params, x)
+    yq, _ = unet.forward(params, x, quant=True)
+    assert np.linalg.norm(yq - y) <= 5e-2 * np.linalg.norm(y)
