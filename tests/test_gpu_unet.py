@@ -1,10 +1,17 @@
-"""The GPU U-Net against the oracle network: forward output, loss and parameter gradients
-on the same weights and inputs.  The GPU stores weights, activations and activation
-gradients in BF16 and accumulates in FP32; the oracle (quant=True) rounds to BF16 at the same
-places and computes in FP64, so both take the ReLU decisions in the same precision.  What
-remains is FP32 versus FP64 accumulation (about 1e-7 relative), which now and then moves a
-stored value across a BF16 rounding boundary (one BF16 ulp, 2^-8); the bars are 2e-3 on the
-forward output and loss and 1e-2 on each gradient tensor."""
+"""The GPU U-Net against the oracle network (forward output, loss, parameter gradients,
+Adam, training).
+
+Two kinds of parity:
+* exact: sparse ternary weights (density 0.006, values -1/0/1, biases 0/1) and inputs in
+  {-1, 0, 1} keep every activation, activation gradient and parameter gradient a small
+  dyadic number, exactly representable in BF16 and summed exactly in FP32; the GPU must
+  then reproduce the oracle bit for bit (this pins every gather, stride and transposition);
+* rounded: He-initialised weights and normal inputs.  The GPU stores weights, activations
+  and activation gradients in BF16; the oracle (quant=True) rounds at the same places in
+  FP64.  One-ulp rounding differences (2^-8) cascade through the 11 layers, so two valid
+  BF16 evaluations differ by about sqrt(11) * 2^-9 ~ 2e-3 to 3e-3 relative (each is about
+  7.5e-3 from the exact FP64 network); the bars are 1e-2 on the output and loss and 8e-2 on
+  each gradient tensor (the coarsest grids sum over 125 to 729 voxels only)."""
 import numpy as np
 import pytest
 
@@ -41,76 +48,105 @@ def he_params(seed=5000, bias_scale=0.05):
     return p
 
 
+def ternary_params(seed=7000, density=0.006):
+    p = {}
+    for i, (name, kind, cin, cout) in enumerate(ounet.LAYERS):
+        shape = ounet.weight_shape(kind, cin, cout)
+        u = inp.uniform01(seed + i, int(np.prod(shape)))
+        p[name + ".w"] = np.where(u < density / 2, -1.0, np.where(u < density, 1.0, 0.0)).reshape(shape)
+        p[name + ".b"] = np.minimum(np.floor(inp.uniform01(seed + 50 + i, cout) * 3.0), 1.0)
+    return p
+
+
 @pytest.fixture(scope="module")
 def nhmf():
     return lib_or_fail()
 
 
-@pytest.mark.parametrize("n_el,p,bc", [(4, 2, 2), (8, 2, 1), (4, 4, 0)])
-def test_forward_loss_and_gradients_match_oracle(nhmf, n_el, p, bc):
+def run_gpu(nhmf, n_el, p, bc, params, x, e):
     M = p * n_el + 1
     prob = nhmf.Problem(n_el, p, 1.0, 1.5, bc)
     nhmf.nhmf_unet_create(prob.ctx, 0)
-    params = he_params()
     flat = flat_params(params)
     assert flat.size == nhmf.nhmf_unet_num_params(prob.ctx)
     nhmf.nhmf_unet_set_params(prob.ctx, flat)
     assert np.array_equal(nhmf.nhmf_unet_get_params(prob.ctx), flat.astype(np.float32))
-    # oracle weights are the FP32 master weights rounded as the GPU stores them (BF16)
-    x = inp.normal(11, 3 * M ** 3).astype(np.float32)
-    e = inp.normal(12, 3 * M ** 3).astype(np.float32)
-    xt, et = cuda(x), cuda(e)
+    xt, et = cuda(x.astype(np.float32)), cuda(e.astype(np.float32))
     y = cuda(np.zeros(3 * M ** 3, dtype=np.float32))
     nhmf.nhmf_unet_forward(prob.ctx, xt, y)
-    xo = x.astype(np.float64).reshape(3, M, M, M)
-    eo = e.astype(np.float64).reshape(3, M, M, M)
-    yo, acts = ounet.forward(params, xo, quant=True)
-    assert rel_l2(host(y), yo.reshape(-1)) <= 2e-3
-    free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
     loss, g = nhmf.nhmf_unet_loss_grad(prob.ctx, xt, et)
-    lo = ounet.loss(yo, eo, free)
-    assert abs(loss - lo) <= 2e-3 * lo
+    return host(y), loss, unflat(g.astype(np.float64))
+
+
+@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0)])
+def test_exact_arithmetic_bit_parity(nhmf, n_el, p, bc):
+    M = p * n_el + 1
+    params = ternary_params()
+    x = np.floor(inp.uniform01(123, 3 * M ** 3) * 3.0 - 1.0)
+    e = np.zeros(3 * M ** 3)
+    e[M ** 3 + (M // 2) * (1 + M + M * M)] = 4.0          # ||f e||^2 = 16: dy is dyadic
+    y, loss, g = run_gpu(nhmf, n_el, p, bc, params, x, e)
+    xo, eo = x.reshape(3, M, M, M), e.reshape(3, M, M, M)
+    free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
+    yo, acts = ounet.forward(params, xo, quant=True)
+    assert np.array_equal(y, yo.reshape(-1))
+    assert loss == ounet.loss(yo, eo, free)
     go = ounet.backward(params, acts, yo, eo, free, quant=True)
-    gg = unflat(g.astype(np.float64))
-    errs = {k: rel_l2(gg[k].reshape(-1), go[k].reshape(-1)) for k in go}
-    assert max(errs.values()) <= 1e-2, errs
+    for k in go:
+        assert np.array_equal(g[k], go[k]), k
+    assert sum(np.count_nonzero(go[k]) for k in go if k.endswith(".w")) > 5000
+
+
+@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0)])
+def test_rounded_parity(nhmf, n_el, p, bc):
+    M = p * n_el + 1
+    params = he_params()
+    x = inp.normal(11, 3 * M ** 3).astype(np.float32).astype(np.float64)
+    e = inp.normal(12, 3 * M ** 3).astype(np.float32).astype(np.float64)
+    y, loss, g = run_gpu(nhmf, n_el, p, bc, params, x, e)
+    xo, eo = x.reshape(3, M, M, M), e.reshape(3, M, M, M)
+    yo, acts = ounet.forward(params, xo, quant=True)
+    assert np.mean(acts["t0"] > 0) > 0.2                    # the network is alive
+    assert rel_l2(y, yo.reshape(-1)) <= 1e-2
+    free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
+    lo = ounet.loss(yo, eo, free)
+    assert abs(loss - lo) <= 1e-2 * lo
+    go = ounet.backward(params, acts, yo, eo, free, quant=True)
+    errs = {k: rel_l2(g[k].reshape(-1), go[k].reshape(-1)) for k in go}
+    assert max(errs.values()) <= 8e-2, errs
 
 
 def test_adam_step_matches_oracle(nhmf):
-    n_el, p, bc = 4, 2, 2
+    n_el, p, bc = 8, 2, 2
     M = p * n_el + 1
     prob = nhmf.Problem(n_el, p, 1.0, 1.5, bc)
     nhmf.nhmf_unet_create(prob.ctx, 4)
     params = he_params()
     nhmf.nhmf_unet_set_params(prob.ctx, flat_params(params))
-    r = inp.normal(21, 3 * M ** 3)
-    e = inp.normal(22, 3 * M ** 3)
     free = ~Mesh(n_el, p).constrained(bc)
-    r[~free] = 0.0
-    e[~free] = 0.0
+    r = np.where(free, inp.normal(21, 3 * M ** 3), 0.0)
+    e = np.where(free, inp.normal(22, 3 * M ** 3), 0.0)
     nhmf.nhmf_unet_record_pair(prob.ctx, cuda(r), cuda(e))
     assert nhmf.nhmf_unet_num_pairs(prob.ctx) == 1
-    l0, l1 = nhmf.nhmf_unet_train(prob.ctx, 1, 1e-3)
-    # oracle: the same pair normalised to unit RMS, one Adam step from the same weights
+    lr = 1e-3
+    l0, _ = nhmf.nhmf_unet_train(prob.ctx, 1, lr)
     xo = (r * np.sqrt(r.size) / np.linalg.norm(r)).reshape(3, M, M, M)
     eo = (e * np.sqrt(e.size) / np.linalg.norm(e)).reshape(3, M, M, M)
+    fo = free.reshape(3, M, M, M).astype(float)
     yo, acts = ounet.forward(params, xo, quant=True)
-    assert abs(l0 - ounet.loss(yo, eo, free.reshape(3, M, M, M).astype(float))) <= 2e-3 * l0
-    go = ounet.backward(params, acts, yo, eo, free.reshape(3, M, M, M).astype(float), quant=True)
-    st = {}
+    assert abs(l0 - ounet.loss(yo, eo, fo)) <= 1e-2 * l0
+    go = ounet.backward(params, acts, yo, eo, fo, quant=True)
     p2 = {k: v.copy() for k, v in params.items()}
-    ounet.adam_step(p2, go, st, lr=1e-3)
+    ounet.adam_step(p2, go, {}, lr=lr)
     new = unflat(nhmf.nhmf_unet_get_params(prob.ctx).astype(np.float64))
-    # the first Adam step moves each weight by about lr * sign(g): compare the step direction
-    for k in ("in.w", "e0.w", "m2.w", "out.w"):
-        d_gpu = new[k] - params[k]
-        d_ora = p2[k] - params[k]
-        agree = np.mean(np.sign(d_gpu) == np.sign(d_ora))
-        assert agree >= 0.9, (k, agree)
+    for k in go:
+        big = np.abs(go[k]) > 0.2 * np.abs(go[k]).max()      # entries whose step is lr * sign(g)
+        d_gpu = (new[k] - params[k])[big]
+        d_ora = (p2[k] - params[k])[big]
+        assert np.mean(np.abs(d_gpu - d_ora) <= 1e-2 * lr) >= 0.97, k
 
 
 def test_training_reduces_loss_and_learned_solve_converges(nhmf):
-    import torch
     n_el, p, S, comp = 4, 2, 4, 0.08
     prob = nhmf.Problem(n_el, p, 1.0, 1.5, 2)
     nhmf.nhmf_unet_create(prob.ctx, 64)
