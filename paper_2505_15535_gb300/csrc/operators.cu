@@ -138,9 +138,16 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       bad |= !(Jm1 > T(-1));
     } else {
       if (t / n3 < nvalid) {
+        if (sizeof(T) == 8) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Fi[k] = cache[k * a.nq + cbase + t];
-        lnJ = cache[9 * a.nq + cbase + t];
+          for (int k = 0; k < 9; ++k) Fi[k] = cache[k * a.nq + cbase + t];
+          lnJ = cache[9 * a.nq + cbase + t];
+        } else {
+          const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Fi[k] = cache[(k * n3 + q) * E + slot];
+          lnJ = cache[(9 * n3 + q) * E + slot];
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Fi[k] = (k % 4 == 0) ? T(1) : T(0);
@@ -157,6 +164,221 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
   __syncthreads();
   from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
   scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<T*>(a.v));
+}
+
+// ------------------------------------------------------------------ FP32 register kernel
+// One thread per element: the element's three components (3 (p+1)^3 values), their values at
+// the Gauss points and the transposed-derivative accumulators stay in registers; every 1D pass
+// is fully unrolled, so its coefficients are compile-time-indexed kernel parameters (constant
+// bank operands of the FMAs) and no shared memory is touched.  For p <= 2.
+template <int P, int STRAT>
+__global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
+  constexpr int n = P + 1, n3 = n * n * n;
+  const long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (ec >= a.col.count) return;
+  const Colour& col = a.col;
+  const int ix = int(ec % col.nx), iy = int((ec / col.nx) % col.ny), iz = int(ec / ((long long)col.nx * col.ny));
+  const int gi0 = P * (col.cx + 2 * ix), gj0 = P * (col.cy + 2 * iy), gk0 = P * (col.cz + 2 * iz);
+  const long long M = a.M;
+  const long long slot = col.slot0 + ec, E = a.nq / n3;
+  const float* __restrict__ du = static_cast<const float*>(a.du);
+  float* __restrict__ v = static_cast<float*>(a.v);
+  auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
+  auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
+
+  // sum-factorised interpolation of three components to the points, in place
+  auto to_points = [&](float (&f)[3][n3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          float t[n];
+#pragma unroll
+          for (int r = 0; r < n; ++r) {
+            float s = a.Bf[r * n] * f[c][idx(0, j, k)];
+#pragma unroll
+            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(m, j, k)], s);
+            t[r] = s;
+          }
+#pragma unroll
+          for (int r = 0; r < n; ++r) f[c][idx(r, j, k)] = t[r];
+        }
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          float t[n];
+#pragma unroll
+          for (int r = 0; r < n; ++r) {
+            float s = a.Bf[r * n] * f[c][idx(i, 0, k)];
+#pragma unroll
+            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(i, m, k)], s);
+            t[r] = s;
+          }
+#pragma unroll
+          for (int r = 0; r < n; ++r) f[c][idx(i, r, k)] = t[r];
+        }
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          float t[n];
+#pragma unroll
+          for (int r = 0; r < n; ++r) {
+            float s = a.Bf[r * n] * f[c][idx(i, j, 0)];
+#pragma unroll
+            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(i, j, m)], s);
+            t[r] = s;
+          }
+#pragma unroll
+          for (int r = 0; r < n; ++r) f[c][idx(i, j, r)] = t[r];
+        }
+    }
+  };
+  auto grad_at = [&](const float (&f)[3][n3], int qx, int qy, int qz, float g[9]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float gx = a.Dcf[qx * n] * f[c][idx(0, qy, qz)];
+      float gy = a.Dcf[qy * n] * f[c][idx(qx, 0, qz)];
+      float gz = a.Dcf[qz * n] * f[c][idx(qx, qy, 0)];
+#pragma unroll
+      for (int m = 1; m < n; ++m) {
+        gx = fmaf(a.Dcf[qx * n + m], f[c][idx(m, qy, qz)], gx);
+        gy = fmaf(a.Dcf[qy * n + m], f[c][idx(qx, m, qz)], gy);
+        gz = fmaf(a.Dcf[qz * n + m], f[c][idx(qx, qy, m)], gz);
+      }
+      g[3 * c + 0] = gx;
+      g[3 * c + 1] = gy;
+      g[3 * c + 2] = gz;
+    }
+  };
+
+  float qv[3][n3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const bool fixed = is_constrained(a.bc, c, gi0 + i, gk0 + k, a.M);
+          qv[c][idx(i, j, k)] = fixed ? 0.f : du[c * a.M3 + node(i, j, k)];
+        }
+  to_points(qv);
+  float ub[STRAT == NHMF_ON_THE_FLY ? 3 : 1][STRAT == NHMF_ON_THE_FLY ? n3 : 1];
+  if constexpr (STRAT == NHMF_ON_THE_FLY) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+#pragma unroll
+          for (int i = 0; i < n; ++i) ub[c][idx(i, j, k)] = a.u32[c * a.M3 + node(i, j, k)];
+    to_points(ub);
+  }
+  float acc[3][n3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < n3; ++q) acc[c][q] = 0.f;
+  const float mu = float(a.mu), lam = float(a.lam), h = float(a.h), invh = float(1.0 / a.h);
+  const float* __restrict__ cache = static_cast<const float*>(a.cache);
+  bool bad = false;
+#pragma unroll
+  for (int qz = 0; qz < n; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < n; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < n; ++qx) {
+        const int q = idx(qx, qy, qz);
+        float Fi[9], lnJ;
+        if constexpr (STRAT == NHMF_ON_THE_FLY) {
+          float H[9];
+          grad_at(ub, qx, qy, qz, H);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) H[k] *= invh;
+          const float Jm1 = kinematics(H, Fi, lnJ);
+          bad |= !(Jm1 > -1.f);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Fi[k] = __ldg(cache + (k * n3 + q) * E + slot);
+          lnJ = __ldg(cache + (9 * n3 + q) * E + slot);
+        }
+        float dH[9], g[9];
+        grad_at(qv, qx, qy, qz, dH);
+        linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
+        // transposed collocation derivative: acc[c][point on the line through q] += Dc[q][m] g
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            acc[c][idx(m, qy, qz)] = fmaf(a.Dcf[qx * n + m], g[3 * c + 0], acc[c][idx(m, qy, qz)]);
+            acc[c][idx(qx, m, qz)] = fmaf(a.Dcf[qy * n + m], g[3 * c + 1], acc[c][idx(qx, m, qz)]);
+            acc[c][idx(qx, qy, m)] = fmaf(a.Dcf[qz * n + m], g[3 * c + 2], acc[c][idx(qx, qy, m)]);
+          }
+      }
+  if (bad) atomicOr(a.status, kStatusNonPosJ);
+  // transposed interpolation back to the nodes: out[i] = sum_q B[q][i] acc[q] per direction
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        float t[n];
+#pragma unroll
+        for (int r = 0; r < n; ++r) {
+          float s = a.Bf[r] * acc[c][idx(0, j, k)];
+#pragma unroll
+          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(m, j, k)], s);
+          t[r] = s;
+        }
+#pragma unroll
+        for (int r = 0; r < n; ++r) acc[c][idx(r, j, k)] = t[r];
+      }
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        float t[n];
+#pragma unroll
+        for (int r = 0; r < n; ++r) {
+          float s = a.Bf[r] * acc[c][idx(i, 0, k)];
+#pragma unroll
+          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(i, m, k)], s);
+          t[r] = s;
+        }
+#pragma unroll
+        for (int r = 0; r < n; ++r) acc[c][idx(i, r, k)] = t[r];
+      }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        float t[n];
+#pragma unroll
+        for (int r = 0; r < n; ++r) {
+          float s = a.Bf[r] * acc[c][idx(i, j, 0)];
+#pragma unroll
+          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(i, j, m)], s);
+          t[r] = s;
+        }
+#pragma unroll
+        for (int r = 0; r < n; ++r) acc[c][idx(i, j, r)] = t[r];
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += acc[c][idx(i, j, k)];
 }
 
 // ------------------------------------------------------------------ point cache
@@ -194,9 +416,11 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       a.cache64_out[9 * a.nq + cbase + t] = lnJ;
     }
     if (a.cache32_out) {
+      // FP32 cache layout [10][n^3][E]: consecutive elements of a colour are contiguous
+      const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a.cache32_out[k * a.nq + cbase + t] = float(Fi[k]);
-      a.cache32_out[9 * a.nq + cbase + t] = float(lnJ);
+      for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + slot] = float(Fi[k]);
+      a.cache32_out[(9 * n3 + q) * E + slot] = float(lnJ);
     }
   }
   if (bad) atomicOr(a.status, kStatusNonPosJ);
@@ -369,7 +593,10 @@ OpArgs base_args(nhmf_ctx* c) {
       a.B[q * n + i] = c->tab.B[q][i];
       a.Dc[q * n + i] = c->tab.Dc[q][i];
       a.D[q * n + i] = c->tab.D[q][i];
+      a.Bf[q * n + i] = float(c->tab.B[q][i]);
+      a.Dcf[q * n + i] = float(c->tab.Dc[q][i]);
     }
+    a.wf[q] = float(c->tab.w[q]);
   }
   a.status = c->status;
   return a;
@@ -430,7 +657,11 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   const size_t smem = slots * sizeof(T);
   if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(T) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "apply memset");
-  nhmf_status st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
+  nhmf_status st;
+  if constexpr (sizeof(T) == 4 && P <= 2)
+    st = run_colours(c, k_apply_reg<P, STRAT>, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
+  else
+    st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
   if (st != NHMF_OK || raw) return st;
   return fix_rows<T>(c, static_cast<const T*>(du), static_cast<T*>(v), 0, T(0), s);
 }

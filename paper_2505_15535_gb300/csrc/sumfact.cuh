@@ -33,6 +33,7 @@ struct OpArgs {
   double h, mu, lam;
   Colour col;
   double B[kMaxN * kMaxN], Dc[kMaxN * kMaxN], D[kMaxN * kMaxN], w[kMaxN];
+  float Bf[kMaxN * kMaxN], Dcf[kMaxN * kMaxN], wf[kMaxN];  // FP32 copies (register kernels)
   const double* u64;
   const float* u32;
   const void* du;
