@@ -84,7 +84,8 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * `cache_mask`, builds the per-quadrature-point cache of the cached strategy (Section 3.2
  * "partial assembly"): F^-1 (9 values) and ln J (1 value) per point, computed in FP64 and
  * stored in FP64 (NHMF_CACHE_FP64) and/or FP32 (NHMF_CACHE_FP32); 10*E*(p+1)^3 values
- * each, layout [10][E*(p+1)^3] with elements in colour-major order.  Synchronises and
+ * each, layout [10][E*(p+1)^3] with elements in colour-major order (the FP32 cache of p <= 2
+ * is [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
  * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
 nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
 
@@ -120,9 +121,14 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *                          (the plain baseline);
  *   NHMF_SOLVER_MIXED_FCG  FP64 flexible CG whose preconditioner is an FP32 Jacobi-CG on the
  *                          FP32 apply (FP64 residuals, dot products and updates outside);
- *   NHMF_SOLVER_LEARNED_FCG FP64 flexible CG preconditioned by the trained U-Net, falling
- *                          back to Jacobi-CG from the current iterate on stagnation. */
-enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2 };
+ *   NHMF_SOLVER_LEARNED_FCG FP64 multi-preconditioned CG with two search directions per
+ *                          iteration, D^-1 r and the trained U-Net's N(r), combined by a 2x2
+ *                          Galerkin step and A-orthogonalised against the previous pair; falls
+ *                          back to Jacobi-CG from the current iterate on stagnation;
+ *   NHMF_SOLVER_MIXED_LEARNED the same with the FP32 inner Jacobi-CG of MIXED_FCG in place of
+ *                          D^-1 r. */
+enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2,
+       NHMF_SOLVER_MIXED_LEARNED = 3 };
 #define NHMF_MAX_STEPS 64
 
 typedef struct {
@@ -143,10 +149,12 @@ typedef struct {
   int record_pairs;     /* JACOBI_CG with a U-Net: store training pairs (Newton (b, du) and CG
                            (r_j, x* - x_j)) in the network's pair store, default 0 */
   int cg_pair_every;    /* CG pairs at iterations j = k, 4k, 16k (k = this), default 8 */
-  double learned_jacobi_weight; /* LEARNED_FCG: z = N(r) + w D^-1 r, default 0 */
   int learned_stall_window;     /* LEARNED_FCG: fall back to Jacobi-CG when the residual */
   double learned_stall_factor;  /* drops by less than this factor over this many iterations
                                    (defaults 10 and 0.9), or after linear_max_iter/4 iterations */
+  int synthetic_pairs;  /* with record_pairs: per Newton iterate, also store this many pairs
+                           (K(u) e, e) for smooth random fields e, default 0 */
+  unsigned long long seed;      /* counter-based generator seed of those fields, default 1 */
 } nhmf_solve_opts;
 
 typedef struct {

@@ -50,7 +50,7 @@ struct SolverWork {
   long long n = 0;
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *qprev = nullptr, *x = nullptr;
   double *b = nullptr, *R = nullptr, *d = nullptr, *t = nullptr, *du = nullptr, *utry = nullptr;
-  double *diag = nullptr, *dinv = nullptr;
+  double *diag = nullptr, *dinv = nullptr, *b2 = nullptr, *x2 = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
   double* sc = nullptr;        // device scalars
   double* partials = nullptr;  // reduction scratch
@@ -95,6 +95,7 @@ void unet_loss_and_grad(nhmf_ctx* c, const float* target, bool accumulate, cudaS
 void unet_adam(UNet& u, float lr, cudaStream_t s);
 void unet_precondition(nhmf_ctx* c, const double* r, double* z, cudaStream_t s);
 nhmf_status unet_record(nhmf_ctx* c, const double* r, const double* e, cudaStream_t s);
+void unet_smooth_field(nhmf_ctx* c, double* e, unsigned long long seed, cudaStream_t s);
 int unet_snapshot_begin(nhmf_ctx* c, const double* r, const double* xj, cudaStream_t s);
 void unet_snapshot_finish(nhmf_ctx* c, int slot, const double* xstar, cudaStream_t s);
 

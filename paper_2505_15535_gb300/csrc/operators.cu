@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       bad |= !(Jm1 > T(-1));
     } else {
       if (t / n3 < nvalid) {
-        if (sizeof(T) == 8) {
+        if (sizeof(T) == 8 || P > 2) {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Fi[k] = cache[k * a.nq + cbase + t];
           lnJ = cache[9 * a.nq + cbase + t];
@@ -416,11 +416,19 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       a.cache64_out[9 * a.nq + cbase + t] = lnJ;
     }
     if (a.cache32_out) {
-      // FP32 cache layout [10][n^3][E]: consecutive elements of a colour are contiguous
-      const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
+      if (P <= 2) {
+        // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
+        // elements of a colour are contiguous
+        const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + slot] = float(Fi[k]);
-      a.cache32_out[(9 * n3 + q) * E + slot] = float(lnJ);
+        for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + slot] = float(Fi[k]);
+        a.cache32_out[(9 * n3 + q) * E + slot] = float(lnJ);
+      } else {
+        // layout [10][E n^3] (same as FP64) for the shared-memory kernel
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a.cache32_out[k * a.nq + cbase + t] = float(Fi[k]);
+        a.cache32_out[9 * a.nq + cbase + t] = float(lnJ);
+      }
     }
   }
   if (bad) atomicOr(a.status, kStatusNonPosJ);

@@ -57,7 +57,8 @@ nhmf_status ensure_work(nhmf_ctx* c) {
   c->work = new SolverWork();
   SolverWork& w = *c->work;
   w.n = n;
-  double** d64[] = {&w.r, &w.z, &w.p, &w.q, &w.qprev, &w.x, &w.b, &w.R, &w.d, &w.t, &w.du, &w.utry, &w.diag, &w.dinv};
+  double** d64[] = {&w.r, &w.z, &w.p, &w.q, &w.qprev, &w.x, &w.b, &w.R, &w.d, &w.t, &w.du, &w.utry, &w.diag, &w.dinv,
+                    &w.b2, &w.x2};
   for (double** p : d64)
     if (cudaMalloc(p, n * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "solver work alloc");
   float** d32[] = {&w.r32, &w.z32, &w.p32, &w.q32, &w.x32, &w.b32, &w.dinv32};
@@ -201,6 +202,137 @@ nhmf_status update_diagonal(Ctx& x) {
   return cuda_check(x.c, cudaGetLastError(), "diagonal inverse");
 }
 
+// z = ||r|| * A32^{-1}(r / ||r||) approximately, by FP32 Jacobi-CG (the mixed preconditioner).
+nhmf_status mixed_inner(Ctx& x, const nhmf_solve_opts& o, const double* r, double* z, long long* inner) {
+  SolverWork& w = x.w;
+  norm2(x.n, r, w.sc + TMP, w.partials, x.s);
+  to_fp32_scaled(x.n, r, w.sc + TMP, true, w.b32, x.s);
+  long long it = 0;
+  double rel = 0.0;
+  nhmf_status st = pcg<float>(x, o.strategy, w.b32, w.x32, w.dinv32, w.r32, w.z32, w.p32, w.q32, o.inner_rtol,
+                              o.inner_max_iter, o.check_every, IN_RZ0, &it, &rel);
+  *inner += it;
+  if (st != NHMF_OK) return st;
+  to_fp64_scaled(x.n, w.x32, w.sc + TMP, z, x.s);
+  return cuda_check(x.c, cudaGetLastError(), "mixed preconditioner");
+}
+
+// Multi-preconditioned CG with two directions per iteration (Bridson and Greif, 2006),
+// truncated to one previous block: Z = [M1(r), M2(r)], P = Z - P_prev G_prev^-1 (AP_prev)^T Z,
+// alpha = (P^T A P)^-1 P^T r, x += P alpha, r -= AP alpha.  A direction is dropped when the
+// 2x2 Gram matrix is near singular.  Returns NHMF_ERR_NOT_CONVERGED on stagnation.
+template <class P1, class P2>
+nhmf_status mpcg2(Ctx& x, int strat, const double* b, double* sol, double rtol, int maxit, P1&& m1, P2&& m2,
+                  long long* iters, double* relres, int stall_window, double stall_factor) {
+  nhmf_ctx* c = x.c;
+  SolverWork& w = x.w;
+  double* sc = w.sc;
+  double bnh;
+  nhmf_status st = norm(x, b, BN, &bnh);
+  if (st != NHMF_OK) return st;
+  cudaMemsetAsync(sol, 0, x.n * sizeof(double), x.s);
+  *iters = 0;
+  *relres = 0.0;
+  if (!(bnh > 0.0)) return bnh == 0.0 ? NHMF_OK : fail(c, NHMF_ERR_NONFINITE, "mpcg: non-finite right-hand side");
+  cudaMemcpyAsync(w.r, b, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+  double *z1 = w.z, *z2 = w.t, *a1 = w.q, *a2 = w.qprev, *p1 = w.p, *p2 = w.x, *q1 = w.R, *q2 = w.d;
+  double G[3] = {0, 0, 0};  // previous block Gram matrix (00, 01, 11)
+  bool have_prev = false, prev_two = false;
+  std::vector<double> hist{bnh};
+  double rn = bnh;
+  long long k = 0;
+  auto dots = [&](std::initializer_list<std::pair<const double*, const double*>> prs, double* out) -> nhmf_status {
+    int i = 0;
+    for (auto& pr : prs) dot(x.n, pr.first, pr.second, sc + 32 + i++, w.partials, x.s);
+    nhmf_status s2 = cuda_check(c, cudaMemcpyAsync(w.host, sc + 32, i * sizeof(double), cudaMemcpyDeviceToHost, x.s), "dots");
+    if (s2 == NHMF_OK) s2 = cuda_check(c, cudaStreamSynchronize(x.s), "dots sync");
+    for (int j = 0; j < i; ++j) out[j] = w.host[j];
+    return s2;
+  };
+  for (; k < maxit;) {
+    if ((st = m1(w.r, z1)) != NHMF_OK) return st;
+    if ((st = m2(w.r, z2)) != NHMF_OK) return st;
+    if ((st = launch_apply(c, NHMF_FP64, strat, z1, a1, x.s)) != NHMF_OK) return st;
+    if ((st = launch_apply(c, NHMF_FP64, strat, z2, a2, x.s)) != NHMF_OK) return st;
+    if (have_prev) {
+      // beta = G_prev^-1 [q1.z1 q1.z2; q2.z1 q2.z2]
+      double C[4] = {0, 0, 0, 0};
+      if (prev_two) {
+        if ((st = dots({{q1, z1}, {q1, z2}, {q2, z1}, {q2, z2}}, C)) != NHMF_OK) return st;
+      } else {
+        if ((st = dots({{q1, z1}, {q1, z2}}, C)) != NHMF_OK) return st;
+      }
+      double B[4];
+      if (prev_two) {
+        const double det = G[0] * G[2] - G[1] * G[1];
+        B[0] = (G[2] * C[0] - G[1] * C[2]) / det;
+        B[1] = (G[2] * C[1] - G[1] * C[3]) / det;
+        B[2] = (G[0] * C[2] - G[1] * C[0]) / det;
+        B[3] = (G[0] * C[3] - G[1] * C[1]) / det;
+      } else {
+        B[0] = C[0] / G[0];
+        B[1] = C[1] / G[0];
+        B[2] = B[3] = 0.0;
+      }
+      axpby(x.n, -B[0], nullptr, p1, 1.0, nullptr, z1, x.s);
+      axpby(x.n, -B[1], nullptr, p1, 1.0, nullptr, z2, x.s);
+      axpby(x.n, -B[0], nullptr, q1, 1.0, nullptr, a1, x.s);
+      axpby(x.n, -B[1], nullptr, q1, 1.0, nullptr, a2, x.s);
+      if (prev_two) {
+        axpby(x.n, -B[2], nullptr, p2, 1.0, nullptr, z1, x.s);
+        axpby(x.n, -B[3], nullptr, p2, 1.0, nullptr, z2, x.s);
+        axpby(x.n, -B[2], nullptr, q2, 1.0, nullptr, a1, x.s);
+        axpby(x.n, -B[3], nullptr, q2, 1.0, nullptr, a2, x.s);
+      }
+    }
+    double D[5];
+    if ((st = dots({{z1, a1}, {z1, a2}, {z2, a2}, {z1, w.r}, {z2, w.r}}, D)) != NHMF_OK) return st;
+    if (!(D[0] > 0.0)) return fail(c, NHMF_ERR_BREAKDOWN, "mpcg: p^T A p <= 0");
+    double al0, al1;
+    const double det = D[0] * D[2] - D[1] * D[1];
+    const bool two = D[2] > 0.0 && det > 1e-10 * D[0] * D[2];
+    if (two) {
+      al0 = (D[2] * D[3] - D[1] * D[4]) / det;
+      al1 = (D[0] * D[4] - D[1] * D[3]) / det;
+    } else {
+      al0 = D[3] / D[0];
+      al1 = 0.0;
+    }
+    axpby(x.n, al0, nullptr, z1, 1.0, nullptr, sol, x.s);
+    axpby(x.n, -al0, nullptr, a1, 1.0, nullptr, w.r, x.s);
+    if (two) {
+      axpby(x.n, al1, nullptr, z2, 1.0, nullptr, sol, x.s);
+      axpby(x.n, -al1, nullptr, a2, 1.0, nullptr, w.r, x.s);
+    }
+    // the new block becomes the previous one (a dropped direction is not kept)
+    std::swap(p1, z1);
+    std::swap(q1, a1);
+    if (two) {
+      std::swap(p2, z2);
+      std::swap(q2, a2);
+    }
+    G[0] = D[0];
+    G[1] = two ? D[1] : 0.0;
+    G[2] = two ? D[2] : 0.0;
+    have_prev = true;
+    prev_two = two;
+    ++k;
+    if ((st = norm(x, w.r, RNORM, &rn)) != NHMF_OK) return st;
+    if (!std::isfinite(rn)) return fail(c, NHMF_ERR_NONFINITE, "mpcg: non-finite residual");
+    hist.push_back(rn);
+    if (rn <= rtol * bnh) break;
+    if (stall_window > 0 && (long long)hist.size() > stall_window &&
+        rn > stall_factor * hist[hist.size() - 1 - stall_window]) {
+      *iters = k;
+      *relres = rn / bnh;
+      return NHMF_ERR_NOT_CONVERGED;
+    }
+  }
+  *iters = k;
+  *relres = rn / bnh;
+  return rn <= rtol * bnh ? NHMF_OK : NHMF_ERR_NOT_CONVERGED;
+}
+
 // One linear solve A(ubar) sol = b with the chosen solver; the diagonal must be current.
 nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* sol, long long* outer,
                    long long* inner, double* relres, int* fallbacks) {
@@ -226,65 +358,53 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     for (int slot : slots) unet_snapshot_finish(x.c, slot, sol, x.s);
     return cuda_check(x.c, cudaGetLastError(), "pair recording");
   }
-  if (o.solver == NHMF_SOLVER_LEARNED_FCG) {
+  if (o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED) {
     if (!x.c->unet) return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no network in this context");
-    auto precond = [&](const double* r, double* z) -> nhmf_status {
-      unet_precondition(x.c, r, z, x.s);
-      if (o.learned_jacobi_weight != 0.0) {
-        cudaMemcpyAsync(w.t, r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
-        jacobi_apply(x.n, w.dinv, w.t, x.s);
-        axpby(x.n, o.learned_jacobi_weight, nullptr, w.t, 1.0, nullptr, z, x.s);
+    auto first = [&](const double* r, double* z) -> nhmf_status {
+      if (o.solver == NHMF_SOLVER_LEARNED_FCG) {
+        cudaMemcpyAsync(z, r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+        jacobi_apply(x.n, w.dinv, z, x.s);
+        return cuda_check(x.c, cudaGetLastError(), "jacobi direction");
       }
-      return cuda_check(x.c, cudaGetLastError(), "learned preconditioner");
+      return mixed_inner(x, o, r, z, inner);
+    };
+    auto second = [&](const double* r, double* z) -> nhmf_status {
+      unet_precondition(x.c, r, z, x.s);
+      return cuda_check(x.c, cudaGetLastError(), "network direction");
     };
     const int cap = std::max(1, o.linear_max_iter / 4);
-    nhmf_status st = fcg(x, o.strategy, b, sol, o.linear_rtol, cap, precond, outer, relres,
-                         o.learned_stall_window, o.learned_stall_factor);
-    if (st == NHMF_OK) return st;
+    nhmf_status st = mpcg2(x, o.strategy, b, sol, o.linear_rtol, cap, first, second, outer, relres,
+                           o.learned_stall_window, o.learned_stall_factor);
     if (st != NHMF_ERR_NOT_CONVERGED) return st;
     // fall back to Jacobi-CG on the remaining residual: A d = r, sol += d
     *fallbacks += 1;
     double bnh, rnh;
     if ((st = norm(x, b, TMP, &bnh)) != NHMF_OK) return st;
     if ((st = norm(x, w.r, TMP, &rnh)) != NHMF_OK) return st;
-    cudaMemcpyAsync(w.t, w.r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+    cudaMemcpyAsync(w.b2, w.r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
     long long it2 = 0;
     double rel2 = 0.0;
     const double rtol2 = rnh > 0.0 ? std::min(1.0, o.linear_rtol * bnh / rnh) : 1.0;
-    st = pcg<double>(x, o.strategy, w.t, w.utry, w.dinv, w.r, w.z, w.p, w.q, rtol2, o.linear_max_iter,
+    st = pcg<double>(x, o.strategy, w.b2, w.x2, w.dinv, w.r, w.z, w.p, w.q, rtol2, o.linear_max_iter,
                      o.check_every, RZ0, &it2, &rel2);
     if (st != NHMF_OK) return st;
-    axpby(x.n, 1.0, nullptr, w.utry, 1.0, nullptr, sol, x.s);
+    axpby(x.n, 1.0, nullptr, w.x2, 1.0, nullptr, sol, x.s);
     *outer += it2;
     *relres = rel2 * rnh / bnh;
     return cuda_check(x.c, cudaGetLastError(), "fallback");
-  }
-  if (o.solver == NHMF_SOLVER_MIXED_FCG) {
-    auto precond = [&](const double* r, double* z) -> nhmf_status {
-      // z = ||r|| * A32^{-1}(r / ||r||) approximately, by FP32 Jacobi-CG
-      norm2(x.n, r, w.sc + TMP, w.partials, x.s);
-      to_fp32_scaled(x.n, r, w.sc + TMP, true, w.b32, x.s);
-      long long it = 0;
-      double rel = 0.0;
-      nhmf_status st = pcg<float>(x, o.strategy, w.b32, w.x32, w.dinv32, w.r32, w.z32, w.p32, w.q32, o.inner_rtol,
-                                  o.inner_max_iter, o.check_every, IN_RZ0, &it, &rel);
-      *inner += it;
-      if (st != NHMF_OK) return st;
-      to_fp64_scaled(x.n, w.x32, w.sc + TMP, z, x.s);
-      return cuda_check(x.c, cudaGetLastError(), "mixed preconditioner");
-    };
-    return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
   }
   return fail(x.c, NHMF_ERR_ARG, "unknown solver");
 }
 
 int cache_mask(const nhmf_solve_opts& o) {
   if (o.strategy != NHMF_CACHED) return 0;
-  return o.solver == NHMF_SOLVER_MIXED_FCG ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32) : NHMF_CACHE_FP64;
+  return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED)
+             ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
+             : NHMF_CACHE_FP64;
 }
 
 nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
-  if (!o || o->solver < 0 || o->solver > 2 || (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED) ||
+  if (!o || o->solver < 0 || o->solver > 3 || (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED) ||
       o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
       o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)
     return fail(c, NHMF_ERR_ARG, "solve: bad options");
@@ -296,7 +416,7 @@ nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
 void free_work(nhmf_ctx* c) {
   if (!c->work) return;
   SolverWork& w = *c->work;
-  void* ptrs[] = {w.r, w.z, w.p, w.q, w.qprev, w.x, w.b, w.R, w.d, w.t, w.du, w.utry, w.diag, w.dinv,
+  void* ptrs[] = {w.r, w.z, w.p, w.q, w.qprev, w.x, w.b, w.R, w.d, w.t, w.du, w.utry, w.diag, w.dinv, w.b2, w.x2,
                   w.r32, w.z32, w.p32, w.q32, w.x32, w.b32, w.dinv32, w.sc, w.partials};
   for (void* p : ptrs) cudaFree(p);
   if (w.host) cudaFreeHost(w.host);
@@ -328,9 +448,10 @@ void nhmf_solve_opts_default(nhmf_solve_opts* o) {
   o->check_every = 10;
   o->record_pairs = 0;
   o->cg_pair_every = 8;
-  o->learned_jacobi_weight = 0.0;
   o->learned_stall_window = 10;
   o->learned_stall_factor = 0.9;
+  o->synthetic_pairs = 0;
+  o->seed = 1;
 }
 
 nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const double* b, double* xsol, long long* iters,
@@ -340,7 +461,7 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   nhmf_status st = check_opts(c, o);
   if (st != NHMF_OK) return st;
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "linear_solve: no linearisation point set");
-  if (o->strategy == NHMF_CACHED && (!c->cache64 || (o->solver == NHMF_SOLVER_MIXED_FCG && !c->cache32)))
+  if (o->strategy == NHMF_CACHED && (!c->cache64 || ((cache_mask(*o) & NHMF_CACHE_FP32) && !c->cache32)))
     return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
   if ((st = ensure_work(c)) != NHMF_OK) return st;
   Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
@@ -407,8 +528,14 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
       long long outer = 0, inner = 0;
       double rel = 0.0;
       if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel, &stats->fallbacks[k])) != NHMF_OK) return st;
-      if (o->record_pairs && o->solver == NHMF_SOLVER_JACOBI_CG && c->unet)
+      if (o->record_pairs && o->solver == NHMF_SOLVER_JACOBI_CG && c->unet) {
         if ((st = unet_record(c, w.b, w.du, x.s)) != NHMF_OK) return st;   // Newton pair (b, du)
+        for (int q = 0; q < o->synthetic_pairs; ++q) {                     // (K e, e), smooth e
+          unet_smooth_field(c, w.t, o->seed + 0x100000ull * (unsigned long long)(step * 64 + it) + q, x.s);
+          if ((st = launch_apply(c, NHMF_FP64, o->strategy, w.t, w.x2, x.s)) != NHMF_OK) return st;
+          if ((st = unet_record(c, w.x2, w.t, x.s)) != NHMF_OK) return st;
+        }
+      }
       stats->linear_iters[k] += outer;
       stats->inner_iters[k] += inner;
       // backtracking: halve the step while det F <= 0 somewhere

@@ -611,6 +611,60 @@ __global__ void k_scale_f32(long long n3, const double* nrm, double mul, float* 
 }
 }  // namespace
 
+namespace {
+// splitmix64 (Steele, Lea and Flood 2014): output k of seed s is mix(s + (k + 1) * gamma).
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// standard normal from outputs 2k and 2k+1 (Box-Muller, first of the pair)
+__device__ __forceinline__ double normal_at(unsigned long long seed, unsigned long long k) {
+  const double u1 = 1.0 - double(splitmix64_at(seed, 2 * k) >> 11) * 0x1.0p-53;
+  const double u2 = double(splitmix64_at(seed, 2 * k + 1) >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+// e_c(x) = sum over octaves L = 1..4 of 2^-L times the trilinear interpolant of N(0,1) values
+// on a (2^L + 1)^3 lattice over the unit cube (node coordinates i/(M-1)); 0 on constrained DoFs.
+__global__ void k_smooth_field(double* e, int M, int bc, unsigned long long seed) {
+  const long long n = (long long)M * M * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i / n);
+    const long long v = i % n;
+    const int x = int(v % M), y = int((v / M) % M), z = int(v / ((long long)M * M));
+    if (constrained_dof(bc, c, v, M)) {
+      e[i] = 0.0;
+      continue;
+    }
+    double s = 0.0;
+    unsigned long long base = 0;
+    for (int L = 1; L <= 4; ++L) {
+      const int G = (1 << L) + 1;
+      const double fx = double(x) / (M - 1) * (G - 1), fy = double(y) / (M - 1) * (G - 1), fz = double(z) / (M - 1) * (G - 1);
+      const int ix = min(int(fx), G - 2), iy = min(int(fy), G - 2), iz = min(int(fz), G - 2);
+      const double tx = fx - ix, ty = fy - iy, tz = fz - iz;
+      double acc = 0.0;
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            const unsigned long long k =
+                base + (unsigned long long)c * G * G * G + (ix + dx) + (unsigned long long)G * ((iy + dy) + G * (iz + dz));
+            const double wgt = (dx ? tx : 1.0 - tx) * (dy ? ty : 1.0 - ty) * (dz ? tz : 1.0 - tz);
+            acc += wgt * normal_at(seed, k);
+          }
+      s += acc / double(1 << L);
+      base += 3ull * G * G * G;
+    }
+    e[i] = s;
+  }
+}
+}  // namespace
+
+void unet_smooth_field(nhmf_ctx* c, double* e, unsigned long long seed, cudaStream_t s) {
+  k_smooth_field<<<kConvBlocks, 256, 0, s>>>(e, c->g.M, c->prm.bc, seed);
+}
+
 // CG snapshot: input slot <- r_j normalised, target slot <- x_j (finished later).
 int unet_snapshot_begin(nhmf_ctx* c, const double* r, const double* xj, cudaStream_t s) {
   UNet& u = *c->unet;

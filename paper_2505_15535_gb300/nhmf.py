@@ -33,7 +33,7 @@ class nhmf_params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("bc", ctypes.c_int), ("top_uz", ctypes.c_double)]
 
 
-NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG = 0, 1, 2
+NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG, NHMF_SOLVER_MIXED_LEARNED = 0, 1, 2, 3
 NHMF_MAX_STEPS = 64
 
 
@@ -45,8 +45,8 @@ class nhmf_solve_opts(ctypes.Structure):
                 ("linear_max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("inner_max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("record_pairs", ctypes.c_int), ("cg_pair_every", ctypes.c_int),
-                ("learned_jacobi_weight", ctypes.c_double), ("learned_stall_window", ctypes.c_int),
-                ("learned_stall_factor", ctypes.c_double)]
+                ("learned_stall_window", ctypes.c_int), ("learned_stall_factor", ctypes.c_double),
+                ("synthetic_pairs", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 class nhmf_solve_stats(ctypes.Structure):
