@@ -153,7 +153,8 @@ typedef struct {
   double learned_stall_factor;  /* drops by less than this factor over this many iterations
                                    (defaults 10 and 0.9), or after linear_max_iter/4 iterations */
   int synthetic_pairs;  /* with record_pairs: per Newton iterate, also store this many pairs
-                           (K(u) e, e) for smooth random fields e, default 0 */
+                           (K(u) e, e) for random fields e at one lattice scale each (from
+                           the coarsest lattice to nodal white noise), default 0 */
   unsigned long long seed;      /* counter-based generator seed of those fields, default 1 */
 } nhmf_solve_opts;
 

@@ -358,6 +358,10 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     for (int slot : slots) unet_snapshot_finish(x.c, slot, sol, x.s);
     return cuda_check(x.c, cudaGetLastError(), "pair recording");
   }
+  if (o.solver == NHMF_SOLVER_MIXED_FCG) {
+    auto precond = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
+    return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+  }
   if (o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED) {
     if (!x.c->unet) return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no network in this context");
     auto first = [&](const double* r, double* z) -> nhmf_status {
@@ -531,7 +535,7 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
       if (o->record_pairs && o->solver == NHMF_SOLVER_JACOBI_CG && c->unet) {
         if ((st = unet_record(c, w.b, w.du, x.s)) != NHMF_OK) return st;   // Newton pair (b, du)
         for (int q = 0; q < o->synthetic_pairs; ++q) {                     // (K e, e), smooth e
-          unet_smooth_field(c, w.t, o->seed + 0x100000ull * (unsigned long long)(step * 64 + it) + q, x.s);
+          unet_smooth_field(c, w.t, o->seed + 0x100000ull * (unsigned long long)(step * 64 + it) + q, x.s);  // scale = seed mod levels
           if ((st = launch_apply(c, NHMF_FP64, o->strategy, w.t, w.x2, x.s)) != NHMF_OK) return st;
           if ((st = unet_record(c, w.x2, w.t, x.s)) != NHMF_OK) return st;
         }

@@ -625,10 +625,16 @@ __device__ __forceinline__ double normal_at(unsigned long long seed, unsigned lo
   const double u2 = double(splitmix64_at(seed, 2 * k + 1) >> 11) * 0x1.0p-53;
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
-// e_c(x) = sum over octaves L = 1..4 of 2^-L times the trilinear interpolant of N(0,1) values
-// on a (2^L + 1)^3 lattice over the unit cube (node coordinates i/(M-1)); 0 on constrained DoFs.
+// Random field at one lattice scale: e_c(x) = trilinear interpolant of N(0,1) values on a
+// (2^L + 1)^3 lattice over the unit cube (node coordinates i/(M-1)); L = 1 + seed mod Lmax with
+// 2^Lmax = M - 1, so the pairs of consecutive seeds sweep from the coarsest lattice to nodal
+// white noise.  Zero on constrained DoFs.
 __global__ void k_smooth_field(double* e, int M, int bc, unsigned long long seed) {
   const long long n = (long long)M * M * M;
+  int Lmax = 0;
+  while ((1 << (Lmax + 1)) <= M - 1) ++Lmax;
+  const int L = 1 + int(seed % (unsigned long long)Lmax);
+  const int G = (1 << L) + 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n; i += (long long)gridDim.x * blockDim.x) {
     const int c = int(i / n);
     const long long v = i % n;
@@ -637,26 +643,18 @@ __global__ void k_smooth_field(double* e, int M, int bc, unsigned long long seed
       e[i] = 0.0;
       continue;
     }
-    double s = 0.0;
-    unsigned long long base = 0;
-    for (int L = 1; L <= 4; ++L) {
-      const int G = (1 << L) + 1;
-      const double fx = double(x) / (M - 1) * (G - 1), fy = double(y) / (M - 1) * (G - 1), fz = double(z) / (M - 1) * (G - 1);
-      const int ix = min(int(fx), G - 2), iy = min(int(fy), G - 2), iz = min(int(fz), G - 2);
-      const double tx = fx - ix, ty = fy - iy, tz = fz - iz;
-      double acc = 0.0;
-      for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-          for (int dx = 0; dx < 2; ++dx) {
-            const unsigned long long k =
-                base + (unsigned long long)c * G * G * G + (ix + dx) + (unsigned long long)G * ((iy + dy) + G * (iz + dz));
-            const double wgt = (dx ? tx : 1.0 - tx) * (dy ? ty : 1.0 - ty) * (dz ? tz : 1.0 - tz);
-            acc += wgt * normal_at(seed, k);
-          }
-      s += acc / double(1 << L);
-      base += 3ull * G * G * G;
-    }
-    e[i] = s;
+    const double fx = double(x) / (M - 1) * (G - 1), fy = double(y) / (M - 1) * (G - 1), fz = double(z) / (M - 1) * (G - 1);
+    const int ix = min(int(fx), G - 2), iy = min(int(fy), G - 2), iz = min(int(fz), G - 2);
+    const double tx = fx - ix, ty = fy - iy, tz = fz - iz;
+    double acc = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const unsigned long long k = (unsigned long long)c * G * G * G + (ix + dx) + (unsigned long long)G * ((iy + dy) + G * (iz + dz));
+          const double wgt = (dx ? tx : 1.0 - tx) * (dy ? ty : 1.0 - ty) * (dz ? tz : 1.0 - tz);
+          acc += wgt * normal_at(seed, k);
+        }
+    e[i] = acc;
   }
 }
 }  // namespace
