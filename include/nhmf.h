@@ -121,12 +121,12 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *                          (the plain baseline);
  *   NHMF_SOLVER_MIXED_FCG  FP64 flexible CG whose preconditioner is an FP32 Jacobi-CG on the
  *                          FP32 apply (FP64 residuals, dot products and updates outside);
- *   NHMF_SOLVER_LEARNED_FCG FP64 multi-preconditioned CG with two search directions per
- *                          iteration, D^-1 r and the trained U-Net's N(r), combined by a 2x2
- *                          Galerkin step and A-orthogonalised against the previous pair; falls
- *                          back to Jacobi-CG from the current iterate on stagnation;
- *   NHMF_SOLVER_MIXED_LEARNED the same with the FP32 inner Jacobi-CG of MIXED_FCG in place of
- *                          D^-1 r. */
+ *   NHMF_SOLVER_LEARNED_FCG FP64 flexible CG preconditioned by the trained U-Net, z = N(r);
+ *                          falls back to Jacobi-CG from the current iterate on stagnation;
+ *   NHMF_SOLVER_MIXED_LEARNED FP64 multi-preconditioned CG with two search directions per
+ *                          iteration, the FP32 inner Jacobi-CG of MIXED_FCG and N(r), combined
+ *                          by a 2x2 Galerkin step and A-orthogonalised against the previous
+ *                          pair; same fallback. */
 enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2,
        NHMF_SOLVER_MIXED_LEARNED = 3 };
 #define NHMF_MAX_STEPS 64

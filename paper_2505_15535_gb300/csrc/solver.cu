@@ -364,21 +364,18 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
   }
   if (o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED) {
     if (!x.c->unet) return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no network in this context");
-    auto first = [&](const double* r, double* z) -> nhmf_status {
-      if (o.solver == NHMF_SOLVER_LEARNED_FCG) {
-        cudaMemcpyAsync(z, r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
-        jacobi_apply(x.n, w.dinv, z, x.s);
-        return cuda_check(x.c, cudaGetLastError(), "jacobi direction");
-      }
-      return mixed_inner(x, o, r, z, inner);
-    };
-    auto second = [&](const double* r, double* z) -> nhmf_status {
+    auto network = [&](const double* r, double* z) -> nhmf_status {
       unet_precondition(x.c, r, z, x.s);
       return cuda_check(x.c, cudaGetLastError(), "network direction");
     };
+    auto inner_cg = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
     const int cap = std::max(1, o.linear_max_iter / 4);
-    nhmf_status st = mpcg2(x, o.strategy, b, sol, o.linear_rtol, cap, first, second, outer, relres,
-                           o.learned_stall_window, o.learned_stall_factor);
+    nhmf_status st =
+        o.solver == NHMF_SOLVER_LEARNED_FCG
+            ? fcg(x, o.strategy, b, sol, o.linear_rtol, cap, network, outer, relres, o.learned_stall_window,
+                  o.learned_stall_factor)
+            : mpcg2(x, o.strategy, b, sol, o.linear_rtol, cap, inner_cg, network, outer, relres,
+                    o.learned_stall_window, o.learned_stall_factor);
     if (st != NHMF_ERR_NOT_CONVERGED) return st;
     // fall back to Jacobi-CG on the remaining residual: A d = r, sol += d
     *fallbacks += 1;
