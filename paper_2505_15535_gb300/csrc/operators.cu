@@ -381,173 +381,6 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
         for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += acc[c][idx(i, j, k)];
 }
 
-// ------------------------------------------------------------------ FP32 component-split kernel
-// Three lanes per element, one per displacement component (lanes 3e, 3e+1, 3e+2 of a warp
-// hold element e; lanes 30 and 31 idle): each lane gathers, interpolates and integrates its
-// own component in registers, and at every Gauss point the nine gradient entries are
-// exchanged with warp shuffles.  Each lane then forms row c of the linearised stress.
-template <int P, int STRAT>
-__global__ void __launch_bounds__(256, 2) k_apply_split(const OpArgs a) {
-  constexpr int n = P + 1, n3 = n * n * n;
-  const int lane = threadIdx.x & 31;
-  const int grp = lane < 30 ? lane / 3 : 9;              // idle lanes shadow group 9
-  const int c = lane < 30 ? lane % 3 : 0;
-  const int base = 3 * grp;
-  const long long ec = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 10 + grp;
-  const bool valid = lane < 30 && ec < a.col.count;
-  const Colour& col = a.col;
-  const long long ecc = valid ? ec : 0;
-  const int ix = int(ecc % col.nx), iy = int((ecc / col.nx) % col.ny), iz = int(ecc / ((long long)col.nx * col.ny));
-  const int gi0 = P * (col.cx + 2 * ix), gj0 = P * (col.cy + 2 * iy), gk0 = P * (col.cz + 2 * iz);
-  const long long M = a.M;
-  const long long slot = col.slot0 + ecc, E = a.nq / n3;
-  const float* __restrict__ du = static_cast<const float*>(a.du);
-  float* __restrict__ v = static_cast<float*>(a.v);
-  auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
-  auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
-  auto pass = [&](float (&f)[n3], int dir, bool transposed) {
-#pragma unroll
-    for (int o1 = 0; o1 < n; ++o1)
-#pragma unroll
-      for (int o2 = 0; o2 < n; ++o2) {
-        float t[n];
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const float coef = transposed ? a.Bf[m * n + r] : a.Bf[r * n + m];
-            const int id = dir == 0 ? idx(m, o1, o2) : (dir == 1 ? idx(o1, m, o2) : idx(o1, o2, m));
-            s = m == 0 ? coef * f[id] : fmaf(coef, f[id], s);
-          }
-          t[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          const int id = dir == 0 ? idx(r, o1, o2) : (dir == 1 ? idx(o1, r, o2) : idx(o1, o2, r));
-          f[id] = t[r];
-        }
-      }
-  };
-  auto grad3 = [&](const float (&f)[n3], int qx, int qy, int qz, float g[3]) {
-    float gx = a.Dcf[qx * n] * f[idx(0, qy, qz)];
-    float gy = a.Dcf[qy * n] * f[idx(qx, 0, qz)];
-    float gz = a.Dcf[qz * n] * f[idx(qx, qy, 0)];
-#pragma unroll
-    for (int m = 1; m < n; ++m) {
-      gx = fmaf(a.Dcf[qx * n + m], f[idx(m, qy, qz)], gx);
-      gy = fmaf(a.Dcf[qy * n + m], f[idx(qx, m, qz)], gy);
-      gz = fmaf(a.Dcf[qz * n + m], f[idx(qx, qy, m)], gz);
-    }
-    g[0] = gx;
-    g[1] = gy;
-    g[2] = gz;
-  };
-  // all nine entries [3 comp][3 dir] of a per-lane row via shuffles within the group
-  auto gather9 = [&](const float row[3], float full[9]) {
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) full[3 * cc + d] = __shfl_sync(0xffffffffu, row[d], base + cc);
-  };
-
-  float qv[n3];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int j = 0; j < n; ++j)
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        const bool fixed = is_constrained(a.bc, c, gi0 + i, gk0 + k, a.M);
-        qv[idx(i, j, k)] = (valid && !fixed) ? du[c * a.M3 + node(i, j, k)] : 0.f;
-      }
-  pass(qv, 0, false);
-  pass(qv, 1, false);
-  pass(qv, 2, false);
-  float ub[STRAT == NHMF_ON_THE_FLY ? n3 : 1];
-  if constexpr (STRAT == NHMF_ON_THE_FLY) {
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int j = 0; j < n; ++j)
-#pragma unroll
-        for (int i = 0; i < n; ++i) ub[idx(i, j, k)] = valid ? a.u32[c * a.M3 + node(i, j, k)] : 0.f;
-    pass(ub, 0, false);
-    pass(ub, 1, false);
-    pass(ub, 2, false);
-  }
-  float acc[n3];
-#pragma unroll
-  for (int q = 0; q < n3; ++q) acc[q] = 0.f;
-  const float mu = float(a.mu), lam = float(a.lam), h = float(a.h), invh = float(1.0 / a.h);
-  const float* __restrict__ cache = static_cast<const float*>(a.cache);
-  bool bad = false;
-#pragma unroll
-  for (int qz = 0; qz < n; ++qz)
-#pragma unroll
-    for (int qy = 0; qy < n; ++qy)
-#pragma unroll
-      for (int qx = 0; qx < n; ++qx) {
-        const int q = idx(qx, qy, qz);
-        float Fi[9], lnJ;
-        if constexpr (STRAT == NHMF_ON_THE_FLY) {
-          float hrow[3], H[9];
-          grad3(ub, qx, qy, qz, hrow);
-          gather9(hrow, H);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) H[k] *= invh;
-          const float Jm1 = kinematics(H, Fi, lnJ);
-          bad |= valid && !(Jm1 > -1.f);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = __ldg(cache + (k * n3 + q) * E + slot);
-          lnJ = __ldg(cache + (9 * n3 + q) * E + slot);
-        }
-        float drow[3], dH[9];
-        grad3(qv, qx, qy, qz, drow);
-        gather9(drow, dH);
-        // row c of s (mu dH + (mu - 2 lam ln J) (F^-1 dH F^-1)^T + 2 lam tr(F^-1 dH) F^-T)
-        float K[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            K[3 * i + j] = fmaf(Fi[3 * i], dH[j], fmaf(Fi[3 * i + 1], dH[3 + j], Fi[3 * i + 2] * dH[6 + j]));
-        const float s = a.wf[qx] * a.wf[qy] * a.wf[qz] * h;
-        const float smu = s * mu, sc1 = s * (mu - 2.f * lam * lnJ), sc2 = s * (2.f * lam * (K[0] + K[4] + K[8]));
-        float g[3];
-#pragma unroll
-        for (int J = 0; J < 3; ++J) {
-          float FiJc, dHcJ, QJc;
-          // select row c without dynamic register indexing
-          FiJc = c == 0 ? Fi[3 * J] : (c == 1 ? Fi[3 * J + 1] : Fi[3 * J + 2]);
-          dHcJ = c == 0 ? dH[J] : (c == 1 ? dH[3 + J] : dH[6 + J]);
-          const float F0c = c == 0 ? Fi[0] : (c == 1 ? Fi[1] : Fi[2]);
-          const float F1c = c == 0 ? Fi[3] : (c == 1 ? Fi[4] : Fi[5]);
-          const float F2c = c == 0 ? Fi[6] : (c == 1 ? Fi[7] : Fi[8]);
-          QJc = fmaf(K[3 * J], F0c, fmaf(K[3 * J + 1], F1c, K[3 * J + 2] * F2c));
-          g[J] = fmaf(smu, dHcJ, fmaf(sc1, QJc, sc2 * FiJc));
-        }
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          acc[idx(m, qy, qz)] = fmaf(a.Dcf[qx * n + m], g[0], acc[idx(m, qy, qz)]);
-          acc[idx(qx, m, qz)] = fmaf(a.Dcf[qy * n + m], g[1], acc[idx(qx, m, qz)]);
-          acc[idx(qx, qy, m)] = fmaf(a.Dcf[qz * n + m], g[2], acc[idx(qx, qy, m)]);
-        }
-      }
-  if (bad) atomicOr(a.status, kStatusNonPosJ);
-  pass(acc, 0, true);
-  pass(acc, 1, true);
-  pass(acc, 2, true);
-  if (!valid) return;
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int j = 0; j < n; ++j)
-#pragma unroll
-      for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += acc[idx(i, j, k)];
-}
-
 // ------------------------------------------------------------------ point cache
 template <int P>
 __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs a) {
@@ -834,7 +667,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
     return cuda_check(c, e, "apply memset");
   nhmf_status st;
   if constexpr (sizeof(T) == 4 && P <= 2)
-    st = run_colours(c, k_apply_split<P, STRAT>, a, 80, 256, 0, s, "apply", NHMF_KIND_APPLY);
+    st = run_colours(c, k_apply_reg<P, STRAT>, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
   else
     st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
   if (st != NHMF_OK || raw) return st;
