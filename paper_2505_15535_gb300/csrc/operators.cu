@@ -381,155 +381,6 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
         for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += acc[c][idx(i, j, k)];
 }
 
-// ------------------------------------------------------------------ FP32 element-per-thread kernel
-// One thread per element.  The sum-factorisation passes run fully unrolled in registers
-// (compile-time coefficients from the constant bank); the Gauss-point loop is a runtime loop
-// over thread-private shared-memory slices (point values in, transposed-derivative
-// accumulators out), which keeps the code small enough for the instruction cache.  Slice
-// layout [value][thread]: consecutive threads hit consecutive banks.
-template <int P> struct F32E { static constexpr int T = 64; };
-
-template <int P, int STRAT>
-__global__ void __launch_bounds__(F32E<P>::T) k_apply_f32e(const OpArgs a) {
-  constexpr int n = P + 1, n3 = n * n * n, T = F32E<P>::T;
-  constexpr int NS = STRAT == NHMF_ON_THE_FLY ? 9 : 6;  // slices of n3 values: qv (3), acc (3), ub (3)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sh = reinterpret_cast<float*>(smem_raw);
-  const int tid = threadIdx.x;
-  auto SQ = [&](int c, int q) -> float& { return sh[(c * n3 + q) * T + tid]; };
-  auto SA = [&](int c, int q) -> float& { return sh[((3 + c) * n3 + q) * T + tid]; };
-  auto SU = [&](int c, int q) -> float& { return sh[((6 + c) * n3 + q) * T + tid]; };
-  (void)NS;
-  const long long ec = blockIdx.x * (long long)T + tid;
-  const bool valid = ec < a.col.count;
-  const Colour& col = a.col;
-  const long long ecc = valid ? ec : 0;
-  const int ix = int(ecc % col.nx), iy = int((ecc / col.nx) % col.ny), iz = int(ecc / ((long long)col.nx * col.ny));
-  const int gi0 = P * (col.cx + 2 * ix), gj0 = P * (col.cy + 2 * iy), gk0 = P * (col.cz + 2 * iz);
-  const long long M = a.M;
-  const long long slot = col.slot0 + ecc, E = a.nq / n3;
-  auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
-  auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
-  auto pass = [&](float (&f)[n3], int dir, bool transposed) {
-#pragma unroll
-    for (int o1 = 0; o1 < n; ++o1)
-#pragma unroll
-      for (int o2 = 0; o2 < n; ++o2) {
-        float t[n];
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const float coef = transposed ? a.Bf[m * n + r] : a.Bf[r * n + m];
-            const int id = dir == 0 ? idx(m, o1, o2) : (dir == 1 ? idx(o1, m, o2) : idx(o1, o2, m));
-            s = m == 0 ? coef * f[id] : fmaf(coef, f[id], s);
-          }
-          t[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          const int id = dir == 0 ? idx(r, o1, o2) : (dir == 1 ? idx(o1, r, o2) : idx(o1, o2, r));
-          f[id] = t[r];
-        }
-      }
-  };
-  // forward: gather, interpolate to the points, park in shared memory
-  auto load_to_points = [&](auto src, bool mask, int slice0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float f[n3];
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-#pragma unroll
-        for (int j = 0; j < n; ++j)
-#pragma unroll
-          for (int i = 0; i < n; ++i) {
-            const bool fixed = mask && is_constrained(a.bc, c, gi0 + i, gk0 + k, a.M);
-            f[idx(i, j, k)] = (valid && !fixed) ? float(src[c * a.M3 + node(i, j, k)]) : 0.f;
-          }
-      pass(f, 0, false);
-      pass(f, 1, false);
-      pass(f, 2, false);
-#pragma unroll
-      for (int q = 0; q < n3; ++q) sh[((slice0 + c) * n3 + q) * T + tid] = f[q];
-    }
-  };
-  load_to_points(static_cast<const float*>(a.du), true, 0);
-  if (STRAT == NHMF_ON_THE_FLY) load_to_points(a.u32, false, 6);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int q = 0; q < n3; ++q) SA(c, q) = 0.f;
-  const float mu = float(a.mu), lam = float(a.lam), h = float(a.h), invh = float(1.0 / a.h);
-  const float* __restrict__ cache = static_cast<const float*>(a.cache);
-  bool bad = false;
-#pragma unroll 1
-  for (int q = 0; q < n3; ++q) {
-    const int qx = q % n, qy = (q / n) % n, qz = q / (n * n);
-    auto grad = [&](int slice0, float g[9]) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          gx = fmaf(a.Dcf[qx * n + m], sh[((slice0 + c) * n3 + idx(m, qy, qz)) * T + tid], gx);
-          gy = fmaf(a.Dcf[qy * n + m], sh[((slice0 + c) * n3 + idx(qx, m, qz)) * T + tid], gy);
-          gz = fmaf(a.Dcf[qz * n + m], sh[((slice0 + c) * n3 + idx(qx, qy, m)) * T + tid], gz);
-        }
-        g[3 * c + 0] = gx;
-        g[3 * c + 1] = gy;
-        g[3 * c + 2] = gz;
-      }
-    };
-    float Fi[9], lnJ;
-    if (STRAT == NHMF_ON_THE_FLY) {
-      float H[9];
-      grad(6, H);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) H[k] *= invh;
-      const float Jm1 = kinematics(H, Fi, lnJ);
-      bad |= valid && !(Jm1 > -1.f);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Fi[k] = __ldg(cache + (k * n3 + q) * E + slot);
-      lnJ = __ldg(cache + (9 * n3 + q) * E + slot);
-    }
-    float dH[9], g[9];
-    grad(0, dH);
-    linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        SA(c, idx(m, qy, qz)) = fmaf(a.Dcf[qx * n + m], g[3 * c + 0], SA(c, idx(m, qy, qz)));
-        SA(c, idx(qx, m, qz)) = fmaf(a.Dcf[qy * n + m], g[3 * c + 1], SA(c, idx(qx, m, qz)));
-        SA(c, idx(qx, qy, m)) = fmaf(a.Dcf[qz * n + m], g[3 * c + 2], SA(c, idx(qx, qy, m)));
-      }
-  }
-  if (bad) atomicOr(a.status, kStatusNonPosJ);
-  float* __restrict__ v = static_cast<float*>(a.v);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float f[n3];
-#pragma unroll
-    for (int q = 0; q < n3; ++q) f[q] = SA(c, q);
-    pass(f, 0, true);
-    pass(f, 1, true);
-    pass(f, 2, true);
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-#pragma unroll
-        for (int j = 0; j < n; ++j)
-#pragma unroll
-          for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += f[idx(i, j, k)];
-    }
-  }
-  (void)SQ;
-  (void)SU;
-}
-
 // ------------------------------------------------------------------ point cache
 template <int P>
 __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs a) {
@@ -816,9 +667,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
     return cuda_check(c, e, "apply memset");
   nhmf_status st;
   if constexpr (sizeof(T) == 4 && P <= 2)
-    st = run_colours(c, k_apply_f32e<P, STRAT>, a, F32E<P>::T, F32E<P>::T,
-                     (size_t)(STRAT == NHMF_ON_THE_FLY ? 9 : 6) * n3 * F32E<P>::T * sizeof(float), s, "apply",
-                     NHMF_KIND_APPLY);
+    st = run_colours(c, k_apply_reg<P, STRAT>, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
   else
     st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
   if (st != NHMF_OK || raw) return st;
