@@ -329,6 +329,125 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ Newton mode
+UNET_LAYERS = [("conv", 3, 16), ("conv", 16, 16), ("down", 16, 16), ("conv", 16, 16), ("down", 16, 16),
+               ("conv", 16, 16), ("up", 16, 16), ("conv", 16, 16), ("up", 16, 16), ("conv", 16, 16),
+               ("conv", 16, 3)]
+
+
+def he_init_flat(seed=5000):
+    """Initial U-Net parameters in the library's flat layout: He-normal weights
+    (std sqrt(2 / (27 c_in))) from seeded N(0, 1) draws, zero biases."""
+    parts = []
+    for k, (_, cin, cout) in enumerate(UNET_LAYERS):
+        parts.append(inp.normal(seed + k, cin * cout * 27) * np.sqrt(2.0 / (27 * cin)))
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts)
+
+NEWTON_METRIC = "Newton time to 1e-8 (mixed FP32-inner / learned vs plain FP64 Jacobi-CG)"
+
+
+def run_newton(args):
+    """Load steps of the compression workload, one solve call per step, for each solver.
+
+    plain: FP64 Jacobi-CG; mixed: FP64 flexible CG with an FP32 inner Jacobi-CG; learned and
+    mixed_learned: the U-Net preconditioner trained on pairs recorded during the plain solve of
+    the first `train_steps` load steps.  Per step: wall time, Newton/outer/inner iterations,
+    the relative difference to the plain solver's state, the oracle's FP64 residual on sampled
+    rows of that state, and the FP32 apply's error against the oracle at that state."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2505_15535_gb300 import nhmf
+    from oracle.fem import Operator
+    from oracle.mesh import Mesh
+    dev = torch.device("cuda", 0)
+    w = inp.WORKLOADS[args.workload]
+    S = w.load_steps
+    last = min(S, args.last_step) if args.last_step else S
+    prob = nhmf.Problem(w.n_el, w.degree, w.mu, w.lam, w.bc)
+    solvers = [s.strip() for s in args.solvers.split(",") if s.strip()]
+    learned = any(s in ("learned", "mixed_learned") for s in solvers)
+    if learned:
+        nhmf.nhmf_unet_create(prob.ctx, args.pairs)
+        nhmf.nhmf_unet_set_params(prob.ctx, he_init_flat())
+    base = dict(compression=w.compression, load_steps=S, linear_rtol=args.linear_rtol,
+                newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter)
+    ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
+           "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED}
+    op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(w.n_dofs, 64, replace=False))
+    out = {"metric": NEWTON_METRIC, "mode": "newton", "workload": f"{w.name}: " + describe(w) +
+           f"; {S} load steps of {w.compression / S:g}", "steps_run": last, "solvers": {}}
+    states = {}
+    for name in solvers:
+        u = torch.zeros(w.n_dofs, dtype=torch.float64, device=dev)
+        per = []
+        first = 1
+        if name in ("learned", "mixed_learned"):
+            # start from the plain solver's state after the training steps
+            first = args.train_steps + 1
+            u = states["plain"][args.train_steps - 1].clone()
+        for step in range(first, last + 1):
+            kw = dict(base, first_step=step, last_step=step, solver=ids[name])
+            if name == "plain" and learned and step <= args.train_steps:
+                kw.update(record_pairs=1, cg_pair_every=8, synthetic_pairs=args.synthetic)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = prob.solve(u, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            states.setdefault(name, []).append(u.clone())
+            rec = {"step": step, "seconds": dt, "newton": st["newton_iters"][0], "outer": st["linear_iters"][0],
+                   "inner": st["inner_iters"][0], "fallbacks": st["fallbacks"][0], "rel_residual": st["rel_residual"][0]}
+            per.append(rec)
+            if name == "plain" and learned and step == args.train_steps:
+                t0 = time.perf_counter()
+                l0, l1 = nhmf.nhmf_unet_train(prob.ctx, args.epochs, 1e-3)
+                torch.cuda.synchronize()
+                out["training"] = {"pairs": nhmf.nhmf_unet_num_pairs(prob.ctx), "epochs": args.epochs,
+                                   "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0}
+        out["solvers"][name] = {"steps": per, "seconds": sum(r["seconds"] for r in per),
+                                "outer": sum(r["outer"] for r in per), "inner": sum(r["inner"] for r in per),
+                                "newton": sum(r["newton"] for r in per), "fallbacks": sum(r["fallbacks"] for r in per)}
+    # per-step agreement with plain and oracle checks on sampled rows
+    if "plain" in states:
+        plain = states["plain"]
+        for name, lst in states.items():
+            off = 0 if name in ("plain", "mixed") else args.train_steps
+            for k, uu in enumerate(lst):
+                rec = out["solvers"][name]["steps"][k]
+                ref = plain[k + off]
+                rec["rel_diff_vs_plain"] = float(torch.linalg.norm(uu - ref) / torch.linalg.norm(ref))
+    for name, lst in states.items():
+        uu = lst[-1].cpu().numpy()
+        R = op.residual_rows(uu, rows)
+        scale = np.abs(op.apply_rows(uu, uu, rows)).max()
+        out["solvers"][name]["oracle_residual_rows_rel"] = float(np.abs(R).max() / scale)
+    # FP32 apply error vs the oracle at the final plain state
+    if "plain" in states:
+        uu = states["plain"][-1]
+        prob.set_linearization(uu, nhmf.NHMF_CACHE_FP32)
+        du = torch.from_numpy(inp.draw_vector(77, w.n_dofs)).to(dev)
+        v32 = torch.empty(w.n_dofs, dtype=torch.float32, device=dev)
+        prob.apply(du.float(), v32, nhmf.NHMF_FP32, nhmf.NHMF_CACHED)
+        ref = op.apply_rows(uu.cpu().numpy(), du.cpu().numpy(), rows)
+        got = v32[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        out["fp32_apply_rel_err_vs_oracle_rows"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    sp = out["solvers"]
+    if "plain" in sp:
+        for name in sp:
+            if name in ("plain",):
+                continue
+            off = 0 if name == "mixed" else args.train_steps
+            t_plain = sum(r["seconds"] for r in sp["plain"]["steps"][off:])
+            sp[name]["speedup_vs_plain_same_steps"] = t_plain / sp[name]["seconds"] if sp[name]["seconds"] else None
+    print(json.dumps(out), flush=True)
+    prob.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,11 +458,24 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--mode", choices=["apply", "newton"], default="apply")
+    ap.add_argument("--workload", default="q2_64_compress")
+    ap.add_argument("--solvers", default="plain,mixed,learned,mixed_learned")
+    ap.add_argument("--last-step", type=int, default=0)
+    ap.add_argument("--train-steps", type=int, default=5)
+    ap.add_argument("--synthetic", type=int, default=8)
+    ap.add_argument("--pairs", type=int, default=150)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--linear-rtol", type=float, default=1e-8)
+    ap.add_argument("--inner-rtol", type=float, default=1e-2)
+    ap.add_argument("--inner-max-iter", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "newton":
+        return run_newton(args)
     return run_gpu(args)
 
 
