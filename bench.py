@@ -467,8 +467,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=150)
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--linear-rtol", type=float, default=1e-8)
-    ap.add_argument("--inner-rtol", type=float, default=1e-2)
-    ap.add_argument("--inner-max-iter", type=int, default=200)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--inner-max-iter", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -143,8 +143,8 @@ typedef struct {
   int max_backtracks;   /* halvings of the Newton step on det F <= 0, default 8 */
   double linear_rtol;   /* default 1e-6 (relative to ||b||) */
   int linear_max_iter;  /* default 20000 */
-  double inner_rtol;    /* mixed: FP32 inner CG relative tolerance, default 1e-2 */
-  int inner_max_iter;   /* mixed: FP32 inner CG iteration cap, default 200 */
+  double inner_rtol;    /* mixed: FP32 inner CG relative tolerance, default 1e-3 */
+  int inner_max_iter;   /* mixed: FP32 inner CG iteration cap, default 1000 */
   int check_every;      /* iterations between host convergence reads, default 10 */
   int record_pairs;     /* JACOBI_CG with a U-Net: store training pairs (Newton (b, du) and CG
                            (r_j, x* - x_j)) in the network's pair store, default 0 */

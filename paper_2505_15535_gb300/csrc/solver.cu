@@ -444,8 +444,8 @@ void nhmf_solve_opts_default(nhmf_solve_opts* o) {
   o->max_backtracks = 8;
   o->linear_rtol = 1e-6;
   o->linear_max_iter = 20000;
-  o->inner_rtol = 1e-2;
-  o->inner_max_iter = 200;
+  o->inner_rtol = 1e-3;
+  o->inner_max_iter = 1000;
   o->check_every = 10;
   o->record_pairs = 0;
   o->cg_pair_every = 8;
