@@ -55,6 +55,13 @@ struct SolverWork {
   double* sc = nullptr;        // device scalars
   double* partials = nullptr;  // reduction scratch
   double* host = nullptr;      // pinned host scalar
+  cudaStream_t stream = nullptr;  // the solvers' own stream (graph capture needs a non-legacy stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // CUDA graphs of `check_every` CG iterations, keyed by the buffers they were captured with
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[16] = {};
+  } graph[2];  // [0] FP64, [1] FP32
 };
 }  // namespace nhmf
 

@@ -4,6 +4,7 @@
 // only every `check_every` iterations.
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "blas.h"
@@ -68,6 +69,10 @@ nhmf_status ensure_work(nhmf_ctx* c) {
   if (cudaMalloc(&w.partials, kPartialSlots * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "partials");
   if (cudaMallocHost(&w.host, 8 * sizeof(double)) != cudaSuccess) return fail(c, NHMF_ERR_OOM, "pinned scalar");
   cudaMemset(w.sc, 0, 64 * sizeof(double));
+  if (cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, NHMF_ERR_CUDA, "solver stream");
   return NHMF_OK;
 }
 
@@ -85,14 +90,69 @@ nhmf_status norm(Ctx& x, const double* v, int slot, double* out) {
   return read_scalar(x, x.w.sc + slot, out);
 }
 
-template <typename T> struct Prec;
-template <> struct Prec<double> { static constexpr int id = NHMF_FP64; };
-template <> struct Prec<float> { static constexpr int id = NHMF_FP32; };
-
 // Jacobi-preconditioned CG from x = 0 on A in precision T.  Scalars use slots base..base+4.
 struct NoSnap {
   void operator()(long long, const void*, const void*) const {}
 };
+
+template <typename T> struct Prec;
+template <> struct Prec<double> { static constexpr int id = NHMF_FP64; };
+template <> struct Prec<float> { static constexpr int id = NHMF_FP32; };
+
+// `chunk` (even) PCG iterations starting at an even iteration count, as plain launches.
+template <typename T>
+nhmf_status pcg_chunk(Ctx& x, int strat, T* sol, T* r, T* z, T* p, T* q, const T* dinv, double* rz0, double* rz1,
+                      double* pq, double* rr, int chunk) {
+  nhmf_status st = NHMF_OK;
+  double* rz[2] = {rz0, rz1};
+  for (int j = 0; j < chunk; ++j) {
+    if ((st = launch_apply(x.c, Prec<T>::id, strat, p, q, x.s)) != NHMF_OK) return st;
+    dot(x.n, p, q, pq, x.w.partials, x.s);
+    pcg_update<T>(x.n, rz[j & 1], pq, sol, r, p, q, dinv, z, rz[(j + 1) & 1], rr, x.w.partials, x.c->status, x.s);
+    pcg_direction<T>(x.n, rz[(j + 1) & 1], rz[j & 1], z, p, x.s);
+  }
+  return st;
+}
+
+// The CUDA graph of one chunk for these buffers (captured on first use and whenever a buffer
+// or the linearisation state changed); null if capture is not possible.
+template <typename T>
+cudaGraphExec_t chunk_graph(Ctx& x, int strat, T* sol, T* r, T* z, T* p, T* q, const T* dinv, double* rz0,
+                            double* rz1, double* pq, double* rr, int chunk) {
+  nhmf_ctx* c = x.c;
+  SolverWork::Graph& G = x.w.graph[sizeof(T) == 4 ? 1 : 0];
+  const void* key[16] = {sol, r, z, p, q, dinv, rz0, rz1, pq, rr, (const void*)(long long)chunk,
+                         (const void*)(long long)strat, c->ubar, c->ubar32, c->cache64, c->cache32};
+  bool same = G.exec != nullptr;
+  for (int i = 0; i < 16 && same; ++i) same = G.key[i] == key[i];
+  if (same) return G.exec;
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(x.s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const nhmf_status st = pcg_chunk<T>(x, strat, sol, r, z, p, q, dinv, rz0, rz1, pq, rr, chunk);
+  const cudaError_t e = cudaStreamEndCapture(x.s, &graph);
+  if (st != NHMF_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  G.exec = exec;
+  for (int i = 0; i < 16; ++i) G.key[i] = key[i];
+  return exec;
+}
 
 template <typename T, class Snap = NoSnap>
 nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z, T* p, T* q, double rtol,
@@ -116,6 +176,22 @@ nhmf_status pcg(Ctx& x, int strat, const T* b, T* sol, const T* dinv, T* r, T* z
   pcg_direction<T>(x.n, rz[0], nullptr, z, p, x.s);
   long long k = 0;
   double rrh = bnh * bnh;
+  // chunks of check_every iterations replay one CUDA graph (not while recording snapshots)
+  const bool graphs = std::is_same<Snap, NoSnap>::value && !c->profiling && check_every % 2 == 0;
+  while (graphs && k + check_every <= maxit) {
+    cudaGraphExec_t exec = chunk_graph<T>(x, strat, sol, r, z, p, q, dinv, rz[0], rz[1], pq, rr, check_every);
+    if (!exec) break;
+    if ((st = cuda_check(c, cudaGraphLaunch(exec, x.s), "pcg graph")) != NHMF_OK) return st;
+    k += check_every;
+    if ((st = read_scalar(x, rr, &rrh)) != NHMF_OK) return st;
+    if (!std::isfinite(rrh)) return fail(c, NHMF_ERR_NONFINITE, "pcg: non-finite residual");
+    if (std::sqrt(rrh) <= rtol * bnh) {
+      *iters = k;
+      *relres = std::sqrt(rrh) / bnh;
+      return nhmf_check_status(c, x.s);
+    }
+  }
+  if (k % 2 == 1) std::swap(rz[0], rz[1]);  // keep the parity convention below
   while (k < maxit) {
     if ((st = launch_apply(c, Prec<T>::id, strat, p, q, x.s)) != NHMF_OK) return st;
     dot(x.n, p, q, pq, x.w.partials, x.s);
@@ -421,6 +497,11 @@ void free_work(nhmf_ctx* c) {
                   w.r32, w.z32, w.p32, w.q32, w.x32, w.b32, w.dinv32, w.sc, w.partials};
   for (void* p : ptrs) cudaFree(p);
   if (w.host) cudaFreeHost(w.host);
+  for (auto& G : w.graph)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (w.ev_in) cudaEventDestroy(w.ev_in);
+  if (w.ev_out) cudaEventDestroy(w.ev_out);
+  if (w.stream) cudaStreamDestroy(w.stream);
   delete c->work;
   c->work = nullptr;
 }
@@ -465,22 +546,30 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   if (o->strategy == NHMF_CACHED && (!c->cache64 || ((cache_mask(*o) & NHMF_CACHE_FP32) && !c->cache32)))
     return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
   if ((st = ensure_work(c)) != NHMF_OK) return st;
-  Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
-  if ((st = update_diagonal(x)) != NHMF_OK) return st;
+  Ctx x{c, c->work->stream, 3 * c->g.M3, *c->work};
+  cudaEventRecord(x.w.ev_in, static_cast<cudaStream_t>(stream));
+  cudaStreamWaitEvent(x.s, x.w.ev_in, 0);
+  auto finish = [&](nhmf_status v) {
+    cudaEventRecord(x.w.ev_out, x.s);
+    cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), x.w.ev_out, 0);
+    cudaStreamSynchronize(x.s);
+    return v;
+  };
+  if ((st = update_diagonal(x)) != NHMF_OK) return finish(st);
   double rel = 0.0;
   int fb = 0;
-  if ((st = linear(x, *o, b, xsol, iters, inner_iters, &rel, &fb)) != NHMF_OK) return st;
+  if ((st = linear(x, *o, b, xsol, iters, inner_iters, &rel, &fb)) != NHMF_OK) return finish(st);
   // true residual with an FP64 apply
-  if ((st = launch_apply(c, NHMF_FP64, o->strategy, xsol, x.w.t, x.s)) != NHMF_OK) return st;
+  if ((st = launch_apply(c, NHMF_FP64, o->strategy, xsol, x.w.t, x.s)) != NHMF_OK) return finish(st);
   axpby(x.n, 1.0, nullptr, b, -1.0, nullptr, x.w.t, x.s);
   double rn, bn;
-  if ((st = norm(x, x.w.t, TMP, &rn)) != NHMF_OK) return st;
-  if ((st = norm(x, b, TMP, &bn)) != NHMF_OK) return st;
+  if ((st = norm(x, x.w.t, TMP, &rn)) != NHMF_OK) return finish(st);
+  if ((st = norm(x, b, TMP, &bn)) != NHMF_OK) return finish(st);
   *rel_res = bn > 0 ? rn / bn : 0.0;
-  return NHMF_OK;
+  return finish(NHMF_OK);
 }
 
-nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_solve_stats* stats, void* stream) {
+static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_solve_stats* stats) {
   using clk = std::chrono::steady_clock;
   if (!c) return NHMF_ERR_ARG;
   nhmf_status st = check_opts(c, o);
@@ -492,7 +581,7 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
   if (first > last || last > S || last - first + 1 > NHMF_MAX_STEPS) return fail(c, NHMF_ERR_ARG, "solve: bad step range");
   if ((st = ensure_work(c)) != NHMF_OK) return st;
   *stats = nhmf_solve_stats{};
-  Ctx x{c, static_cast<cudaStream_t>(stream), 3 * c->g.M3, *c->work};
+  Ctx x{c, c->work->stream, 3 * c->g.M3, *c->work};
   SolverWork& w = x.w;
   const long long M2 = (long long)c->g.M * c->g.M;
   const unsigned bc_blocks = (unsigned)((M2 + 255) / 256);
@@ -576,4 +665,19 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
   return NHMF_OK;
 }
 
+}
+
+nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_solve_stats* stats, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  nhmf_status st = ensure_work(c);
+  if (st != NHMF_OK) return st;
+  // the solver runs on the context's own stream, ordered after the caller's stream
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(c->work->ev_in, cs);
+  cudaStreamWaitEvent(c->work->stream, c->work->ev_in, 0);
+  st = solve_impl(c, o, u, stats);
+  cudaEventRecord(c->work->ev_out, c->work->stream);
+  cudaStreamWaitEvent(cs, c->work->ev_out, 0);
+  cudaStreamSynchronize(c->work->stream);
+  return st;
 }  // extern "C"
