@@ -448,6 +448,75 @@ def run_newton(args):
     return 0
 
 
+# ------------------------------------------------------------------ U-Net mode
+def unet_flops(M):
+    """Algorithmic FLOPs of one forward pass on an M^3 grid: 2 * 27 * c_in * c_out per output
+    voxel of each stride-1 and stride-2 convolution, and per coarse input voxel of each
+    transposed convolution (the channel counts the network defines; 3-channel ends counted
+    at 3)."""
+    M1 = (M - 1) // 2 + 1
+    M2 = (M1 - 1) // 2 + 1
+    v0, v1, v2 = M ** 3, M1 ** 3, M2 ** 3
+    macs = 27 * (v0 * 3 * 16 + v0 * 256 + v1 * 256 + v1 * 256 + v2 * 256 + v2 * 256 + v2 * 256 +
+                 v1 * 256 + v1 * 256 + v0 * 256 + v0 * 16 * 3)
+    return 2.0 * macs
+
+
+def run_unet(args):
+    """Forward pass and one training step (forward, loss, backward, Adam) of the U-Net on the
+    Q2 64^3 nodal grid (129^3), timed with CUDA events over `steps` repetitions."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2505_15535_gb300 import nhmf
+    w = inp.WORKLOADS["q2_64_compress"]
+    M = w.n_nodes_1d
+    dev = torch.device("cuda", 0)
+    prob = nhmf.Problem(w.n_el, w.degree, w.mu, w.lam, w.bc)
+    nhmf.nhmf_unet_create(prob.ctx, 1)
+    nhmf.nhmf_unet_set_params(prob.ctx, he_init_flat())
+    x = torch.from_numpy(inp.normal(31, w.n_dofs)).to(dev)
+    e = torch.from_numpy(inp.normal(32, w.n_dofs)).to(dev)
+    nhmf.nhmf_unet_record_pair(prob.ctx, x, e)
+    xf = x.float()
+    y = torch.empty_like(xf)
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        nhmf.nhmf_unet_forward(prob.ctx, xf, y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(args.steps):
+        nhmf.nhmf_unet_forward(prob.ctx, xf, y)
+    b.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / args.steps
+    t0 = time.perf_counter()
+    nhmf.nhmf_unet_train(prob.ctx, args.steps, 1e-4)
+    torch.cuda.synchronize()
+    train_ms = (time.perf_counter() - t0) / args.steps * 1e3
+    fl = unet_flops(M)
+    peak = MEASURED.get("bf16_tflops")
+    out = {"mode": "unet", "grid": f"{M}^3 (Q2 64^3 nodes)", "forward_ms": fwd_ms,
+           "forward_tflops": fl / (fwd_ms * 1e-3) / 1e12, "train_step_ms": train_ms,
+           "train_tflops": 3 * fl / (train_ms * 1e-3) / 1e12, "flops_forward": fl,
+           "bf16_peak_tflops_measured": peak,
+           "forward_frac_of_bf16_peak": (fl / (fwd_ms * 1e-3) / 1e12 / peak) if peak else None}
+    print(json.dumps(out), flush=True)
+    prob.close()
+    return 0
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+MEASURED = _measured_peaks()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,7 +527,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["apply", "newton"], default="apply")
+    ap.add_argument("--mode", choices=["apply", "newton", "unet"], default="apply")
     ap.add_argument("--workload", default="q2_64_compress")
     ap.add_argument("--solvers", default="plain,mixed,learned,mixed_learned")
     ap.add_argument("--last-step", type=int, default=0)
@@ -476,6 +545,8 @@ def main():
         return run_reference(args)
     if args.mode == "newton":
         return run_newton(args)
+    if args.mode == "unet":
+        return run_unet(args)
     return run_gpu(args)
 
 
