@@ -299,6 +299,18 @@ def run_gpu(args):
                         "gdofs": wv.n_dofs / (sm * 1e-3) / 1e9, "ms": sm, "kernel_ms": km,
                         "tflops": fl / (km * 1e-3) / 1e12, "alu_frac": fl / (km * 1e-3) / 1e12 / peak,
                         "hbm_gbs": bts / (km * 1e-3) / 1e9}
+            # FP64-accurate double-float arithmetic on the FP32 pipe (cached strategy)
+            x = dv
+            y = torch.empty_like(x)
+            for _ in range(3):
+                pv.apply(x, y, nhmf.NHMF_DF64, nhmf.NHMF_CACHED)
+            sm, km, _ = time_applies(torch, pv, nhmf, x, y, nhmf.NHMF_DF64, nhmf.NHMF_CACHED, vs, flush)
+            fl = canonical_flops(wv, "cached")
+            variants[f"{name}/df64/cached"] = {
+                "gdofs": wv.n_dofs / (sm * 1e-3) / 1e9, "ms": sm, "kernel_ms": km,
+                "tflops": fl / (km * 1e-3) / 1e12, "alu_frac": fl / (km * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                "hbm_gbs": compulsory_bytes(wv, "cached", 8) / (km * 1e-3) / 1e9,
+                "note": "alu_frac against the native FP64 peak (double-float runs on the FP32 pipe)"}
             if pv is not prob:
                 pv.close()
 

@@ -50,7 +50,7 @@ typedef enum {
   NHMF_ERR_STATE = 8          /* call out of order (e.g. apply before set_linearization) */
 } nhmf_status;
 
-enum { NHMF_FP64 = 0, NHMF_FP32 = 1 };                     /* arithmetic of an apply */
+enum { NHMF_FP64 = 0, NHMF_FP32 = 1, NHMF_DF64 = 2 };      /* arithmetic of an apply */
 enum { NHMF_ON_THE_FLY = 0, NHMF_CACHED = 1 };             /* the paper's two strategies */
 enum { NHMF_BC_NONE = 0, NHMF_BC_CLAMP_X0 = 1, NHMF_BC_COMPRESSION = 2 };
 enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2 };         /* bit mask for set_linearization */
@@ -91,7 +91,9 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mas
 
 /* v = A(u) du with u the current linearisation point (Algorithm 1 for NHMF_ON_THE_FLY, the
  * cached variant for NHMF_CACHED).  `precision` NHMF_FP64: du, v are double*; NHMF_FP32: du,
- * v are float* and all arithmetic after the cache build runs in FP32 with FP32 accumulation.
+ * v are float* and all arithmetic after the cache build runs in FP32 with FP32 accumulation;
+ * NHMF_DF64 (cached strategy only): du, v are double* and the arithmetic is double-float (pairs
+ * of FP32 numbers, about 48 significant bits) on the FP32 pipe, reading the FP64 point cache.
  * du and v are device arrays of 3*M^3 entries and must not overlap.  Asynchronous.
  * NHMF_ERR_STATE if no linearisation point (or no cache of that precision) is set. */
 nhmf_status nhmf_tangent_apply(nhmf_ctx* ctx, int precision, int strategy, const void* du,

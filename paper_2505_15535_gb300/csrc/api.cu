@@ -135,11 +135,13 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
 
 nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v, void* stream) {
   if (!c) return NHMF_ERR_ARG;
-  if (!du || !v || du == v || (precision != NHMF_FP64 && precision != NHMF_FP32) ||
+  if (!du || !v || du == v || (precision != NHMF_FP64 && precision != NHMF_FP32 && precision != NHMF_DF64) ||
       (strategy != NHMF_ON_THE_FLY && strategy != NHMF_CACHED))
     return fail(c, NHMF_ERR_ARG, "tangent_apply: bad argument");
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "tangent_apply: no linearisation point set");
-  if (strategy == NHMF_CACHED && ((precision == NHMF_FP64 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32)))
+  if (precision == NHMF_DF64 && strategy != NHMF_CACHED)
+    return fail(c, NHMF_ERR_ARG, "tangent_apply: NHMF_DF64 supports the cached strategy only");
+  if (strategy == NHMF_CACHED && ((precision != NHMF_FP32 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32)))
     return fail(c, NHMF_ERR_STATE, "tangent_apply: no point cache of this precision");
   return launch_apply(c, precision, strategy, du, v, as_stream(stream));
 }

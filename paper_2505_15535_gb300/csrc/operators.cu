@@ -8,6 +8,7 @@
 // classes run as eight launches in a fixed order.
 #include <algorithm>
 
+#include "df64.cuh"
 #include "sumfact.cuh"
 
 namespace nhmf {
@@ -52,9 +53,15 @@ __device__ __forceinline__ void gather(const OpArgs& a, const TS* __restrict__ s
   }
 }
 
+template <typename T> struct Store { using type = T; };
+template <> struct Store<df64> { using type = double; };
+__device__ __forceinline__ double to_store(double x) { return x; }
+__device__ __forceinline__ float to_store(float x) { return x; }
+__device__ __forceinline__ double to_store(df64 x) { return to_double(x); }
+
 template <int P, int NI, typename T>
 __device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long long e0, int nvalid,
-                                            T* __restrict__ out) {
+                                            typename Store<T>::type* __restrict__ out) {
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1);
   for (int t = threadIdx.x; t < NI; t += blockDim.x) {
     const int e = t / n3;
@@ -63,7 +70,7 @@ __device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long 
     item_node<P>(a, e0 + e, t % n3, gi, gj, gk);
     const long long node = gi + (long long)a.M * (gj + (long long)a.M * gk);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[c * a.M3 + node] += src[c * NI + t];
+    for (int c = 0; c < 3; ++c) out[c * a.M3 + node] += to_store(src[c * NI + t]);
   }
 }
 
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
   const T invh = T(1.0 / a.h);
 
-  if (STRAT == NHMF_ON_THE_FLY) {
+  if constexpr (STRAT == NHMF_ON_THE_FLY) {
     if (sizeof(T) == 8)
       gather<P, NI>(a, a.u64, e0, nvalid, false, G);
     else
@@ -118,18 +125,18 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
     __syncthreads();
     to_points<n, NI>(sB, G, Vq, U);
   }
-  gather<P, NI>(a, static_cast<const T*>(a.du), e0, nvalid, true, G);
+  gather<P, NI>(a, static_cast<const typename Store<T>::type*>(a.du), e0, nvalid, true, G);
   __syncthreads();
   to_points<n, NI>(sB, G, Vq + 0, Vq);  // in-place target is fine: passes ping-pong via G
   // (to_points(in=G, tmp=Vq, out=Vq): x: G->Vq, y: Vq->G, z: G->Vq)
 
   const T mu = T(a.mu), lam = T(a.lam);
-  const T* cache = static_cast<const T*>(a.cache);
+  const typename Store<T>::type* cache = static_cast<const typename Store<T>::type*>(a.cache);
   const long long cbase = (a.col.slot0 + e0) * n3;
   bool bad = false;
   for (int t = threadIdx.x; t < NI; t += blockDim.x) {
     T Fi[9], lnJ;
-    if (STRAT == NHMF_ON_THE_FLY) {
+    if constexpr (STRAT == NHMF_ON_THE_FLY) {
       T H[9];
       colloc_grad<n, NI>(sDc, U, t, H);
 #pragma unroll
@@ -138,15 +145,15 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       bad |= !(Jm1 > T(-1));
     } else {
       if (t / n3 < nvalid) {
-        if (sizeof(T) == 8 || P > 2) {
+        if (sizeof(typename Store<T>::type) == 8 || P > 2) {
 #pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = cache[k * a.nq + cbase + t];
-          lnJ = cache[9 * a.nq + cbase + t];
+          for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
+          lnJ = T(cache[9 * a.nq + cbase + t]);
         } else {
           const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = cache[(k * n3 + q) * E + slot];
-          lnJ = cache[(9 * n3 + q) * E + slot];
+          for (int k = 0; k < 9; ++k) Fi[k] = T(cache[(k * n3 + q) * E + slot]);
+          lnJ = T(cache[(9 * n3 + q) * E + slot]);
         }
       } else {
 #pragma unroll
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
   if (bad) atomicOr(a.status, kStatusNonPosJ);
   __syncthreads();
   from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
-  scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<T*>(a.v));
+  scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<typename Store<T>::type*>(a.v));
 }
 
 // ------------------------------------------------------------------ FP32 register kernel
@@ -653,6 +660,7 @@ nhmf_status fix_rows(nhmf_ctx* c, const T* src, T* out, int mode, T value, cudaS
 
 template <int P, typename T, int STRAT>
 nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t s) {
+  using S = typename Store<T>::type;
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, T>::NE, NI = NE * n3;
   OpArgs a = base_args(c);
   if (raw) a.bc = NHMF_BC_NONE;  // unconstrained operator K: no masking, no identity rows
@@ -663,7 +671,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   a.cache = sizeof(T) == 8 ? (const void*)c->cache64 : (const void*)c->cache32;
   const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;
   const size_t smem = slots * sizeof(T);
-  if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(T) * 3 * c->g.M3, s); e != cudaSuccess)
+  if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "apply memset");
   nhmf_status st;
   if constexpr (sizeof(T) == 4 && P <= 2)
@@ -671,11 +679,15 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   else
     st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
   if (st != NHMF_OK || raw) return st;
-  return fix_rows<T>(c, static_cast<const T*>(du), static_cast<T*>(v), 0, T(0), s);
+  return fix_rows<S>(c, static_cast<const S*>(du), static_cast<S*>(v), 0, S(0), s);
 }
 
 template <int P>
 nhmf_status apply_dispatch_p(nhmf_ctx* c, int prec, int strat, const void* du, void* v, bool raw, cudaStream_t s) {
+  if (prec == NHMF_DF64) {
+    if (strat != NHMF_CACHED) return fail(c, NHMF_ERR_ARG, "df64 apply: cached strategy only");
+    return apply_p<P, df64, NHMF_CACHED>(c, du, v, raw, s);
+  }
   if (prec == NHMF_FP64)
     return strat == NHMF_CACHED ? apply_p<P, double, NHMF_CACHED>(c, du, v, raw, s)
                                 : apply_p<P, double, NHMF_ON_THE_FLY>(c, du, v, raw, s);

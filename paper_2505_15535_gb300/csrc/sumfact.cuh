@@ -25,6 +25,8 @@ template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; 
 template <> struct Cfg<2, float> { static constexpr int NE = 32, THREADS = 288; };
 template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
+struct df64;
+template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
 
 // Kernel arguments (by value; lives in the constant bank).
 struct OpArgs {

@@ -41,6 +41,9 @@ def test_fp64_apply_both_strategies(nhmf, p, n_el, bc):
         v = cuda(np.zeros_like(u))
         prob.apply(dut, v, nhmf.NHMF_FP64, strat)
         assert rel_l2(host(v), ref) <= FP64_TOL, (strat, rel_l2(host(v), ref))
+    vdf = cuda(np.zeros_like(u))                  # double-float arithmetic: same FP64 bar
+    prob.apply(dut, vdf, nhmf.NHMF_DF64, nhmf.NHMF_CACHED)
+    assert rel_l2(host(vdf), ref) <= FP64_TOL, ("df64", rel_l2(host(vdf), ref))
     for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
         v32 = cuda(np.zeros(u.size, dtype=np.float32))
         prob.apply(cuda(du.astype(np.float32)), v32, nhmf.NHMF_FP32, strat)

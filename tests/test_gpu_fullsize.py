@@ -45,6 +45,9 @@ def test_fullsize_sampled_rows(name):
         prob.apply(dut.float(), v32, nhmf.NHMF_FP32, strat)
         got32 = host(v32[idx])
         assert np.linalg.norm(got32 - ref) <= 1e-5 * np.linalg.norm(ref)
+    vdf = torch.empty_like(dut)
+    prob.apply(dut, vdf, nhmf.NHMF_DF64, nhmf.NHMF_CACHED)
+    assert np.linalg.norm(host(vdf[idx]) - ref) <= 1e-12 * np.linalg.norm(ref)
     r = torch.empty_like(dut)
     prob.residual(cuda(u), r)
     assert np.linalg.norm(host(r[idx]) - rref) <= 1e-12 * np.linalg.norm(rref)
