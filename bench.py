@@ -221,7 +221,7 @@ def run_gpu(args):
     prob = nhmf.Problem.from_workload(w)
     ut = torch.from_numpy(u).to(dev)
     t0 = time.perf_counter()
-    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
     torch.cuda.synchronize()
     cache_build_s = time.perf_counter() - t0
     dut = torch.from_numpy(du).to(dev)
@@ -283,7 +283,7 @@ def run_gpu(args):
             else:
                 pv = nhmf.Problem.from_workload(wv)
                 pv.set_linearization(torch.from_numpy(inp.draw_u(wv)).to(dev),
-                                     nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+                                     nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
                 dv = torch.from_numpy(inp.draw_du(wv)).to(dev)
             for prec_name, prec, dt in (("fp64", nhmf.NHMF_FP64, torch.float64), ("fp32", nhmf.NHMF_FP32, torch.float32)):
                 x = dv.to(dt)

@@ -53,7 +53,7 @@ typedef enum {
 enum { NHMF_FP64 = 0, NHMF_FP32 = 1, NHMF_DF64 = 2 };      /* arithmetic of an apply */
 enum { NHMF_ON_THE_FLY = 0, NHMF_CACHED = 1 };             /* the paper's two strategies */
 enum { NHMF_BC_NONE = 0, NHMF_BC_CLAMP_X0 = 1, NHMF_BC_COMPRESSION = 2 };
-enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2 };         /* bit mask for set_linearization */
+enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2, NHMF_CACHE_DF64 = 4 }; /* bit mask for set_linearization */
 
 typedef struct nhmf_ctx nhmf_ctx;
 
@@ -83,7 +83,9 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * call) for later tangent/diagonal calls: copies u into the context and, for each bit of
  * `cache_mask`, builds the per-quadrature-point cache of the cached strategy (Section 3.2
  * "partial assembly"): F^-1 (9 values) and ln J (1 value) per point, computed in FP64 and
- * stored in FP64 (NHMF_CACHE_FP64) and/or FP32 (NHMF_CACHE_FP32); 10*E*(p+1)^3 values
+ * stored in FP64 (NHMF_CACHE_FP64), FP32 (NHMF_CACHE_FP32) and/or as double-float pairs
+ * (NHMF_CACHE_DF64, for the NHMF_DF64 apply, layout as FP64 with a (hi, lo) FP32 pair per
+ * value); 10*E*(p+1)^3 values
  * each, layout [10][E*(p+1)^3] with elements in colour-major order (the FP32 cache of p <= 2
  * is [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
  * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
@@ -93,7 +95,8 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mas
  * cached variant for NHMF_CACHED).  `precision` NHMF_FP64: du, v are double*; NHMF_FP32: du,
  * v are float* and all arithmetic after the cache build runs in FP32 with FP32 accumulation;
  * NHMF_DF64 (cached strategy only): du, v are double* and the arithmetic is double-float (pairs
- * of FP32 numbers, about 48 significant bits) on the FP32 pipe, reading the FP64 point cache.
+ * of FP32 numbers, about 48 significant bits) on the FP32 pipe, reading the NHMF_CACHE_DF64
+ * point cache.
  * du and v are device arrays of 3*M^3 entries and must not overlap.  Asynchronous.
  * NHMF_ERR_STATE if no linearisation point (or no cache of that precision) is set. */
 nhmf_status nhmf_tangent_apply(nhmf_ctx* ctx, int precision, int strategy, const void* du,

@@ -86,6 +86,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->ubar32);
   cudaFree(c->cache64);
   cudaFree(c->cache32);
+  cudaFree(c->cachedf);
   free_work(c);
   unet_free(c);
   delete c;
@@ -110,7 +111,7 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
 }
 
 nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void* stream) {
-  if (!c || !u || mask < 0 || mask > 3) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
+  if (!c || !u || mask < 0 || mask > 7) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
   cudaStream_t s = as_stream(stream);
   const size_t n = 3 * c->g.M3;
   c->have_lin = false;
@@ -123,6 +124,9 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
     if ((st = cuda_check(c, cudaMalloc(&c->cache64, cache_elems * sizeof(double)), "cache64 alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP32) && !c->cache32)
     if ((st = cuda_check(c, cudaMalloc(&c->cache32, cache_elems * sizeof(float)), "cache32 alloc")) != NHMF_OK) return st;
+  if ((mask & NHMF_CACHE_DF64) && !c->cachedf)
+    if ((st = cuda_check(c, cudaMalloc(&c->cachedf, cache_elems * sizeof(float2)), "cachedf alloc")) != NHMF_OK) return st;
+  if (!(mask & NHMF_CACHE_DF64) && c->cachedf) { cudaFree(c->cachedf); c->cachedf = nullptr; }
   if (!(mask & NHMF_CACHE_FP64) && c->cache64) { cudaFree(c->cache64); c->cache64 = nullptr; }
   if (!(mask & NHMF_CACHE_FP32) && c->cache32) { cudaFree(c->cache32); c->cache32 = nullptr; }
   if (mask) {
@@ -141,7 +145,8 @@ nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const v
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "tangent_apply: no linearisation point set");
   if (precision == NHMF_DF64 && strategy != NHMF_CACHED)
     return fail(c, NHMF_ERR_ARG, "tangent_apply: NHMF_DF64 supports the cached strategy only");
-  if (strategy == NHMF_CACHED && ((precision != NHMF_FP32 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32)))
+  if (strategy == NHMF_CACHED && ((precision == NHMF_FP64 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32) ||
+                                  (precision == NHMF_DF64 && !c->cachedf)))
     return fail(c, NHMF_ERR_STATE, "tangent_apply: no point cache of this precision");
   return launch_apply(c, precision, strategy, du, v, as_stream(stream));
 }

@@ -74,6 +74,7 @@ struct nhmf_ctx {
   float* ubar32 = nullptr;    // its FP32 copy (FP32 on-the-fly apply)
   double* cache64 = nullptr;  // [10][nq]
   float* cache32 = nullptr;   // [10][nq]
+  float2* cachedf = nullptr;  // [10][nq] (hi, lo) double-float pairs
   unsigned* status = nullptr; // device status word: bit 0 det F <= 0, bit 1 non-finite
   bool have_lin = false;
   std::string err;

@@ -7,6 +7,7 @@
 // so the read-modify-write scatter of a launch is race-free and deterministic.  The eight
 // classes run as eight launches in a fixed order.
 #include <algorithm>
+#include <type_traits>
 
 #include "df64.cuh"
 #include "sumfact.cuh"
@@ -145,7 +146,16 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       bad |= !(Jm1 > T(-1));
     } else {
       if (t / n3 < nvalid) {
-        if (sizeof(typename Store<T>::type) == 8 || P > 2) {
+        if constexpr (std::is_same<T, df64>::value) {
+          const float2* cdf = static_cast<const float2*>(a.cache);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const float2 z = cdf[k * a.nq + cbase + t];
+            Fi[k] = T(z.x, z.y);
+          }
+          const float2 z = cdf[9 * a.nq + cbase + t];
+          lnJ = T(z.x, z.y);
+        } else if (sizeof(typename Store<T>::type) == 8 || P > 2) {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
           lnJ = T(cache[9 * a.nq + cbase + t]);
@@ -422,6 +432,15 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       for (int k = 0; k < 9; ++k) a.cache64_out[k * a.nq + cbase + t] = Fi[k];
       a.cache64_out[9 * a.nq + cbase + t] = lnJ;
     }
+    if (a.cachedf_out) {
+      auto split = [](double d) {
+        const float hi = __double2float_rn(d);
+        return make_float2(hi, __double2float_rn(d - (double)hi));
+      };
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a.cachedf_out[k * a.nq + cbase + t] = split(Fi[k]);
+      a.cachedf_out[9 * a.nq + cbase + t] = split(lnJ);
+    }
     if (a.cache32_out) {
       if (P <= 2) {
         // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
@@ -668,7 +687,8 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   a.u32 = c->ubar32;
   a.du = du;
   a.v = v;
-  a.cache = sizeof(T) == 8 ? (const void*)c->cache64 : (const void*)c->cache32;
+  a.cache = std::is_same<T, df64>::value ? (const void*)c->cachedf
+            : (sizeof(T) == 8 ? (const void*)c->cache64 : (const void*)c->cache32);
   const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;
   const size_t smem = slots * sizeof(T);
   if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
@@ -702,6 +722,7 @@ nhmf_status cache_p(nhmf_ctx* c, cudaStream_t s) {
   a.u64 = c->ubar;
   a.cache64_out = c->cache64;
   a.cache32_out = c->cache32;
+  a.cachedf_out = c->cachedf;
   const size_t smem = (kTabSlots + 6 * (size_t)NI) * sizeof(double);
   return run_colours(c, k_cache<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "cache build", NHMF_KIND_CACHE);
 }

@@ -43,6 +43,7 @@ struct OpArgs {
   const void* cache;
   double* cache64_out;
   float* cache32_out;
+  float2* cachedf_out;
   unsigned* status;
 };
 

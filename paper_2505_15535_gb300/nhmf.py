@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONP
 NHMF_FP64, NHMF_FP32, NHMF_DF64 = 0, 1, 2
 NHMF_ON_THE_FLY, NHMF_CACHED = 0, 1
 NHMF_BC_NONE, NHMF_BC_CLAMP_X0, NHMF_BC_COMPRESSION = 0, 1, 2
-NHMF_CACHE_FP64, NHMF_CACHE_FP32 = 1, 2
+NHMF_CACHE_FP64, NHMF_CACHE_FP32, NHMF_CACHE_DF64 = 1, 2, 4
 NHMF_KIND_APPLY, NHMF_KIND_CACHE, NHMF_KIND_RESIDUAL, NHMF_KIND_DIAGONAL = 0, 1, 2, 3
 
 

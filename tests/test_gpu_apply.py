@@ -35,7 +35,7 @@ def test_fp64_apply_both_strategies(nhmf, p, n_el, bc):
     op = Operator(Mesh(n_el, p), w.mu, w.lam, bc)
     ref = op.apply(u, du)
     prob = nhmf.Problem.from_workload(w)
-    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
     dut = cuda(du)
     for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
         v = cuda(np.zeros_like(u))
@@ -109,7 +109,7 @@ def test_bitwise_determinism(nhmf):
     import torch
     w, u, du = case(6, 2, 1)
     prob = nhmf.Problem.from_workload(w)
-    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
     for prec, dt in ((nhmf.NHMF_FP64, np.float64), (nhmf.NHMF_FP32, np.float32)):
         for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
             dut = cuda(du.astype(dt))

@@ -33,7 +33,7 @@ def test_fullsize_sampled_rows(name):
     ref = op.apply_rows(u, du, rows)
     rref = op.residual_rows(u, rows)
     prob = nhmf.Problem.from_workload(w)
-    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
     dut = cuda(du)
     idx = torch.from_numpy(rows).to("cuda:0")
     for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
