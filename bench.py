@@ -221,7 +221,8 @@ def run_gpu(args):
     prob = nhmf.Problem.from_workload(w)
     ut = torch.from_numpy(u).to(dev)
     t0 = time.perf_counter()
-    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
+    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
+                           nhmf.NHMF_CACHE_SPATIAL)
     torch.cuda.synchronize()
     cache_build_s = time.perf_counter() - t0
     dut = torch.from_numpy(du).to(dev)
@@ -283,7 +284,8 @@ def run_gpu(args):
             else:
                 pv = nhmf.Problem.from_workload(wv)
                 pv.set_linearization(torch.from_numpy(inp.draw_u(wv)).to(dev),
-                                     nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
+                                     nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
+                                     nhmf.NHMF_CACHE_SPATIAL)
                 dv = torch.from_numpy(inp.draw_du(wv)).to(dev)
             for prec_name, prec, dt in (("fp64", nhmf.NHMF_FP64, torch.float64), ("fp32", nhmf.NHMF_FP32, torch.float32)):
                 x = dv.to(dt)
@@ -299,6 +301,18 @@ def run_gpu(args):
                         "gdofs": wv.n_dofs / (sm * 1e-3) / 1e9, "ms": sm, "kernel_ms": km,
                         "tflops": fl / (km * 1e-3) / 1e12, "alu_frac": fl / (km * 1e-3) / 1e12 / peak,
                         "hbm_gbs": bts / (km * 1e-3) / 1e9}
+            # Algorithm 2 (partial assembly in the current configuration), FP64
+            x = dv
+            y = torch.empty_like(x)
+            for _ in range(3):
+                pv.apply(x, y, nhmf.NHMF_FP64, nhmf.NHMF_SPATIAL)
+            sm, km, _ = time_applies(torch, pv, nhmf, x, y, nhmf.NHMF_FP64, nhmf.NHMF_SPATIAL, vs, flush)
+            n = wv.degree + 1
+            fl = wv.n_elements * 36 * 2 * n ** 4 + wv.n_qp * 260
+            variants[f"{name}/fp64/spatial"] = {
+                "gdofs": wv.n_dofs / (sm * 1e-3) / 1e9, "ms": sm, "kernel_ms": km,
+                "tflops": fl / (km * 1e-3) / 1e12, "alu_frac": fl / (km * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                "hbm_gbs": (2 * 8 * wv.n_dofs + 36 * 8 * wv.n_qp) / (km * 1e-3) / 1e9}
             # FP64-accurate double-float arithmetic on the FP32 pipe (cached strategy)
             x = dv
             y = torch.empty_like(x)

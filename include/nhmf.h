@@ -51,9 +51,10 @@ typedef enum {
 } nhmf_status;
 
 enum { NHMF_FP64 = 0, NHMF_FP32 = 1, NHMF_DF64 = 2 };      /* arithmetic of an apply */
-enum { NHMF_ON_THE_FLY = 0, NHMF_CACHED = 1 };             /* the paper's two strategies */
+enum { NHMF_ON_THE_FLY = 0, NHMF_CACHED = 1, NHMF_SPATIAL = 2 }; /* point-code strategies */
 enum { NHMF_BC_NONE = 0, NHMF_BC_CLAMP_X0 = 1, NHMF_BC_COMPRESSION = 2 };
-enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2, NHMF_CACHE_DF64 = 4 }; /* bit mask for set_linearization */
+enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2, NHMF_CACHE_DF64 = 4, NHMF_CACHE_SPATIAL = 8 };
+/* bit mask for set_linearization */
 
 typedef struct nhmf_ctx nhmf_ctx;
 
@@ -85,14 +86,20 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * "partial assembly"): F^-1 (9 values) and ln J (1 value) per point, computed in FP64 and
  * stored in FP64 (NHMF_CACHE_FP64), FP32 (NHMF_CACHE_FP32) and/or as double-float pairs
  * (NHMF_CACHE_DF64, for the NHMF_DF64 apply, layout as FP64 with a (hi, lo) FP32 pair per
- * value); 10*E*(p+1)^3 values
+ * value) and/or the 36-value FP64 cache of NHMF_SPATIAL (NHMF_CACHE_SPATIAL: J c in Voigt
+ * order 11, 22, 33, 23, 13, 12 as the upper triangle of a 6x6 matrix (21), tau (6, Voigt),
+ * F^-1 (9, row-major); layout [36][E*(p+1)^3]); 10*E*(p+1)^3 values
  * each, layout [10][E*(p+1)^3] with elements in colour-major order (the FP32 cache of p <= 2
  * is [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
  * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
 nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
 
-/* v = A(u) du with u the current linearisation point (Algorithm 1 for NHMF_ON_THE_FLY, the
- * cached variant for NHMF_CACHED).  `precision` NHMF_FP64: du, v are double*; NHMF_FP32: du,
+/* v = A(u) du with u the current linearisation point.  Strategies: NHMF_ON_THE_FLY
+ * (Algorithm 1: F, F^-1, ln J recomputed at every point), NHMF_CACHED (F^-1 and ln J read from
+ * the point cache), NHMF_SPATIAL (Algorithm 2, partial assembly in the current configuration,
+ * Eq. DF:cur: per point J c (21 values, minor and major symmetry), the Kirchhoff stress
+ * tau = J sigma (6) and F^-1 (9) are read from the NHMF_CACHE_SPATIAL cache, and
+ * G = [J c : sym(grad du) + grad du tau] F^-T with grad du = Grad du F^-1; FP64 only).  `precision` NHMF_FP64: du, v are double*; NHMF_FP32: du,
  * v are float* and all arithmetic after the cache build runs in FP32 with FP32 accumulation;
  * NHMF_DF64 (cached strategy only): du, v are double* and the arithmetic is double-float (pairs
  * of FP32 numbers, about 48 significant bits) on the FP32 pipe, reading the NHMF_CACHE_DF64

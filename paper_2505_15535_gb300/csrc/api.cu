@@ -87,6 +87,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->cache64);
   cudaFree(c->cache32);
   cudaFree(c->cachedf);
+  cudaFree(c->cachesp);
   free_work(c);
   unet_free(c);
   delete c;
@@ -111,7 +112,7 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
 }
 
 nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void* stream) {
-  if (!c || !u || mask < 0 || mask > 7) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
+  if (!c || !u || mask < 0 || mask > 15) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
   cudaStream_t s = as_stream(stream);
   const size_t n = 3 * c->g.M3;
   c->have_lin = false;
@@ -124,6 +125,10 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
     if ((st = cuda_check(c, cudaMalloc(&c->cache64, cache_elems * sizeof(double)), "cache64 alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP32) && !c->cache32)
     if ((st = cuda_check(c, cudaMalloc(&c->cache32, cache_elems * sizeof(float)), "cache32 alloc")) != NHMF_OK) return st;
+  if ((mask & NHMF_CACHE_SPATIAL) && !c->cachesp)
+    if ((st = cuda_check(c, cudaMalloc(&c->cachesp, 36 * (size_t)c->g.nq * sizeof(double)), "cachesp alloc")) != NHMF_OK)
+      return st;
+  if (!(mask & NHMF_CACHE_SPATIAL) && c->cachesp) { cudaFree(c->cachesp); c->cachesp = nullptr; }
   if ((mask & NHMF_CACHE_DF64) && !c->cachedf)
     if ((st = cuda_check(c, cudaMalloc(&c->cachedf, cache_elems * sizeof(float2)), "cachedf alloc")) != NHMF_OK) return st;
   if (!(mask & NHMF_CACHE_DF64) && c->cachedf) { cudaFree(c->cachedf); c->cachedf = nullptr; }
@@ -140,8 +145,12 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
 nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const void* du, void* v, void* stream) {
   if (!c) return NHMF_ERR_ARG;
   if (!du || !v || du == v || (precision != NHMF_FP64 && precision != NHMF_FP32 && precision != NHMF_DF64) ||
-      (strategy != NHMF_ON_THE_FLY && strategy != NHMF_CACHED))
+      (strategy != NHMF_ON_THE_FLY && strategy != NHMF_CACHED && strategy != NHMF_SPATIAL))
     return fail(c, NHMF_ERR_ARG, "tangent_apply: bad argument");
+  if (strategy == NHMF_SPATIAL && precision != NHMF_FP64)
+    return fail(c, NHMF_ERR_ARG, "tangent_apply: NHMF_SPATIAL is FP64 only");
+  if (strategy == NHMF_SPATIAL && !c->cachesp)
+    return fail(c, NHMF_ERR_STATE, "tangent_apply: no NHMF_CACHE_SPATIAL cache");
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "tangent_apply: no linearisation point set");
   if (precision == NHMF_DF64 && strategy != NHMF_CACHED)
     return fail(c, NHMF_ERR_ARG, "tangent_apply: NHMF_DF64 supports the cached strategy only");

@@ -136,6 +136,32 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
   const long long cbase = (a.col.slot0 + e0) * n3;
   bool bad = false;
   for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    if constexpr (STRAT == NHMF_SPATIAL) {
+      // Algorithm 2: J c, tau and F^-1 from the 36-value cache
+      T Jc[21], tau[6], Fs[9];
+      if (t / n3 < nvalid) {
+        const double* sp = a.cachesp_in;
+#pragma unroll
+        for (int k = 0; k < 21; ++k) Jc[k] = T(sp[k * a.nq + cbase + t]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tau[k] = T(sp[(21 + k) * a.nq + cbase + t]);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fs[k] = T(sp[(27 + k) * a.nq + cbase + t]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 21; ++k) Jc[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tau[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fs[k] = (k % 4 == 0) ? T(1) : T(0);
+      }
+      T dH[9], g[9];
+      colloc_grad<n, NI>(sDc, Vq, t, dH);
+      spatial_stress(Jc, tau, Fs, dH, sW[t % n3], g);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
+      continue;
+    }
     T Fi[9], lnJ;
     if constexpr (STRAT == NHMF_ON_THE_FLY) {
       T H[9];
@@ -432,6 +458,47 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       for (int k = 0; k < 9; ++k) a.cache64_out[k * a.nq + cbase + t] = Fi[k];
       a.cache64_out[9 * a.nq + cbase + t] = lnJ;
     }
+    if (a.cachesp_out) {
+      // Algorithm 2 cache from the model's P and dP only: tau = P F^T;
+      // J a_ijkl = (dP[e_k (x) F_l.] F^T)_ij, J c_ijkl = J a_ijkl - delta_ik tau_jl
+      double F[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.0 : 0.0) + H[k];
+      double P[9], tau[9];
+      const double c2 = 2.0 * a.lam * lnJ - a.mu;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) P[3 * i + J] = fma(a.mu, F[3 * i + J], c2 * Fi[3 * J + i]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          tau[3 * i + j] = fma(P[3 * i], F[3 * j], fma(P[3 * i + 1], F[3 * j + 1], P[3 * i + 2] * F[3 * j + 2]));
+      double* out = a.cachesp_out;
+      const int pk[6] = {0, 1, 2, 1, 0, 0}, pl[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+      for (int K = 0; K < 6; ++K) {
+        const int k = pk[K], l = pl[K];
+        double X[9], dP[9];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int L = 0; L < 3; ++L) X[3 * m + L] = (m == k) ? F[3 * l + L] : 0.0;
+        linearised_stress(Fi, lnJ, X, a.mu, a.lam, 1.0, dP);
+#pragma unroll
+        for (int I = 0; I <= K; ++I) {
+          const int i = pk[I], j = pl[I];
+          const double Ja = fma(dP[3 * i], F[3 * j], fma(dP[3 * i + 1], F[3 * j + 1], dP[3 * i + 2] * F[3 * j + 2]));
+          out[tri6(I, K) * a.nq + cbase + t] = Ja - (i == k ? tau[3 * j + l] : 0.0);
+        }
+      }
+      const int vi[6] = {0, 4, 8, 5, 2, 1};  // tau in Voigt order 11, 22, 33, 23, 13, 12
+#pragma unroll
+      for (int V = 0; V < 6; ++V) out[(21 + V) * a.nq + cbase + t] = tau[vi[V]];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[(27 + k) * a.nq + cbase + t] = Fi[k];
+    }
     if (a.cachedf_out) {
       auto split = [](double d) {
         const float hi = __double2float_rn(d);
@@ -689,7 +756,8 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   a.v = v;
   a.cache = std::is_same<T, df64>::value ? (const void*)c->cachedf
             : (sizeof(T) == 8 ? (const void*)c->cache64 : (const void*)c->cache32);
-  const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;
+  a.cachesp_in = c->cachesp;
+  const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;  // spatial: as cached
   const size_t smem = slots * sizeof(T);
   if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "apply memset");
@@ -708,9 +776,11 @@ nhmf_status apply_dispatch_p(nhmf_ctx* c, int prec, int strat, const void* du, v
     if (strat != NHMF_CACHED) return fail(c, NHMF_ERR_ARG, "df64 apply: cached strategy only");
     return apply_p<P, df64, NHMF_CACHED>(c, du, v, raw, s);
   }
-  if (prec == NHMF_FP64)
+  if (prec == NHMF_FP64) {
+    if (strat == NHMF_SPATIAL) return apply_p<P, double, NHMF_SPATIAL>(c, du, v, raw, s);
     return strat == NHMF_CACHED ? apply_p<P, double, NHMF_CACHED>(c, du, v, raw, s)
                                 : apply_p<P, double, NHMF_ON_THE_FLY>(c, du, v, raw, s);
+  }
   return strat == NHMF_CACHED ? apply_p<P, float, NHMF_CACHED>(c, du, v, raw, s)
                               : apply_p<P, float, NHMF_ON_THE_FLY>(c, du, v, raw, s);
 }
@@ -723,6 +793,7 @@ nhmf_status cache_p(nhmf_ctx* c, cudaStream_t s) {
   a.cache64_out = c->cache64;
   a.cache32_out = c->cache32;
   a.cachedf_out = c->cachedf;
+  a.cachesp_out = c->cachesp;
   const size_t smem = (kTabSlots + 6 * (size_t)NI) * sizeof(double);
   return run_colours(c, k_cache<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "cache build", NHMF_KIND_CACHE);
 }

@@ -44,6 +44,8 @@ struct OpArgs {
   double* cache64_out;
   float* cache32_out;
   float2* cachedf_out;
+  double* cachesp_out;
+  const double* cachesp_in;
   unsigned* status;
 };
 
@@ -200,6 +202,48 @@ __device__ __forceinline__ void linearised_stress(const T Fi[9], T lnJ, const T 
       const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
       g[3 * i + j] = fma(smu, dH[3 * i + j], fma(sc1, Qji, sc2 * Fi[3 * j + i]));
     }
+}
+
+// Voigt index of the pair (i, j): 11, 22, 33, 23, 13, 12 -> 0..5.
+__host__ __device__ constexpr int voigt(int i, int j) {
+  return i == j ? i : (i + j == 3 ? 3 : (i + j == 2 ? 4 : 5));
+}
+// Index of (I, K), I <= K, in the row-major upper triangle of a 6x6 matrix.
+__host__ __device__ constexpr int tri6(int I, int K) { return I * 6 - I * (I - 1) / 2 + (K - I); }
+
+// Algorithm 2 point code (current configuration, Eq. DF:cur), scaled by s:
+//   g = dH F^-1 (spatial gradient), e_hat = (g00, g11, g22, g12+g21, g02+g20, g01+g10),
+//   sig_I = sum_K Jc[I][K] e_hat_K (J c : sym(g)), X = sig + g tau, G = s X F^-T.
+template <typename T>
+__device__ __forceinline__ void spatial_stress(const T Jc[21], const T tau[6], const T Fi[9], const T dH[9], T s,
+                                               T out[9]) {
+  T gs[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      gs[3 * k + l] = fma(dH[3 * k + 0], Fi[l], fma(dH[3 * k + 1], Fi[3 + l], dH[3 * k + 2] * Fi[6 + l]));
+  const T eh[6] = {gs[0], gs[4], gs[8], gs[5] + gs[7], gs[2] + gs[6], gs[1] + gs[3]};
+  T sv[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    T acc = T(0);
+#pragma unroll
+    for (int K = 0; K < 6; ++K) acc = fma(Jc[I <= K ? tri6(I, K) : tri6(K, I)], eh[K], acc);
+    sv[I] = acc;
+  }
+  T X[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      X[3 * i + j] = fma(gs[3 * i + 0], tau[voigt(0, j)],
+                         fma(gs[3 * i + 1], tau[voigt(1, j)], fma(gs[3 * i + 2], tau[voigt(2, j)], sv[voigt(i, j)])));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+      out[3 * i + J] = s * fma(X[3 * i + 0], Fi[3 * J + 0], fma(X[3 * i + 1], Fi[3 * J + 1], X[3 * i + 2] * Fi[3 * J + 2]));
 }
 
 }  // namespace nhmf

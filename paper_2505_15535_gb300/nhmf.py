@@ -16,9 +16,9 @@ NHMF_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPOS_J",
                 5: "ERR_NONFINITE", 6: "ERR_BREAKDOWN", 7: "ERR_NOT_CONVERGED", 8: "ERR_STATE"}
 NHMF_FP64, NHMF_FP32, NHMF_DF64 = 0, 1, 2
-NHMF_ON_THE_FLY, NHMF_CACHED = 0, 1
+NHMF_ON_THE_FLY, NHMF_CACHED, NHMF_SPATIAL = 0, 1, 2
 NHMF_BC_NONE, NHMF_BC_CLAMP_X0, NHMF_BC_COMPRESSION = 0, 1, 2
-NHMF_CACHE_FP64, NHMF_CACHE_FP32, NHMF_CACHE_DF64 = 1, 2, 4
+NHMF_CACHE_FP64, NHMF_CACHE_FP32, NHMF_CACHE_DF64, NHMF_CACHE_SPATIAL = 1, 2, 4, 8
 NHMF_KIND_APPLY, NHMF_KIND_CACHE, NHMF_KIND_RESIDUAL, NHMF_KIND_DIAGONAL = 0, 1, 2, 3
 
 

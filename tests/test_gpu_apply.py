@@ -35,9 +35,10 @@ def test_fp64_apply_both_strategies(nhmf, p, n_el, bc):
     op = Operator(Mesh(n_el, p), w.mu, w.lam, bc)
     ref = op.apply(u, du)
     prob = nhmf.Problem.from_workload(w)
-    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
+                           nhmf.NHMF_CACHE_SPATIAL)
     dut = cuda(du)
-    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED, nhmf.NHMF_SPATIAL):
         v = cuda(np.zeros_like(u))
         prob.apply(dut, v, nhmf.NHMF_FP64, strat)
         assert rel_l2(host(v), ref) <= FP64_TOL, (strat, rel_l2(host(v), ref))

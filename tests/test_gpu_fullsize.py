@@ -33,7 +33,8 @@ def test_fullsize_sampled_rows(name):
     ref = op.apply_rows(u, du, rows)
     rref = op.residual_rows(u, rows)
     prob = nhmf.Problem.from_workload(w)
-    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
+                           nhmf.NHMF_CACHE_SPATIAL)
     dut = cuda(du)
     idx = torch.from_numpy(rows).to("cuda:0")
     for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
@@ -45,6 +46,9 @@ def test_fullsize_sampled_rows(name):
         prob.apply(dut.float(), v32, nhmf.NHMF_FP32, strat)
         got32 = host(v32[idx])
         assert np.linalg.norm(got32 - ref) <= 1e-5 * np.linalg.norm(ref)
+    vsp = torch.empty_like(dut)
+    prob.apply(dut, vsp, nhmf.NHMF_FP64, nhmf.NHMF_SPATIAL)
+    assert np.linalg.norm(host(vsp[idx]) - ref) <= 1e-12 * np.linalg.norm(ref)
     vdf = torch.empty_like(dut)
     prob.apply(dut, vdf, nhmf.NHMF_DF64, nhmf.NHMF_CACHED)
     assert np.linalg.norm(host(vdf[idx]) - ref) <= 1e-12 * np.linalg.norm(ref)
