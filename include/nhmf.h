@@ -58,13 +58,20 @@ enum { NHMF_CACHE_FP64 = 1, NHMF_CACHE_FP32 = 2, NHMF_CACHE_DF64 = 4, NHMF_CACHE
 
 typedef struct nhmf_ctx nhmf_ctx;
 
+enum { NHMF_MODEL_COMPRESSIBLE = 0, NHMF_MODEL_SPLIT = 1 };
+
 typedef struct {
   int n_el;       /* N, elements per direction, >= 1 */
   int degree;     /* p, 1..4 */
-  double mu;      /* shear modulus, > 0 (Eq. hypref) */
-  double lambda;  /* Lame constant, >= 0 (Eq. hypref; the energy uses lambda (ln J)^2) */
+  double mu;      /* shear modulus, > 0 */
+  double lambda;  /* second constant, >= 0: the Lame constant lambda of Eq. hypref (the energy
+                     uses lambda (ln J)^2), or the bulk modulus kappa of Eq. hypcomplex */
   int bc;         /* NHMF_BC_* preset */
   double top_uz;  /* prescribed u_z on z = 1 for NHMF_BC_COMPRESSION (solver only) */
+  int model;      /* NHMF_MODEL_COMPRESSIBLE: Psi = mu/2 (tr C - 3 - 2 ln J) + lambda (ln J)^2
+                     (Eq. hypref); NHMF_MODEL_SPLIT: Psi = mu/2 (tr Cbar - 3)
+                     + kappa/2 ((J^2 - 1)/2 - ln J), Cbar = J^(-2/3) C (Eq. hypcomplex), which
+                     supports the NHMF_ON_THE_FLY and NHMF_SPATIAL strategies */
 } nhmf_params;
 
 /* Create a context for one mesh/material on the current CUDA device.  Allocates the

@@ -57,11 +57,12 @@ def reference_basis(p: int):
 class Operator:
     """Neo-Hookean operators on a structured mesh with Lame parameters (mu, lam)."""
 
-    def __init__(self, mesh: Mesh, mu: float, lam: float, bc: int = 0):
+    def __init__(self, mesh: Mesh, mu: float, lam: float, bc: int = 0, model: int = 0):
         self.mesh = mesh
         self.mu = float(mu)
         self.lam = float(lam)
         self.bc = bc
+        self.model = model
         self.Phi, self.Gref, self.W = reference_basis(mesh.p)
         self.G = self.Gref / mesh.h                     # physical gradients (affine cube)
         self.vol = self.W * mesh.h ** 3                 # w_q * J_q
@@ -97,12 +98,12 @@ class Operator:
         total = 0.0
         for _, conn in self._chunks():
             F = np.eye(3) + self.gradients(u, conn)
-            total = total + np.einsum("eq,q->", energy_density(F, self.mu, self.lam), self.vol)
+            total = total + np.einsum("eq,q->", energy_density(F, self.mu, self.lam, self.model), self.vol)
         return total
 
     def element_residuals(self, u, conn):
         F = np.eye(3) + self.gradients(u, conn)
-        P = piola(F, self.mu, self.lam)
+        P = piola(F, self.mu, self.lam, self.model)
         return np.einsum("eqcd,qad,q->eca", P, self.G, self.vol)
 
     def residual(self, u, elems=None) -> np.ndarray:
@@ -114,7 +115,7 @@ class Operator:
 
     def element_applies(self, u, du, conn):
         F = np.eye(3) + self.gradients(u, conn)
-        L = tangent_moduli(F, self.mu, self.lam)
+        L = tangent_moduli(F, self.mu, self.lam, self.model)
         dH = self.gradients(du, conn)
         G = np.einsum("eqiJkL,eqkL->eqiJ", L, dH)          # G = L : Grad du
         return np.einsum("eqcd,qad,q->eca", G, self.G, self.vol)
@@ -161,7 +162,7 @@ class Operator:
         """K_e[(c,a), (k,b)] = sum_q L_{c d k l} G[q,b,l] G[q,a,d] w_q h^3 (raw, no Dirichlet)."""
         conn = self.mesh.element_nodes(np.array([e]))
         F = np.eye(3) + self.gradients(u, conn)[0]
-        L = tangent_moduli(F, self.mu, self.lam)
+        L = tangent_moduli(F, self.mu, self.lam, self.model)
         nq = self.G.shape[1]
         Ke = np.einsum("qcdkl,qbl,qad,q->cakb", L, self.G, self.G, self.vol)
         return Ke.reshape(3 * nq, 3 * nq)
@@ -189,7 +190,7 @@ class Operator:
         d = np.zeros(mesh.n_dofs)
         for sub, conn in self._chunks():
             F = np.eye(3) + self.gradients(u, conn)
-            L = tangent_moduli(F, self.mu, self.lam)
+            L = tangent_moduli(F, self.mu, self.lam, self.model)
             de = np.einsum("eqcdcl,qal,qad,q->eca", L, self.G, self.G, self.vol)
             self._scatter(d, conn, de)
         d[self.fixed] = 1.0

@@ -54,7 +54,8 @@ nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
   if (!prm || !out) return NHMF_ERR_ARG;
   *out = nullptr;
   if (prm->n_el < 1 || prm->n_el > 4096 || prm->degree < 1 || prm->degree > 4 || !(prm->mu > 0.0) ||
-      !(prm->lambda >= 0.0) || prm->bc < NHMF_BC_NONE || prm->bc > NHMF_BC_COMPRESSION)
+      !(prm->lambda >= 0.0) || prm->bc < NHMF_BC_NONE || prm->bc > NHMF_BC_COMPRESSION ||
+      (prm->model != NHMF_MODEL_COMPRESSIBLE && prm->model != NHMF_MODEL_SPLIT))
     return NHMF_ERR_ARG;
   nhmf_ctx* c = new (std::nothrow) nhmf_ctx();
   if (!c) return NHMF_ERR_OOM;
@@ -113,6 +114,8 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
 
 nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void* stream) {
   if (!c || !u || mask < 0 || mask > 15) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
+  if (c->prm.model == NHMF_MODEL_SPLIT && (mask & (NHMF_CACHE_FP64 | NHMF_CACHE_FP32 | NHMF_CACHE_DF64)))
+    return fail(c, NHMF_ERR_ARG, "set_linearization: the split model has only the spatial (Algorithm 2) cache");
   cudaStream_t s = as_stream(stream);
   const size_t n = 3 * c->g.M3;
   c->have_lin = false;
@@ -147,6 +150,8 @@ nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const v
   if (!du || !v || du == v || (precision != NHMF_FP64 && precision != NHMF_FP32 && precision != NHMF_DF64) ||
       (strategy != NHMF_ON_THE_FLY && strategy != NHMF_CACHED && strategy != NHMF_SPATIAL))
     return fail(c, NHMF_ERR_ARG, "tangent_apply: bad argument");
+  if (c->prm.model == NHMF_MODEL_SPLIT && (strategy == NHMF_CACHED || precision == NHMF_DF64))
+    return fail(c, NHMF_ERR_ARG, "tangent_apply: the split model supports NHMF_ON_THE_FLY and NHMF_SPATIAL");
   if (strategy == NHMF_SPATIAL && precision != NHMF_FP64)
     return fail(c, NHMF_ERR_ARG, "tangent_apply: NHMF_SPATIAL is FP64 only");
   if (strategy == NHMF_SPATIAL && !c->cachesp)

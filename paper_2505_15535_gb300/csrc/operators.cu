@@ -162,14 +162,16 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
       continue;
     }
-    T Fi[9], lnJ;
+    T Fi[9], lnJ, Jm1 = T(0), F[9];
     if constexpr (STRAT == NHMF_ON_THE_FLY) {
       T H[9];
       colloc_grad<n, NI>(sDc, U, t, H);
 #pragma unroll
       for (int k = 0; k < 9; ++k) H[k] *= invh;
-      const T Jm1 = kinematics(H, Fi, lnJ);
+      Jm1 = kinematics(H, Fi, lnJ);
       bad |= !(Jm1 > T(-1));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? T(1) : T(0)) + H[k];
     } else {
       if (t / n3 < nvalid) {
         if constexpr (std::is_same<T, df64>::value) {
@@ -199,7 +201,10 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
     }
     T dH[9], g[9];
     colloc_grad<n, NI>(sDc, Vq, t, dH);
-    linearised_stress(Fi, lnJ, dH, mu, lam, sW[t % n3], g);
+    if constexpr (STRAT == NHMF_ON_THE_FLY)
+      model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, sW[t % n3], g);
+    else
+      linearised_stress(Fi, lnJ, dH, mu, lam, sW[t % n3], g);
 #pragma unroll
     for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
   }
@@ -338,14 +343,16 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
 #pragma unroll
       for (int qx = 0; qx < n; ++qx) {
         const int q = idx(qx, qy, qz);
-        float Fi[9], lnJ;
+        float Fi[9], lnJ, Jm1 = 0.f, F[9];
         if constexpr (STRAT == NHMF_ON_THE_FLY) {
           float H[9];
           grad_at(ub, qx, qy, qz, H);
 #pragma unroll
           for (int k = 0; k < 9; ++k) H[k] *= invh;
-          const float Jm1 = kinematics(H, Fi, lnJ);
+          Jm1 = kinematics(H, Fi, lnJ);
           bad |= !(Jm1 > -1.f);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.f : 0.f) + H[k];
         } else {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Fi[k] = __ldg(cache + (k * n3 + q) * E + slot);
@@ -353,7 +360,10 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
         }
         float dH[9], g[9];
         grad_at(qv, qx, qy, qz, dH);
-        linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
+        if constexpr (STRAT == NHMF_ON_THE_FLY)
+          model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
+        else
+          linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
         // transposed collocation derivative: acc[c][point on the line through q] += Dc[q][m] g
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -465,11 +475,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.0 : 0.0) + H[k];
       double P[9], tau[9];
-      const double c2 = 2.0 * a.lam * lnJ - a.mu;
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int J = 0; J < 3; ++J) P[3 * i + J] = fma(a.mu, F[3 * i + J], c2 * Fi[3 * J + i]);
+      model_piola(a.model, F, Fi, lnJ, Jm1, a.mu, a.lam, P);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
         for (int m = 0; m < 3; ++m)
 #pragma unroll
           for (int L = 0; L < 3; ++L) X[3 * m + L] = (m == k) ? F[3 * l + L] : 0.0;
-        linearised_stress(Fi, lnJ, X, a.mu, a.lam, 1.0, dP);
+        model_dP(a.model, F, Fi, lnJ, Jm1, X, a.mu, a.lam, 1.0, dP);
 #pragma unroll
         for (int I = 0; I <= K; ++I) {
           const int i = pk[I], j = pl[I];
@@ -555,17 +561,15 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_residual(const OpAr
     const double Jm1 = kinematics(H, Fi, lnJ);
     if (!(Jm1 > -1.0)) flags |= kStatusNonPosJ;
     const double s = sW[t % n3];
-    const double c2 = 2.0 * a.lam * lnJ - a.mu;
+    double F[9], P[9];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.0 : 0.0) + H[k];
+    model_piola(a.model, F, Fi, lnJ, Jm1, a.mu, a.lam, P);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        // P = mu F + (2 lambda ln J - mu) F^-T
-        const double F = (i == j ? 1.0 : 0.0) + H[3 * i + j];
-        const double Pij = fma(a.mu, F, c2 * Fi[3 * j + i]);
-        if (!isfinite(Pij)) flags |= kStatusNonFinite;
-        G[(3 * i + j) * NI + t] = s * Pij;
-      }
+    for (int k = 0; k < 9; ++k) {
+      if (!isfinite(P[k])) flags |= kStatusNonFinite;
+      G[k * NI + t] = s * P[k];
+    }
   }
   if (flags) atomicOr(a.status, flags);
   __syncthreads();
@@ -592,8 +596,8 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
   T* sBB = sB + kTabSlots;  // 3 product tables, n*n each
   T* sBD = sBB + kMaxN * kMaxN;
   T* sDD = sBD + kMaxN * kMaxN;
-  T* Cq = sDD + kMaxN * kMaxN + 1;  // [10][NI]: Finv (9) and ln J at the points
-  T* S = Cq + 10 * NI;              // [3][NI]
+  T* Cq = sDD + kMaxN * kMaxN + 1;  // [20][NI]: Finv (9), ln J, and for the split model F (9), J - 1
+  T* S = Cq + 20 * NI;              // [3][NI]
   T* tmp = S + 3 * NI;              // [3][NI]
   T* R = tmp + 3 * NI;              // [3][NI]
   load_tables<P>(a, sB, sDc, sD, sW, a.h);
@@ -614,10 +618,15 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
     colloc_grad<n, NI>(sDc, tmp, t, H);
 #pragma unroll
     for (int k = 0; k < 9; ++k) H[k] *= invh;
-    kinematics(H, Fi, lnJ);
+    const double Jm1 = kinematics(H, Fi, lnJ);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Cq[k * NI + t] = Fi[k];
     Cq[9 * NI + t] = lnJ;
+    if (a.model == NHMF_MODEL_SPLIT) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Cq[(10 + k) * NI + t] = (k % 4 == 0 ? 1.0 : 0.0) + H[k];
+      Cq[19 * NI + t] = Jm1;
+    }
     for (int c = 0; c < 3; ++c) R[c * NI + t] = 0.0;
   }
   __syncthreads();
@@ -625,11 +634,29 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
     for (int l = d; l < 3; ++l) {
       for (int t = threadIdx.x; t < NI; t += blockDim.x) {
         const double s = sW[t % n3] * (d == l ? 1.0 : 2.0);
-        const double kap = a.mu + 2.0 * a.lam * (1.0 - Cq[9 * NI + t]);
+        if (a.model == NHMF_MODEL_SPLIT) {
+          // L_cdcl = mu a d_dl - 2/3 mu a (F_cd Fi_lc + Fi_dc F_cl) + (2/9 mu a I1 + kappa J^2
+          //          + mu a I1/3 - kappa/2 (J^2 - 1)) Fi_dc Fi_lc
+          const double lnJ = Cq[9 * NI + t], J = 1.0 + Cq[19 * NI + t], J2 = J * J;
+          const double mua = a.mu * exp(-2.0 / 3.0 * lnJ);
+          double I1 = 0.0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double L = (d == l ? a.mu : 0.0) + kap * Cq[(3 * d + c) * NI + t] * Cq[(3 * l + c) * NI + t];
-          S[c * NI + t] = s * L;
+          for (int k = 0; k < 9; ++k) I1 += Cq[(10 + k) * NI + t] * Cq[(10 + k) * NI + t];
+          const double cff = 2.0 / 9.0 * mua * I1 + a.lam * J2 + mua * I1 / 3.0 - 0.5 * a.lam * (J2 - 1.0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double Fidc = Cq[(3 * d + c) * NI + t], Filc = Cq[(3 * l + c) * NI + t];
+            const double Fcd = Cq[(10 + 3 * c + d) * NI + t], Fcl = Cq[(10 + 3 * c + l) * NI + t];
+            const double L = (d == l ? mua : 0.0) - 2.0 / 3.0 * mua * (Fcd * Filc + Fidc * Fcl) + cff * Fidc * Filc;
+            S[c * NI + t] = s * L;
+          }
+        } else {
+          const double kap = a.mu + 2.0 * a.lam * (1.0 - Cq[9 * NI + t]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double L = (d == l ? a.mu : 0.0) + kap * Cq[(3 * d + c) * NI + t] * Cq[(3 * l + c) * NI + t];
+            S[c * NI + t] = s * L;
+          }
         }
       }
       __syncthreads();
@@ -682,6 +709,7 @@ OpArgs base_args(nhmf_ctx* c) {
   a.N = c->g.N;
   a.M = c->g.M;
   a.bc = c->prm.bc;
+  a.model = c->prm.model;
   a.M3 = c->g.M3;
   a.nq = c->g.nq;
   a.h = c->g.h;
@@ -818,7 +846,7 @@ nhmf_status diagonal_p(nhmf_ctx* c, double* d, cudaStream_t s) {
   OpArgs a = base_args(c);
   a.u64 = c->ubar;
   a.v = d;
-  const size_t smem = (kTabSlots + 3 * kMaxN * kMaxN + 1 + 19 * (size_t)NI) * sizeof(double);
+  const size_t smem = (kTabSlots + 3 * kMaxN * kMaxN + 1 + 29 * (size_t)NI) * sizeof(double);
   if (cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "diagonal memset");
   nhmf_status st = run_colours(c, k_diagonal<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "diagonal", NHMF_KIND_DIAGONAL);

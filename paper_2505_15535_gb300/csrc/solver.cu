@@ -285,7 +285,9 @@ nhmf_status mixed_inner(Ctx& x, const nhmf_solve_opts& o, const double* r, doubl
   to_fp32_scaled(x.n, r, w.sc + TMP, true, w.b32, x.s);
   long long it = 0;
   double rel = 0.0;
-  nhmf_status st = pcg<float>(x, o.strategy, w.b32, w.x32, w.dinv32, w.r32, w.z32, w.p32, w.q32, o.inner_rtol,
+  // the spatial cache is FP64 only: the FP32 inner operator then runs on the fly
+  const int s32 = o.strategy == NHMF_SPATIAL ? NHMF_ON_THE_FLY : o.strategy;
+  nhmf_status st = pcg<float>(x, s32, w.b32, w.x32, w.dinv32, w.r32, w.z32, w.p32, w.q32, o.inner_rtol,
                               o.inner_max_iter, o.check_every, IN_RZ0, &it, &rel);
   *inner += it;
   if (st != NHMF_OK) return st;
@@ -474,6 +476,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
 }
 
 int cache_mask(const nhmf_solve_opts& o) {
+  if (o.strategy == NHMF_SPATIAL) return NHMF_CACHE_SPATIAL;
   if (o.strategy != NHMF_CACHED) return 0;
   return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED)
              ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
@@ -481,7 +484,8 @@ int cache_mask(const nhmf_solve_opts& o) {
 }
 
 nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
-  if (!o || o->solver < 0 || o->solver > 3 || (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED) ||
+  if (!o || o->solver < 0 || o->solver > 3 ||
+      (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED && o->strategy != NHMF_SPATIAL) ||
       o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
       o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)
     return fail(c, NHMF_ERR_ARG, "solve: bad options");
@@ -543,6 +547,8 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   nhmf_status st = check_opts(c, o);
   if (st != NHMF_OK) return st;
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "linear_solve: no linearisation point set");
+  if (o->strategy == NHMF_SPATIAL && !c->cachesp)
+    return fail(c, NHMF_ERR_STATE, "linear_solve: the spatial strategy needs the NHMF_CACHE_SPATIAL cache");
   if (o->strategy == NHMF_CACHED && (!c->cache64 || ((cache_mask(*o) & NHMF_CACHE_FP32) && !c->cache32)))
     return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
   if ((st = ensure_work(c)) != NHMF_OK) return st;

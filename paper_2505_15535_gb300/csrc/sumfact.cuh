@@ -30,7 +30,7 @@ template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
 
 // Kernel arguments (by value; lives in the constant bank).
 struct OpArgs {
-  int N, M, bc;
+  int N, M, bc, model;
   long long M3, nq;
   double h, mu, lam;
   Colour col;
@@ -202,6 +202,77 @@ __device__ __forceinline__ void linearised_stress(const T Fi[9], T lnJ, const T 
       const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
       g[3 * i + j] = fma(smu, dH[3 * i + j], fma(sc1, Qji, sc2 * Fi[3 * j + i]));
     }
+}
+
+// Split neo-Hookean model (Eq. hypcomplex), with a = J^(-2/3), I1 = F : F:
+//   P  = mu a (F - I1/3 F^-T) + kappa/2 (J^2 - 1) F^-T
+//   dP = mu a dH - 2/3 mu a tr(F^-1 dH) F
+//        + (2/9 mu a I1 tr(F^-1 dH) - 2/3 mu a F:dH + kappa J^2 tr(F^-1 dH)) F^-T
+//        + (mu a I1/3 - kappa/2 (J^2 - 1)) F^-T dH^T F^-T
+template <typename T>
+__device__ __forceinline__ void split_stress_dP(const T F[9], const T Fi[9], T lnJ, T Jm1, const T dH[9], T mu,
+                                                T kappa, T s, T g[9]) {
+  const T a = exp(T(-2) / T(3) * lnJ);
+  const T J = T(1) + Jm1;
+  const T J2 = J * J;
+  T I1 = T(0), FdH = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    I1 = fma(F[k], F[k], I1);
+    FdH = fma(F[k], dH[k], FdH);
+  }
+  T K[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      K[3 * i + j] = fma(Fi[3 * i + 0], dH[j], fma(Fi[3 * i + 1], dH[3 + j], Fi[3 * i + 2] * dH[6 + j]));
+  const T trK = K[0] + K[4] + K[8];
+  const T mua = mu * a;
+  const T c1 = s * mua;
+  const T cF = -s * T(2) / T(3) * mua * trK;
+  const T c3 = s * (T(2) / T(9) * mua * I1 * trK - T(2) / T(3) * mua * FdH + kappa * J2 * trK);
+  const T c4 = s * (mua * I1 / T(3) - kappa / T(2) * (J2 - T(1)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
+      g[3 * i + j] = fma(c1, dH[3 * i + j], fma(cF, F[3 * i + j], fma(c3, Fi[3 * j + i], c4 * Qji)));
+    }
+}
+
+// P of the selected model
+template <typename T>
+__device__ __forceinline__ void model_piola(int model, const T F[9], const T Fi[9], T lnJ, T Jm1, T mu, T lam, T P[9]) {
+  if (model == NHMF_MODEL_SPLIT) {
+    const T a = exp(T(-2) / T(3) * lnJ);
+    const T J = T(1) + Jm1;
+    T I1 = T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) I1 = fma(F[k], F[k], I1);
+    const T cT = -mu * a * I1 / T(3) + lam / T(2) * (J * J - T(1));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) P[3 * i + j] = fma(mu * a, F[3 * i + j], cT * Fi[3 * j + i]);
+  } else {
+    const T c2 = T(2) * lam * lnJ - mu;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) P[3 * i + j] = fma(mu, F[3 * i + j], c2 * Fi[3 * j + i]);
+  }
+}
+
+// dP[dH] of the selected model, scaled by s (F = I + H needed by the split model only)
+template <typename T>
+__device__ __forceinline__ void model_dP(int model, const T F[9], const T Fi[9], T lnJ, T Jm1, const T dH[9], T mu,
+                                         T lam, T s, T g[9]) {
+  if (model == NHMF_MODEL_SPLIT)
+    split_stress_dP(F, Fi, lnJ, Jm1, dH, mu, lam, s, g);
+  else
+    linearised_stress(Fi, lnJ, dH, mu, lam, s, g);
 }
 
 // Voigt index of the pair (i, j): 11, 22, 33, 23, 13, 12 -> 0..5.

@@ -30,7 +30,8 @@ class NhmfError(RuntimeError):
 
 class nhmf_params(ctypes.Structure):
     _fields_ = [("n_el", ctypes.c_int), ("degree", ctypes.c_int), ("mu", ctypes.c_double),
-                ("lambda_", ctypes.c_double), ("bc", ctypes.c_int), ("top_uz", ctypes.c_double)]
+                ("lambda_", ctypes.c_double), ("bc", ctypes.c_int), ("top_uz", ctypes.c_double),
+                ("model", ctypes.c_int)]
 
 
 NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG, NHMF_SOLVER_MIXED_LEARNED = 0, 1, 2, 3
@@ -140,8 +141,11 @@ def _check(ctx, st):
 
 
 # ---- the C entry points, same names ---------------------------------------------------
-def nhmf_create(n_el, degree, mu, lam, bc, top_uz=0.0):
-    prm = nhmf_params(n_el, degree, mu, lam, bc, top_uz)
+NHMF_MODEL_COMPRESSIBLE, NHMF_MODEL_SPLIT = 0, 1
+
+
+def nhmf_create(n_el, degree, mu, lam, bc, top_uz=0.0, model=0):
+    prm = nhmf_params(n_el, degree, mu, lam, bc, top_uz, model)
     ctx = _P()
     st = lib().nhmf_create(ctypes.byref(prm), ctypes.byref(ctx))
     if st != NHMF_OK:
@@ -294,9 +298,9 @@ def nhmf_unet_train(ctx, epochs, lr, stream=None):
 class Problem:
     """One mesh + material on the current CUDA device (owns an nhmf context)."""
 
-    def __init__(self, n_el, degree, mu, lam, bc, top_uz=0.0):
-        self.n_el, self.degree, self.mu, self.lam, self.bc = n_el, degree, mu, lam, bc
-        self.ctx = nhmf_create(n_el, degree, mu, lam, bc, top_uz)
+    def __init__(self, n_el, degree, mu, lam, bc, top_uz=0.0, model=0):
+        self.n_el, self.degree, self.mu, self.lam, self.bc, self.model = n_el, degree, mu, lam, bc, model
+        self.ctx = nhmf_create(n_el, degree, mu, lam, bc, top_uz, model)
         self.n_dofs = nhmf_num_dofs(self.ctx)
 
     @classmethod

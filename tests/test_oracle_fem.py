@@ -212,3 +212,23 @@ def test_row_extraction_matches_full_operators():
     rows = RNG.choice(mesh.n_dofs, 30, replace=False)
     assert np.allclose(op.apply_rows(u, du, rows), op.apply(u, du)[rows], atol=1e-14)
     assert np.allclose(op.residual_rows(u, rows), op.residual(u)[rows], atol=1e-14)
+
+
+# ---- the split neo-Hookean model (Eq. hypcomplex) through the same operators
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_split_model_residual_and_tangent_are_derivatives(p):
+    mesh = Mesh(2, p)
+    op = Operator(mesh, 1.0, 5.0, bc=0, model=1)
+    u = rand_u(mesh, 0.1)
+    R = op.residual(u)
+    for i in RNG.choice(mesh.n_dofs, 10, replace=False):
+        uc = u.astype(complex)
+        uc[i] += 1e-30j
+        assert abs(np.imag(op.energy(uc)) / 1e-30 - R[i]) <= 1e-13 * max(1.0, np.abs(R).max())
+    du = RNG.standard_normal(mesh.n_dofs)
+    W = op.apply(u, du)
+    Rc = op.residual(u + 1e-30j * du)
+    assert np.linalg.norm(np.imag(Rc) / 1e-30 - W) <= 1e-12 * np.linalg.norm(W)
+    x, y = RNG.standard_normal(mesh.n_dofs), RNG.standard_normal(mesh.n_dofs)
+    a, b = y @ op.apply(u, x), x @ op.apply(u, y)
+    assert abs(a - b) <= 1e-13 * (abs(a) + abs(b))

@@ -82,3 +82,36 @@ def test_nonpositive_jacobian_raises():
         piola(F, 1.0, 1.5)
     with pytest.raises(NonPositiveJacobian):
         tangent_moduli(F, 1.0, 1.5)
+
+
+# ---- split (isochoric-volumetric) neo-Hookean model, Eq. hypcomplex
+@pytest.mark.parametrize("mu,kappa", [(1.0, 2.0), (0.4225, 100.0)])
+def test_split_model_stress_and_moduli_are_derivatives(mu, kappa):
+    F = random_F()
+    P = piola(F, mu, kappa, 1)
+    L = tangent_moduli(F, mu, kappa, 1)
+    for i in range(3):
+        for J in range(3):
+            Fc = F.astype(complex)
+            Fc[:, i, J] += 1e-30j
+            assert np.allclose(np.imag(energy_density(Fc, mu, kappa, 1)) / 1e-30, P[:, i, J], rtol=1e-13, atol=1e-13)
+            assert np.allclose(np.imag(piola(Fc, mu, kappa, 1)) / 1e-30, L[:, :, :, i, J], rtol=1e-13, atol=1e-12)
+    assert np.allclose(L, np.transpose(L, (0, 3, 4, 1, 2)), atol=1e-13)
+
+
+def test_split_model_isochoric_invariance_and_identity():
+    mu, kappa = 0.8, 3.0
+    # the isochoric part does not see volume changes: Psi(s F) - Psi_vol(s^3) = Psi(F) - Psi_vol(1) for det F = 1
+    F = np.array([[1.1, 0.1, 0.0], [0.0, 1.0 / 1.1, 0.05], [0.0, 0.0, 1.0]])[None]
+    assert abs(np.linalg.det(F[0]) - 1.0) < 1e-15
+    s = 1.2
+    vol = lambda J: 0.5 * kappa * (0.5 * (J * J - 1.0) - np.log(J))
+    assert abs((energy_density(s * F, mu, kappa, 1) - vol(s ** 3)) - energy_density(F, mu, kappa, 1))[0] < 1e-13
+    # stress free at F = I; at F = I the tangent is isotropic linear elasticity with (mu, kappa - 2 mu / 3)
+    assert np.allclose(piola(np.eye(3)[None], mu, kappa, 1), 0.0, atol=1e-15)
+    L = tangent_moduli(np.eye(3)[None], mu, kappa, 1)[0]
+    d = np.eye(3)
+    lam_eff = kappa - 2.0 * mu / 3.0
+    ref = (mu * (np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d))
+           + lam_eff * np.einsum("ij,kl->ijkl", d, d))
+    assert np.allclose(L, ref, atol=1e-14)
