@@ -191,6 +191,16 @@ def time_applies(torch, prob, nhmf, du, v, prec, strat, steps, flush):
     return step_ms, kms / steps, launches
 
 
+def max_over_ranks(values, dist, device=None):
+    """Element-wise maximum of a list of floats over all ranks (the slowest rank's times)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_gpu(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -237,10 +247,7 @@ def run_gpu(args):
                                                     args.steps, flush)
         barrier()
     clocks = clk.summary()
-    if dist is not None:
-        t = torch.tensor([step_ms, kernel_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, kernel_ms = t.tolist()
+    step_ms, kernel_ms = max_over_ranks([step_ms, kernel_ms], dist, dev)
     value = world * w.n_dofs / (step_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -327,6 +334,18 @@ def run_gpu(args):
                 "note": "alu_frac against the native FP64 peak (double-float runs on the FP32 pipe)"}
             if pv is not prob:
                 pv.close()
+        # the split neo-Hookean model (Eq. hypcomplex): on the fly and Algorithm 2
+        ws = inp.WORKLOADS[MAIN]
+        ps = nhmf.Problem(ws.n_el, ws.degree, ws.mu, 5.0, ws.bc, model=nhmf.NHMF_MODEL_SPLIT)
+        ps.set_linearization(torch.from_numpy(u).to(dev), nhmf.NHMF_CACHE_SPATIAL)
+        y = torch.empty_like(dut)
+        for sname, sid in (("otf", nhmf.NHMF_ON_THE_FLY), ("spatial", nhmf.NHMF_SPATIAL)):
+            for _ in range(3):
+                ps.apply(dut, y, nhmf.NHMF_FP64, sid)
+            sm, km, _ = time_applies(torch, ps, nhmf, dut, y, nhmf.NHMF_FP64, sid, vs, flush)
+            variants[f"{MAIN}_split_kappa5/fp64/{sname}"] = {"gdofs": ws.n_dofs / (sm * 1e-3) / 1e9, "ms": sm,
+                                                           "kernel_ms": km}
+        ps.close()
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
