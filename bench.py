@@ -419,7 +419,8 @@ def run_newton(args):
     base = dict(compression=w.compression, load_steps=S, linear_rtol=args.linear_rtol,
                 newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter)
     ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
-           "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED}
+           "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED,
+           "gmg": nhmf.NHMF_SOLVER_GMG, "mixed_gmg": nhmf.NHMF_SOLVER_MIXED_GMG}
     op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(w.n_dofs, 64, replace=False))
@@ -460,7 +461,7 @@ def run_newton(args):
     if "plain" in states:
         plain = states["plain"]
         for name, lst in states.items():
-            off = 0 if name in ("plain", "mixed") else args.train_steps
+            off = args.train_steps if name in ("learned", "mixed_learned") else 0
             for k, uu in enumerate(lst):
                 rec = out["solvers"][name]["steps"][k]
                 ref = plain[k + off]
@@ -485,7 +486,7 @@ def run_newton(args):
         for name in sp:
             if name in ("plain",):
                 continue
-            off = 0 if name == "mixed" else args.train_steps
+            off = args.train_steps if name in ("learned", "mixed_learned") else 0
             t_plain = sum(r["seconds"] for r in sp["plain"]["steps"][off:])
             sp[name]["speedup_vs_plain_same_steps"] = t_plain / sp[name]["seconds"] if sp[name]["seconds"] else None
     print(json.dumps(out), flush=True)

@@ -145,9 +145,18 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *   NHMF_SOLVER_MIXED_LEARNED FP64 multi-preconditioned CG with two search directions per
  *                          iteration, the FP32 inner Jacobi-CG of MIXED_FCG and N(r), combined
  *                          by a 2x2 Galerkin step and A-orthogonalised against the previous
- *                          pair; same fallback. */
+ *                          pair; same fallback;
+ *   NHMF_SOLVER_GMG        FP64 flexible CG preconditioned by one geometric-multigrid V-cycle
+ *                          (Section 2.3): levels N, N/2, ... (halving while N is even and
+ *                          N/2 >= 2), level operators at the linearisation point interpolated
+ *                          to each level, Chebyshev smoothing on the inverse diagonal
+ *                          (smoother_degree steps on [lmax/smoother_range, 1.2 lmax], lmax from
+ *                          12 power iterations), transfer by interpolation and its transpose,
+ *                          Jacobi-CG to 1e-10 on the coarsest level;
+ *   NHMF_SOLVER_MIXED_GMG  the same V-cycle in FP32 (FP32 applies, smoothers, transfers)
+ *                          inside FP64 flexible CG. */
 enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2,
-       NHMF_SOLVER_MIXED_LEARNED = 3 };
+       NHMF_SOLVER_MIXED_LEARNED = 3, NHMF_SOLVER_GMG = 4, NHMF_SOLVER_MIXED_GMG = 5 };
 #define NHMF_MAX_STEPS 64
 
 typedef struct {
@@ -175,6 +184,8 @@ typedef struct {
                            (K(u) e, e) for random fields e at one lattice scale each (from
                            the coarsest lattice to nodal white noise), default 0 */
   unsigned long long seed;      /* counter-based generator seed of those fields, default 1 */
+  int smoother_degree;          /* GMG: Chebyshev steps per pre-/post-smoothing, default 3 */
+  double smoother_range;        /* GMG: lmax / lmin of the Chebyshev interval, default 15 */
 } nhmf_solve_opts;
 
 typedef struct {

@@ -3,6 +3,7 @@
 #include <cstring>
 #include <new>
 
+#include "gmg.h"
 #include "internal.h"
 
 namespace nhmf {
@@ -89,6 +90,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->cache32);
   cudaFree(c->cachedf);
   cudaFree(c->cachesp);
+  gmg_free(c);
   free_work(c);
   unet_free(c);
   delete c;

@@ -45,6 +45,7 @@ struct Geometry {
 
 namespace nhmf {
 struct UNet;
+struct Gmg;
 // Work vectors of the solvers, allocated on first use.
 struct SolverWork {
   long long n = 0;
@@ -85,6 +86,7 @@ struct nhmf_ctx {
   std::vector<Rec> prof;
   nhmf::SolverWork* work = nullptr;
   nhmf::UNet* unet = nullptr;
+  nhmf::Gmg* gmg = nullptr;    // multigrid hierarchy, built on first use
 };
 
 namespace nhmf {
@@ -113,6 +115,7 @@ nhmf_status launch_apply(nhmf_ctx* c, int precision, int strategy, const void* d
                          cudaStream_t s, bool raw = false);
 // On every constrained DoF: out = src (mode 0) or out = value (mode 1).
 nhmf_status fix_rows64(nhmf_ctx* c, const double* src, double* out, int mode, double value, cudaStream_t s);
+nhmf_status fix_rows32(nhmf_ctx* c, const float* src, float* out, int mode, float value, cudaStream_t s);
 nhmf_status launch_cache_build(nhmf_ctx* c, cudaStream_t s);
 nhmf_status launch_residual(nhmf_ctx* c, const double* u, double* r, cudaStream_t s);
 nhmf_status launch_diagonal(nhmf_ctx* c, double* d, cudaStream_t s);

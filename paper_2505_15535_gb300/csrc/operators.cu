@@ -900,6 +900,10 @@ nhmf_status fix_rows64(nhmf_ctx* c, const double* src, double* out, int mode, do
   return fix_rows<double>(c, src, out, mode, value, s);
 }
 
+nhmf_status fix_rows32(nhmf_ctx* c, const float* src, float* out, int mode, float value, cudaStream_t s) {
+  return fix_rows<float>(c, src, out, mode, value, s);
+}
+
 nhmf_status launch_to_fp32(const double* x, float* y, long long n, cudaStream_t s) {
   k_to_fp32<<<1216, 256, 0, s>>>(x, y, n);
   return cudaGetLastError() == cudaSuccess ? NHMF_OK : NHMF_ERR_CUDA;

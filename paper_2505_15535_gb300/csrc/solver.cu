@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "blas.h"
+#include "gmg.h"
 #include "internal.h"
 #include "unet.h"
 
@@ -411,6 +412,41 @@ nhmf_status mpcg2(Ctx& x, int strat, const double* b, double* sol, double rtol, 
   return rn <= rtol * bnh ? NHMF_OK : NHMF_ERR_NOT_CONVERGED;
 }
 
+// One geometric-multigrid V-cycle for A_l x = b on level l (x overwritten).
+template <typename T>
+nhmf_status vcycle(nhmf_ctx* c, int l, const nhmf_solve_opts& o, const T* b, T* x, cudaStream_t s,
+                   long long* coarse_iters) {
+  Gmg& G = *c->gmg;
+  GmgLevel& L = G.L[l];
+  const bool fp32 = sizeof(T) == 4;
+  const int strat = (fp32 && o.strategy == NHMF_SPATIAL) ? NHMF_ON_THE_FLY : o.strategy;
+  nhmf_status st;
+  if (l == 0) {
+    Ctx cx{L.ctx, s, L.n, *L.ctx->work};
+    long long it = 0;
+    double rel = 0.0;
+    st = pcg<T>(cx, strat, b, x, Buf<T>::dinv(L), Buf<T>::r(L), Buf<T>::d(L), Buf<T>::t1(L), Buf<T>::t2(L), 1e-10,
+                10000, 10, fp32 ? IN_RZ0 : RZ0, &it, &rel);
+    *coarse_iters += it;
+    return st;
+  }
+  GmgLevel& C = G.L[l - 1];
+  const int deg = o.smoother_degree > 0 ? o.smoother_degree : 3;
+  const double range = o.smoother_range > 1.0 ? o.smoother_range : 15.0;
+  if ((st = chebyshev<T>(L, strat, b, x, deg, range, true, s)) != NHMF_OK) return st;
+  if ((st = launch_apply(L.ctx, Buf<T>::prec, strat, x, Buf<T>::r(L), s)) != NHMF_OK) return st;
+  gmg_bminus<T>(L.n, b, Buf<T>::r(L), s);
+  gmg_restrict<T>(L, Buf<T>::r(L), Buf<T>::b(C), s);
+  if (fp32)
+    st = fix_rows32(C.ctx, nullptr, reinterpret_cast<float*>(Buf<T>::b(C)), 1, 0.f, s);
+  else
+    st = fix_rows64(C.ctx, nullptr, reinterpret_cast<double*>(Buf<T>::b(C)), 1, 0.0, s);
+  if (st != NHMF_OK) return st;
+  if ((st = vcycle<T>(c, l - 1, o, Buf<T>::b(C), Buf<T>::x(C), s, coarse_iters)) != NHMF_OK) return st;
+  gmg_prolong_add<T>(L, Buf<T>::x(C), x, Buf<T>::q(L), s);
+  return chebyshev<T>(L, strat, b, x, deg, range, false, s);
+}
+
 // One linear solve A(ubar) sol = b with the chosen solver; the diagonal must be current.
 nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* sol, long long* outer,
                    long long* inner, double* relres, int* fallbacks) {
@@ -438,6 +474,23 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
   }
   if (o.solver == NHMF_SOLVER_MIXED_FCG) {
     auto precond = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
+    return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+  }
+  if (o.solver == NHMF_SOLVER_GMG || o.solver == NHMF_SOLVER_MIXED_GMG) {
+    const bool f32 = o.solver == NHMF_SOLVER_MIXED_GMG;
+    nhmf_status st = gmg_prepare(x.c, o.strategy, f32, x.s);
+    if (st != NHMF_OK) return st;
+    GmgLevel& top = x.c->gmg->L.back();
+    const int ltop = (int)x.c->gmg->L.size() - 1;
+    auto precond = [&](const double* r, double* z) -> nhmf_status {
+      if (!f32) return vcycle<double>(x.c, ltop, o, r, z, x.s, inner);
+      norm2(x.n, r, w.sc + TMP, w.partials, x.s);
+      to_fp32_scaled(x.n, r, w.sc + TMP, true, top.b32, x.s);
+      nhmf_status s2 = vcycle<float>(x.c, ltop, o, top.b32, top.x32, x.s, inner);
+      if (s2 != NHMF_OK) return s2;
+      to_fp64_scaled(x.n, top.x32, w.sc + TMP, z, x.s);
+      return cuda_check(x.c, cudaGetLastError(), "mixed gmg");
+    };
     return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
   }
   if (o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED) {
@@ -478,13 +531,14 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
 int cache_mask(const nhmf_solve_opts& o) {
   if (o.strategy == NHMF_SPATIAL) return NHMF_CACHE_SPATIAL;
   if (o.strategy != NHMF_CACHED) return 0;
-  return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED)
+  return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED ||
+          o.solver == NHMF_SOLVER_MIXED_GMG)
              ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
              : NHMF_CACHE_FP64;
 }
 
 nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
-  if (!o || o->solver < 0 || o->solver > 3 ||
+  if (!o || o->solver < 0 || o->solver > 5 ||
       (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED && o->strategy != NHMF_SPATIAL) ||
       o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
       o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)
@@ -538,6 +592,8 @@ void nhmf_solve_opts_default(nhmf_solve_opts* o) {
   o->learned_stall_factor = 0.9;
   o->synthetic_pairs = 0;
   o->seed = 1;
+  o->smoother_degree = 3;
+  o->smoother_range = 15.0;
 }
 
 nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const double* b, double* xsol, long long* iters,

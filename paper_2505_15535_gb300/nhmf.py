@@ -35,6 +35,7 @@ class nhmf_params(ctypes.Structure):
 
 
 NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG, NHMF_SOLVER_MIXED_LEARNED = 0, 1, 2, 3
+NHMF_SOLVER_GMG, NHMF_SOLVER_MIXED_GMG = 4, 5
 NHMF_MAX_STEPS = 64
 
 
@@ -47,7 +48,8 @@ class nhmf_solve_opts(ctypes.Structure):
                 ("inner_max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("record_pairs", ctypes.c_int), ("cg_pair_every", ctypes.c_int),
                 ("learned_stall_window", ctypes.c_int), ("learned_stall_factor", ctypes.c_double),
-                ("synthetic_pairs", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("synthetic_pairs", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("smoother_degree", ctypes.c_int), ("smoother_range", ctypes.c_double)]
 
 
 class nhmf_solve_stats(ctypes.Structure):
