@@ -226,7 +226,8 @@ def run_gpu(args):
     strategy = args.strategy
     strat = nhmf.NHMF_CACHED if strategy == "cached" else nhmf.NHMF_ON_THE_FLY
 
-    w = inp.WORKLOADS[MAIN]
+    main = args.apply_workload
+    w = inp.WORKLOADS[main]
     u, du = inp.draw_u(w), inp.draw_du(w)
     prob = nhmf.Problem.from_workload(w)
     ut = torch.from_numpy(u).to(dev)
@@ -284,9 +285,9 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants:
         vs = max(5, min(args.steps, 30))
-        for name in (MAIN, COMPANION):
+        for name in ((main, COMPANION) if main == MAIN else (main,)):
             wv = inp.WORKLOADS[name]
-            if name == MAIN:
+            if name == main:
                 pv, dv = prob, dut
             else:
                 pv = nhmf.Problem.from_workload(wv)
@@ -335,7 +336,7 @@ def run_gpu(args):
             if pv is not prob:
                 pv.close()
         # the split neo-Hookean model (Eq. hypcomplex): on the fly and Algorithm 2
-        ws = inp.WORKLOADS[MAIN]
+        ws = inp.WORKLOADS[main]
         ps = nhmf.Problem(ws.n_el, ws.degree, ws.mu, 5.0, ws.bc, model=nhmf.NHMF_MODEL_SPLIT)
         ps.set_linearization(torch.from_numpy(u).to(dev), nhmf.NHMF_CACHE_SPATIAL)
         y = torch.empty_like(dut)
@@ -343,7 +344,7 @@ def run_gpu(args):
             for _ in range(3):
                 ps.apply(dut, y, nhmf.NHMF_FP64, sid)
             sm, km, _ = time_applies(torch, ps, nhmf, dut, y, nhmf.NHMF_FP64, sid, vs, flush)
-            variants[f"{MAIN}_split_kappa5/fp64/{sname}"] = {"gdofs": ws.n_dofs / (sm * 1e-3) / 1e9, "ms": sm,
+            variants[f"{main}_split_kappa5/fp64/{sname}"] = {"gdofs": ws.n_dofs / (sm * 1e-3) / 1e9, "ms": sm,
                                                            "kernel_ms": km}
         ps.close()
 
@@ -360,7 +361,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{MAIN}: " + describe(w) + f"; FP64 tangent apply, {strategy} strategy",
+            "config": {"workload": f"{main}: " + describe(w) + f"; FP64 tangent apply, {strategy} strategy",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -575,6 +576,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", choices=["apply", "newton", "unet"], default="apply")
     ap.add_argument("--workload", default="q2_64_compress")
+    ap.add_argument("--apply-workload", default=MAIN)
     ap.add_argument("--solvers", default="plain,mixed,learned,mixed_learned")
     ap.add_argument("--last-step", type=int, default=0)
     ap.add_argument("--train-steps", type=int, default=5)
