@@ -255,7 +255,7 @@ nhmf_status gmg_build(nhmf_ctx* c) {
 }
 
 // Level linearisation points, diagonals and eigenvalue estimates at the fine point c->ubar.
-nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s) {
+nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero) {
   nhmf_status st = gmg_build(c);
   if (st != NHMF_OK) return st;
   Gmg& G = *c->gmg;
@@ -265,7 +265,10 @@ nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s) {
   for (int l = nl - 2; l >= 0; --l) {
     GmgLevel& F = G.L[l + 1];
     GmgLevel& C = G.L[l];
-    map3d<double>(F.I, F.ctx->ubar, C.x, F.t1, F.t2, s);
+    if (coarse_at_zero)
+      cudaMemsetAsync(C.x, 0, C.n * sizeof(double), s);  // linear elasticity on the coarse levels
+    else
+      map3d<double>(F.I, F.ctx->ubar, C.x, F.t1, F.t2, s);
     if ((st = nhmf_set_linearization(C.ctx, C.x, mask, s)) != NHMF_OK)
       return fail(c, st, std::string("gmg: coarse linearisation: ") + nhmf_last_error(C.ctx));
   }
@@ -349,6 +352,8 @@ void gmg_prolong_add(GmgLevel& F, const T* e_coarse, T* x_fine, T* scratch, cuda
   map3d<T>(F.P, e_coarse, scratch, Buf<T>::t1(F), Buf<T>::t2(F), s);
   k_add<T><<<kB, kT, 0, s>>>(F.n, scratch, x_fine);
 }
+
+void gmg_start_vector(long long n, double* v, cudaStream_t s) { k_start<<<kB, kT, 0, s>>>(n, v); }
 
 template <typename T>
 void gmg_bminus(long long n, const T* b, T* y, cudaStream_t s) {

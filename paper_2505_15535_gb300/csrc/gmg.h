@@ -34,7 +34,9 @@ struct Gmg {
 
 void gmg_free(nhmf_ctx* c);
 nhmf_status gmg_build(nhmf_ctx* c);
-nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s);
+// Level linearisation points (interpolated from the fine one, or zero on the coarse levels),
+// diagonals and eigenvalue estimates.
+nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero);
 // per-level buffers by precision
 template <typename T> struct Buf;
 template <> struct Buf<double> {
@@ -66,5 +68,6 @@ nhmf_status chebyshev(GmgLevel& L, int strat, const T* b, T* x, int degree, doub
 template <typename T> void gmg_restrict(GmgLevel& F, const T* r_fine, T* r_coarse, cudaStream_t s);
 template <typename T> void gmg_prolong_add(GmgLevel& F, const T* e_coarse, T* x_fine, T* scratch, cudaStream_t s);
 template <typename T> void gmg_bminus(long long n, const T* b, T* y, cudaStream_t s);
+void gmg_start_vector(long long n, double* v, cudaStream_t s);
 
 }  // namespace nhmf
