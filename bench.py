@@ -348,6 +348,26 @@ def run_gpu(args):
                                                            "kernel_ms": km}
         ps.close()
 
+    # ---- Newton to 1e-8: plain FP64 Jacobi-CG vs mixed-precision multigrid, first two load
+    # steps of the Q2 64^3 compression workload (the second half of the metric; bounded time)
+    newton = None
+    if not args.no_newton:
+        wn = inp.WORKLOADS["q2_64_compress"]
+        pn = nhmf.Problem.from_workload(wn)
+        newton = {"workload": f"q2_64_compress: {describe(wn)}; load steps 1-2 of {wn.load_steps}"}
+        for sname, sid in (("plain_fp64_jacobi_cg", nhmf.NHMF_SOLVER_JACOBI_CG),
+                           ("mixed_fp32_gmg", nhmf.NHMF_SOLVER_MIXED_GMG)):
+            un = torch.zeros(wn.n_dofs, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = pn.solve(un, solver=sid, load_steps=wn.load_steps, compression=wn.compression, last_step=2,
+                          linear_rtol=1e-8)
+            torch.cuda.synchronize()
+            newton[sname] = {"seconds": time.perf_counter() - t0, "newton_iters": sum(st["newton_iters"]),
+                             "outer_iters": st["total_linear_iters"], "rel_residual": max(st["rel_residual"])}
+        newton["speedup"] = newton["plain_fp64_jacobi_cg"]["seconds"] / newton["mixed_fp32_gmg"]["seconds"]
+        pn.close()
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -366,7 +386,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches + args.steps),   # 8 colour launches + 1 Dirichlet fix per step
-            "clocks": clocks, "cache_build_s": cache_build_s, "variants": variants,
+            "clocks": clocks, "cache_build_s": cache_build_s, "variants": variants, "newton": newton,
         }
         print(json.dumps(line), flush=True)
     prob.close()
@@ -573,6 +593,7 @@ def main():
     ap.add_argument("--strategy", choices=["cached", "otf"], default="cached")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", choices=["apply", "newton", "unet"], default="apply")
     ap.add_argument("--workload", default="q2_64_compress")
