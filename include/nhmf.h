@@ -123,6 +123,15 @@ nhmf_status nhmf_residual(nhmf_ctx* ctx, const double* u, double* r, void* strea
 /* d = diag(A(u)) in FP64 at the current linearisation point (1 on D).  Asynchronous. */
 nhmf_status nhmf_diagonal(nhmf_ctx* ctx, double* d, void* stream);
 
+/* Heterogeneous material: per-element factors f_e > 0 multiplying mu and lambda (kappa) on
+ * element e (the paper's test material has inclusions 100x stiffer than the matrix,
+ * Section 3.1).  `factors` is a device array of N^3 doubles in natural element order
+ * ex + N (ey + N ez), copied into the context; NULL restores the homogeneous material.  Every
+ * operator (residual, tangent apply of every strategy and precision, diagonal, solvers and
+ * the multigrid levels, whose coarse elements take the mean of their eight children) uses
+ * them.  Synchronises. */
+nhmf_status nhmf_set_material_factors(nhmf_ctx* ctx, const double* factors, void* stream);
+
 /* Synchronise `stream`, read and clear the device status word.  Returns NHMF_OK,
  * NHMF_ERR_NONPOS_J or NHMF_ERR_NONFINITE. */
 nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);

@@ -152,3 +152,17 @@ def draw_du(w: Workload) -> np.ndarray:
 def draw_vector(seed: int, n: int) -> np.ndarray:
     """A plain N(0, 1) vector (test directions, right-hand sides)."""
     return normal(seed, n)
+
+
+def inclusion_factors(n_el: int, stiffness: float = 100.0) -> np.ndarray:
+    """Per-element material factors [N^3] (element ex + N (ey + N ez)) of a unit cube with two
+    spherical inclusions `stiffness` times stiffer than the matrix (centres (0.3, 0.5, 0.5) and
+    (0.7, 0.5, 0.5), radius 0.15, decided at element centres): a structured stand-in for the
+    heterogeneous plate with two stiff inclusions of the paper's test case."""
+    h = 1.0 / n_el
+    c = (np.arange(n_el) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    f = np.ones((n_el, n_el, n_el))
+    for cx in (0.3, 0.7):
+        f[(x - cx) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2 <= 0.15 ** 2] = stiffness
+    return f.reshape(-1)

@@ -11,6 +11,10 @@ Shape-function values and gradients at the points are evaluated directly as prod
 1D Lagrange polynomials, O((p+1)^6) per element -- no sum factorisation -- and L is formed
 explicitly per point (the "naive" route of Section 3.2.1).
 
+Heterogeneous material (the paper's test has inclusions 100x stiffer, Section 3.1): an
+optional per-element factor f_e multiplies mu and lambda on element e; both energies are
+linear in (mu, lambda), so P, L and every element contribution scale by f_e.
+
 Dirichlet handling (a reading; the paper does not state it for the operator): with D the
 constrained DoFs, the constrained operator is  A du = P_f K P_f du + P_D du  (identity rows
 and columns on D), and residual rows on D are zero.  bc = 0 gives the raw operator.
@@ -57,12 +61,13 @@ def reference_basis(p: int):
 class Operator:
     """Neo-Hookean operators on a structured mesh with Lame parameters (mu, lam)."""
 
-    def __init__(self, mesh: Mesh, mu: float, lam: float, bc: int = 0, model: int = 0):
+    def __init__(self, mesh: Mesh, mu: float, lam: float, bc: int = 0, model: int = 0, factors=None):
         self.mesh = mesh
         self.mu = float(mu)
         self.lam = float(lam)
         self.bc = bc
         self.model = model
+        self.factors = None if factors is None else np.asarray(factors, dtype=np.float64)
         self.Phi, self.Gref, self.W = reference_basis(mesh.p)
         self.G = self.Gref / mesh.h                     # physical gradients (affine cube)
         self.vol = self.W * mesh.h ** 3                 # w_q * J_q
@@ -92,40 +97,47 @@ class Operator:
             sub = elems[s:s + _CHUNK]
             yield sub, mesh.element_nodes(sub)
 
+    def _f(self, elems, shape_tail):
+        """Material factors of the listed elements, shaped to broadcast over shape_tail."""
+        if self.factors is None:
+            return 1.0
+        return self.factors[np.asarray(elems)].reshape((-1,) + (1,) * shape_tail)
+
     # -- global operators -------------------------------------------------------------
     def energy(self, u):
         """Discrete potential energy sum_e sum_q Psi(F_q) w_q h^3 (complex u allowed for complex-step checks)."""
         total = 0.0
-        for _, conn in self._chunks():
+        for sub, conn in self._chunks():
             F = np.eye(3) + self.gradients(u, conn)
-            total = total + np.einsum("eq,q->", energy_density(F, self.mu, self.lam, self.model), self.vol)
+            psi = energy_density(F, self.mu, self.lam, self.model) * self._f(sub, 1)
+            total = total + np.einsum("eq,q->", psi, self.vol)
         return total
 
-    def element_residuals(self, u, conn):
+    def element_residuals(self, u, conn, elems):
         F = np.eye(3) + self.gradients(u, conn)
         P = piola(F, self.mu, self.lam, self.model)
-        return np.einsum("eqcd,qad,q->eca", P, self.G, self.vol)
+        return np.einsum("eqcd,qad,q->eca", P, self.G, self.vol) * self._f(elems, 2)
 
     def residual(self, u, elems=None) -> np.ndarray:
         r = np.zeros(self.mesh.n_dofs, dtype=np.result_type(u, np.float64))
         for sub, conn in self._chunks(elems):
-            self._scatter(r, conn, self.element_residuals(u, conn))
+            self._scatter(r, conn, self.element_residuals(u, conn, sub))
         r[self.fixed] = 0.0
         return r
 
-    def element_applies(self, u, du, conn):
+    def element_applies(self, u, du, conn, elems):
         F = np.eye(3) + self.gradients(u, conn)
         L = tangent_moduli(F, self.mu, self.lam, self.model)
         dH = self.gradients(du, conn)
         G = np.einsum("eqiJkL,eqkL->eqiJ", L, dH)          # G = L : Grad du
-        return np.einsum("eqcd,qad,q->eca", G, self.G, self.vol)
+        return np.einsum("eqcd,qad,q->eca", G, self.G, self.vol) * self._f(elems, 2)
 
     def apply(self, u, du, elems=None) -> np.ndarray:
         """A du = P_f K(u) P_f du + P_D du."""
         dm = np.where(self.fixed, 0.0, du)
         v = np.zeros(self.mesh.n_dofs)
         for sub, conn in self._chunks(elems):
-            self._scatter(v, conn, self.element_applies(u, dm, conn))
+            self._scatter(v, conn, self.element_applies(u, dm, conn, sub))
         v[self.fixed] = du[self.fixed]
         return v
 
@@ -139,7 +151,7 @@ class Operator:
         dm = np.where(self.fixed, 0.0, du)
         v = np.zeros(mesh.n_dofs)
         conn = mesh.element_nodes(elems)
-        self._scatter(v, conn, self.element_applies(u, dm, conn))
+        self._scatter(v, conn, self.element_applies(u, dm, conn, elems))
         out = v[dofs]
         fx = self.fixed[dofs]
         out[fx] = du[dofs][fx]
@@ -153,7 +165,7 @@ class Operator:
         elems = np.array(elems, dtype=np.int64)
         r = np.zeros(mesh.n_dofs)
         conn = mesh.element_nodes(elems)
-        self._scatter(r, conn, self.element_residuals(u, conn))
+        self._scatter(r, conn, self.element_residuals(u, conn, elems))
         out = r[dofs]
         out[self.fixed[dofs]] = 0.0
         return out
@@ -165,7 +177,8 @@ class Operator:
         L = tangent_moduli(F, self.mu, self.lam, self.model)
         nq = self.G.shape[1]
         Ke = np.einsum("qcdkl,qbl,qad,q->cakb", L, self.G, self.G, self.vol)
-        return Ke.reshape(3 * nq, 3 * nq)
+        fe = 1.0 if self.factors is None else self.factors[e]
+        return fe * Ke.reshape(3 * nq, 3 * nq)
 
     def assemble(self, u) -> np.ndarray:
         """Dense global matrix of the constrained operator (tiny meshes only)."""
@@ -191,7 +204,7 @@ class Operator:
         for sub, conn in self._chunks():
             F = np.eye(3) + self.gradients(u, conn)
             L = tangent_moduli(F, self.mu, self.lam, self.model)
-            de = np.einsum("eqcdcl,qal,qad,q->eca", L, self.G, self.G, self.vol)
+            de = np.einsum("eqcdcl,qal,qad,q->eca", L, self.G, self.G, self.vol) * self._f(sub, 2)
             self._scatter(d, conn, de)
         d[self.fixed] = 1.0
         return d

@@ -25,7 +25,7 @@ def newton_load_steps(op: Operator, steps: int, compression: float, rtol: float 
                       max_iter: int = 20, first: int = 1, last: int | None = None,
                       u0: np.ndarray | None = None, max_backtracks: int = 8):
     mesh = op.mesh
-    raw = Operator(mesh, op.mu, op.lam, bc=0, model=op.model)
+    raw = Operator(mesh, op.mu, op.lam, bc=0, model=op.model, factors=op.factors)
     fixed = op.fixed
     u = np.zeros(mesh.n_dofs) if u0 is None else u0.copy()
     last = steps if last is None else last

@@ -100,6 +100,24 @@ size_t nhmf_num_dofs(const nhmf_ctx* c) { return c ? (size_t)(3 * c->g.M3) : 0; 
 
 const char* nhmf_last_error(const nhmf_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+nhmf_status nhmf_set_material_factors(nhmf_ctx* c, const double* factors, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  gmg_free(c);  // the coarse levels carry the factors: rebuild them on next use
+  if (!factors) {
+    cudaFree(c->factor);
+    c->factor = nullptr;
+    return NHMF_OK;
+  }
+  nhmf_status st = NHMF_OK;
+  if (!c->factor) st = cuda_check(c, cudaMalloc(&c->factor, c->g.E * sizeof(double)), "factor alloc");
+  if (st == NHMF_OK)
+    st = cuda_check(c, cudaMemcpyAsync(c->factor, factors, c->g.E * sizeof(double), cudaMemcpyDeviceToDevice, s),
+                    "factor copy");
+  if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "factor sync");
+  return st;
+}
+
 nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
   if (!c) return NHMF_ERR_ARG;
   unsigned h = 0;

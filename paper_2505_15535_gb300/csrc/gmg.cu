@@ -206,6 +206,21 @@ nhmf_status gmg_build(nhmf_ctx* c) {
   Gmg& G = *c->gmg;
   const int nl = (int)Ns.size();
   G.L.resize(nl);
+  // material factors of every level: coarse elements take the mean of their eight children
+  std::vector<std::vector<double>> fac(nl);
+  if (c->factor) {
+    fac[nl - 1].resize(c->g.E);
+    cudaMemcpy(fac[nl - 1].data(), c->factor, c->g.E * sizeof(double), cudaMemcpyDeviceToHost);
+    for (int l = nl - 2; l >= 0; --l) {
+      const int Nf = Ns[nl - 2 - l], Ncs = Ns[nl - 1 - l];
+      fac[l].assign((size_t)Ncs * Ncs * Ncs, 0.0);
+      for (int z = 0; z < Nf; ++z)
+        for (int y = 0; y < Nf; ++y)
+          for (int x = 0; x < Nf; ++x)
+            fac[l][(x / 2) + (size_t)Ncs * ((y / 2) + (size_t)Ncs * (z / 2))] +=
+                0.125 * fac[l + 1][x + (size_t)Nf * (y + (size_t)Nf * z)];
+    }
+  }
   for (int l = 0; l < nl; ++l) {
     const int N = Ns[nl - 1 - l];  // level 0 = coarsest
     GmgLevel& L = G.L[l];
@@ -218,6 +233,17 @@ nhmf_status gmg_build(nhmf_ctx* c) {
       if (st != NHMF_OK) {
         gmg_free(c);
         return fail(c, st, "gmg: level context");
+      }
+      if (c->factor) {
+        double* dev = nullptr;
+        bool fok = cudaMalloc(&dev, fac[l].size() * sizeof(double)) == cudaSuccess &&
+                   cudaMemcpy(dev, fac[l].data(), fac[l].size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (fok) st = nhmf_set_material_factors(L.ctx, dev, nullptr);
+        cudaFree(dev);
+        if (!fok || st != NHMF_OK) {
+          gmg_free(c);
+          return fail(c, NHMF_ERR_OOM, "gmg: level factors");
+        }
       }
     }
     if (ensure_work(L.ctx) != NHMF_OK) {

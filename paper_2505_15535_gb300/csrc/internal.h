@@ -77,6 +77,7 @@ struct nhmf_ctx {
   float* cache32 = nullptr;   // [10][nq]
   float2* cachedf = nullptr;  // [10][nq] (hi, lo) double-float pairs
   double* cachesp = nullptr;  // [36][nq] J c (21), tau (6), F^-1 (9): Algorithm 2
+  double* factor = nullptr;   // [E] per-element material factors (natural order), or null
   unsigned* status = nullptr; // device status word: bit 0 det F <= 0, bit 1 non-finite
   bool have_lin = false;
   std::string err;

@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
       }
       T dH[9], g[9];
       colloc_grad<n, NI>(sDc, Vq, t, dH);
-      spatial_stress(Jc, tau, Fs, dH, sW[t % n3], g);
+      const T sf = a.factor ? sW[t % n3] * T(elem_factor(a, e0 + min(t / n3, nvalid - 1))) : sW[t % n3];
+      spatial_stress(Jc, tau, Fs, dH, sf, g);
 #pragma unroll
       for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
       continue;
@@ -201,10 +202,11 @@ __global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
     }
     T dH[9], g[9];
     colloc_grad<n, NI>(sDc, Vq, t, dH);
+    const T sf = a.factor ? sW[t % n3] * T(elem_factor(a, e0 + min(t / n3, nvalid - 1))) : sW[t % n3];
     if constexpr (STRAT == NHMF_ON_THE_FLY)
-      model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, sW[t % n3], g);
+      model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, sf, g);
     else
-      linearised_stress(Fi, lnJ, dH, mu, lam, sW[t % n3], g);
+      linearised_stress(Fi, lnJ, dH, mu, lam, sf, g);
 #pragma unroll
     for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
   }
@@ -333,7 +335,8 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int q = 0; q < n3; ++q) acc[c][q] = 0.f;
-  const float mu = float(a.mu), lam = float(a.lam), h = float(a.h), invh = float(1.0 / a.h);
+  const float mu = float(a.mu), lam = float(a.lam), invh = float(1.0 / a.h);
+  const float h = float(a.h * elem_factor(a, ec));  // the material factor rides on the point weight
   const float* __restrict__ cache = static_cast<const float*>(a.cache);
   bool bad = false;
 #pragma unroll
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_residual(const OpAr
     for (int k = 0; k < 9; ++k) H[k] *= invh;
     const double Jm1 = kinematics(H, Fi, lnJ);
     if (!(Jm1 > -1.0)) flags |= kStatusNonPosJ;
-    const double s = sW[t % n3];
+    const double s = sW[t % n3] * elem_factor(a, e0 + min(t / n3, nvalid - 1));
     double F[9], P[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.0 : 0.0) + H[k];
@@ -633,7 +636,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
   for (int d = 0; d < 3; ++d)
     for (int l = d; l < 3; ++l) {
       for (int t = threadIdx.x; t < NI; t += blockDim.x) {
-        const double s = sW[t % n3] * (d == l ? 1.0 : 2.0);
+        const double s = sW[t % n3] * (d == l ? 1.0 : 2.0) * elem_factor(a, e0 + min(t / n3, nvalid - 1));
         if (a.model == NHMF_MODEL_SPLIT) {
           // L_cdcl = mu a d_dl - 2/3 mu a (F_cd Fi_lc + Fi_dc F_cl) + (2/9 mu a I1 + kappa J^2
           //          + mu a I1/3 - kappa/2 (J^2 - 1)) Fi_dc Fi_lc
@@ -728,6 +731,7 @@ OpArgs base_args(nhmf_ctx* c) {
     a.wf[q] = float(c->tab.w[q]);
   }
   a.status = c->status;
+  a.factor = c->factor;
   return a;
 }
 

@@ -46,6 +46,7 @@ struct OpArgs {
   float2* cachedf_out;
   double* cachesp_out;
   const double* cachesp_in;
+  const double* factor;  // per-element material factor (natural element order) or null
   unsigned* status;
 };
 
@@ -67,6 +68,15 @@ __device__ __forceinline__ void item_node(const OpArgs& a, long long e_in_colour
   gi = P * (c.cx + 2 * ix) + q % n;
   gj = P * (c.cy + 2 * iy) + (q / n) % n;
   gk = P * (c.cz + 2 * iz) + q / (n * n);
+}
+
+// Material factor of element e_in_colour of the launch's colour class (1 if homogeneous).
+__device__ __forceinline__ double elem_factor(const OpArgs& a, long long e_in_colour) {
+  if (!a.factor) return 1.0;
+  const Colour& c = a.col;
+  const long long ix = e_in_colour % c.nx, iy = (e_in_colour / c.nx) % c.ny, iz = e_in_colour / ((long long)c.nx * c.ny);
+  const long long ex = c.cx + 2 * ix, ey = c.cy + 2 * iy, ez = c.cz + 2 * iz;
+  return a.factor[ex + (long long)a.N * (ey + (long long)a.N * ez)];
 }
 
 // One 1D pass along direction DIR over NC arrays of NI items:

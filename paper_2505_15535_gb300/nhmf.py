@@ -83,6 +83,7 @@ _SIGS = {
     "nhmf_residual": (ctypes.c_int, [_P, _P, _P, _P]),
     "nhmf_diagonal": (ctypes.c_int, [_P, _P, _P]),
     "nhmf_check_status": (ctypes.c_int, [_P, _P]),
+    "nhmf_set_material_factors": (ctypes.c_int, [_P, _P, _P]),
     "nhmf_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "nhmf_solve_opts_default": (None, [ctypes.POINTER(nhmf_solve_opts)]),
     "nhmf_solve": (ctypes.c_int, [_P, ctypes.POINTER(nhmf_solve_opts), _P, ctypes.POINTER(nhmf_solve_stats), _P]),
@@ -181,6 +182,12 @@ def nhmf_residual(ctx, u, r, stream=None):
 
 def nhmf_diagonal(ctx, d, stream=None):
     _check(ctx, lib().nhmf_diagonal(ctx, _ptr(d), _stream(stream)))
+
+
+def nhmf_set_material_factors(ctx, factors, stream=None):
+    """factors: CUDA FP64 tensor of N^3 per-element factors (natural order), or None."""
+    _check(ctx, lib().nhmf_set_material_factors(ctx, _ptr(factors) if factors is not None else None,
+                                                _stream(stream)))
 
 
 def nhmf_check_status(ctx, stream=None):

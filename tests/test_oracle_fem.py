@@ -232,3 +232,23 @@ def test_split_model_residual_and_tangent_are_derivatives(p):
     x, y = RNG.standard_normal(mesh.n_dofs), RNG.standard_normal(mesh.n_dofs)
     a, b = y @ op.apply(u, x), x @ op.apply(u, y)
     assert abs(a - b) <= 1e-13 * (abs(a) + abs(b))
+
+
+# ---- heterogeneous material: per-element factors (stiff inclusions)
+def test_element_factors_scale_contributions():
+    mesh = Mesh(8, 1)
+    f = inp.inclusion_factors(8, 100.0)
+    assert set(np.unique(f)) == {1.0, 100.0}
+    op = Operator(mesh, 1.0, 1.5, bc=0, factors=f)
+    u = rand_u(mesh, 0.05)
+    # residual = energy gradient and tangent = residual derivative still hold
+    R = op.residual(u)
+    for i in RNG.choice(mesh.n_dofs, 6, replace=False):
+        uc = u.astype(complex); uc[i] += 1e-30j
+        assert abs(np.imag(op.energy(uc)) / 1e-30 - R[i]) <= 1e-13 * np.abs(R).max()
+    du = RNG.standard_normal(mesh.n_dofs)
+    W = op.apply(u, du)
+    assert np.linalg.norm(np.imag(op.residual(u + 1e-30j * du)) / 1e-30 - W) <= 1e-12 * np.linalg.norm(W)
+    # a uniform factor scales the operator
+    op2 = Operator(mesh, 1.0, 1.5, bc=0, factors=np.full(mesh.n_elements, 3.0))
+    assert np.allclose(op2.apply(u, du), 3.0 * Operator(mesh, 1.0, 1.5, bc=0).apply(u, du), rtol=1e-13, atol=1e-13)
