@@ -157,7 +157,8 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *                          pair; same fallback;
  *   NHMF_SOLVER_GMG        FP64 flexible CG preconditioned by one geometric-multigrid V-cycle
  *                          (Section 2.3): levels N, N/2, ... (halving while N is even and
- *                          N/2 >= 2), level operators at the linearisation point interpolated
+ *                          N/2 >= 2) with degree p, then degree 1 on the coarsest mesh when
+ *                          p > 1; level operators at the linearisation point interpolated
  *                          to each level, Chebyshev smoothing on the inverse diagonal
  *                          (smoother_degree steps on [lmax/smoother_range, 1.2 lmax], lmax from
  *                          12 power iterations), transfer by interpolation and its transpose,

@@ -101,23 +101,24 @@ double node_coord(const double* t, int p, int N, int i) {
   return (e + t[i - p * e]) / N;
 }
 
-// out node i of a mesh with N_out elements gets the value of the FE function of the mesh with
-// N_in elements at its position: weights of the n Lagrange functions of the containing element.
-void build_eval_map(const double* t, int p, int N_out, int N_in, std::vector<int>& ptr, std::vector<int>& col,
-                    std::vector<double>& w) {
-  const int M_out = p * N_out + 1, n = p + 1;
+// Node i of the output mesh (N_out elements of degree p_out, GLL nodes t_out) gets the value of
+// the FE function of the input mesh (N_in elements of degree p_in, nodes t_in) at its position:
+// the weights of the p_in + 1 Lagrange functions of the containing input element.
+void build_eval_map(const double* t_out, int p_out, int N_out, const double* t_in, int p_in, int N_in,
+                    std::vector<int>& ptr, std::vector<int>& col, std::vector<double>& w) {
+  const int M_out = p_out * N_out + 1, n = p_in + 1;
   ptr.assign(1, 0);
   col.clear();
   w.clear();
   for (int i = 0; i < M_out; ++i) {
-    const double x = node_coord(t, p, N_out, i);
+    const double x = node_coord(t_out, p_out, N_out, i);
     int e = int(std::floor(x * N_in + 1e-12));
     e = std::max(0, std::min(e, N_in - 1));
     const double xi = x * N_in - e;
     for (int b = 0; b < n; ++b) {
-      const double v = lagrange(t, n, b, xi);
+      const double v = lagrange(t_in, n, b, xi);
       if (std::fabs(v) < 1e-15) continue;
-      col.push_back(p * e + b);
+      col.push_back(p_in * e + b);
       w.push_back(v);
     }
     ptr.push_back((int)col.size());
@@ -197,38 +198,53 @@ void gmg_free(nhmf_ctx* c) {
   c->gmg = nullptr;
 }
 
-// Builds the hierarchy N, N/2, ... down to an odd N or N = 2 (at most 12 levels).
+// Builds the hierarchy: meshes N, N/2, ... (halving while N is even and N/2 >= 2) with the fine
+// degree p, then, for p > 1, one more level of degree 1 on the coarsest mesh (p-coarsening:
+// the coarsest solve then has at most a few hundred DoFs).
 nhmf_status gmg_build(nhmf_ctx* c) {
   if (c->gmg) return NHMF_OK;
-  std::vector<int> Ns{c->g.N};
-  while (Ns.back() % 2 == 0 && Ns.back() / 2 >= 2 && Ns.size() < 12) Ns.push_back(Ns.back() / 2);
+  std::vector<int> Ns{c->g.N}, Ps{c->g.p};
+  while (Ns.back() % 2 == 0 && Ns.back() / 2 >= 2 && Ns.size() < 12) {
+    Ns.push_back(Ns.back() / 2);
+    Ps.push_back(c->g.p);
+  }
+  if (c->g.p > 1) {
+    Ns.push_back(Ns.back());
+    Ps.push_back(1);
+  }
   c->gmg = new Gmg();
   Gmg& G = *c->gmg;
   const int nl = (int)Ns.size();
   G.L.resize(nl);
-  // material factors of every level: coarse elements take the mean of their eight children
+  // material factors per level (fine to coarse index k = nl - 1 - l): coarse elements take the
+  // mean of their eight children; a p-coarsened level keeps its mesh's factors
   std::vector<std::vector<double>> fac(nl);
   if (c->factor) {
-    fac[nl - 1].resize(c->g.E);
-    cudaMemcpy(fac[nl - 1].data(), c->factor, c->g.E * sizeof(double), cudaMemcpyDeviceToHost);
-    for (int l = nl - 2; l >= 0; --l) {
-      const int Nf = Ns[nl - 2 - l], Ncs = Ns[nl - 1 - l];
-      fac[l].assign((size_t)Ncs * Ncs * Ncs, 0.0);
+    fac[0].resize(c->g.E);
+    cudaMemcpy(fac[0].data(), c->factor, c->g.E * sizeof(double), cudaMemcpyDeviceToHost);
+    for (int k = 1; k < nl; ++k) {
+      const int Nf = Ns[k - 1], Ncs = Ns[k];
+      if (Nf == Ncs) {
+        fac[k] = fac[k - 1];
+        continue;
+      }
+      fac[k].assign((size_t)Ncs * Ncs * Ncs, 0.0);
       for (int z = 0; z < Nf; ++z)
         for (int y = 0; y < Nf; ++y)
           for (int x = 0; x < Nf; ++x)
-            fac[l][(x / 2) + (size_t)Ncs * ((y / 2) + (size_t)Ncs * (z / 2))] +=
-                0.125 * fac[l + 1][x + (size_t)Nf * (y + (size_t)Nf * z)];
+            fac[k][(x / 2) + (size_t)Ncs * ((y / 2) + (size_t)Ncs * (z / 2))] +=
+                0.125 * fac[k - 1][x + (size_t)Nf * (y + (size_t)Nf * z)];
     }
   }
   for (int l = 0; l < nl; ++l) {
-    const int N = Ns[nl - 1 - l];  // level 0 = coarsest
+    const int k = nl - 1 - l;  // index in Ns / Ps (0 = finest)
     GmgLevel& L = G.L[l];
     if (l == nl - 1) {
       L.ctx = c;
     } else {
       nhmf_params prm = c->prm;
-      prm.n_el = N;
+      prm.n_el = Ns[k];
+      prm.degree = Ps[k];
       nhmf_status st = nhmf_create(&prm, &L.ctx);
       if (st != NHMF_OK) {
         gmg_free(c);
@@ -236,8 +252,8 @@ nhmf_status gmg_build(nhmf_ctx* c) {
       }
       if (c->factor) {
         double* dev = nullptr;
-        bool fok = cudaMalloc(&dev, fac[l].size() * sizeof(double)) == cudaSuccess &&
-                   cudaMemcpy(dev, fac[l].data(), fac[l].size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        bool fok = cudaMalloc(&dev, fac[k].size() * sizeof(double)) == cudaSuccess &&
+                   cudaMemcpy(dev, fac[k].data(), fac[k].size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
         if (fok) st = nhmf_set_material_factors(L.ctx, dev, nullptr);
         cudaFree(dev);
         if (!fok || st != NHMF_OK) {
@@ -250,7 +266,7 @@ nhmf_status gmg_build(nhmf_ctx* c) {
       gmg_free(c);
       return fail(c, NHMF_ERR_OOM, "gmg: level work");
     }
-    L.M = c->g.p * N + 1;
+    L.M = Ps[k] * Ns[k] + 1;
     L.n = 3LL * L.M * L.M * L.M;
     bool ok = true;
     for (double** p : {&L.diag, &L.dinv, &L.x, &L.b, &L.r, &L.d, &L.q, &L.t1, &L.t2})
@@ -261,20 +277,25 @@ nhmf_status gmg_build(nhmf_ctx* c) {
       gmg_free(c);
       return fail(c, NHMF_ERR_OOM, "gmg: level vectors");
     }
-    if (l > 0) {
-      const int Nc = Ns[nl - l];
-      std::vector<int> ptr, col, tp, tc;
-      std::vector<double> w, tw;
-      build_eval_map(c->tab.nodes, c->g.p, N, Nc, ptr, col, w);  // prolongation: fine nodes from coarse
-      ok = upload(L.P, L.M, c->g.p * Nc + 1, ptr, col, w);
-      transpose_map(L.M, c->g.p * Nc + 1, ptr, col, w, tp, tc, tw);
-      ok = ok && upload(L.R, c->g.p * Nc + 1, L.M, tp, tc, tw);
-      build_eval_map(c->tab.nodes, c->g.p, Nc, N, ptr, col, w);  // interpolation: coarse nodes from fine
-      ok = ok && upload(L.I, c->g.p * Nc + 1, L.M, ptr, col, w);
-      if (!ok) {
-        gmg_free(c);
-        return fail(c, NHMF_ERR_OOM, "gmg: transfer maps");
-      }
+  }
+  for (int l = 1; l < nl; ++l) {
+    GmgLevel& L = G.L[l];
+    GmgLevel& C = G.L[l - 1];
+    const nhmf_ctx* fc = L.ctx;
+    const nhmf_ctx* cc = C.ctx;
+    std::vector<int> ptr, col, tp, tc;
+    std::vector<double> w, tw;
+    // prolongation: fine nodes from the coarse function; restriction: its transpose;
+    // interpolation of the linearisation point: coarse nodes from the fine function
+    build_eval_map(fc->tab.nodes, fc->g.p, fc->g.N, cc->tab.nodes, cc->g.p, cc->g.N, ptr, col, w);
+    bool ok = upload(L.P, L.M, C.M, ptr, col, w);
+    transpose_map(L.M, C.M, ptr, col, w, tp, tc, tw);
+    ok = ok && upload(L.R, C.M, L.M, tp, tc, tw);
+    build_eval_map(cc->tab.nodes, cc->g.p, cc->g.N, fc->tab.nodes, fc->g.p, fc->g.N, ptr, col, w);
+    ok = ok && upload(L.I, C.M, L.M, ptr, col, w);
+    if (!ok) {
+      gmg_free(c);
+      return fail(c, NHMF_ERR_OOM, "gmg: transfer maps");
     }
   }
   return NHMF_OK;
