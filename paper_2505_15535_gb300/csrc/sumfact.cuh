@@ -18,9 +18,17 @@ namespace nhmf {
 // several blocks per SM.
 template <int P, typename T> struct Cfg;
 template <> struct Cfg<1, double> { static constexpr int NE = 32, THREADS = 256; };
-template <> struct Cfg<2, double> { static constexpr int NE = 32, THREADS = 288; };
+#ifndef NHMF_Q2D_NE
+#define NHMF_Q2D_NE 32
+#define NHMF_Q2D_THREADS 288
+#endif
+#ifndef NHMF_Q4D_NE
+#define NHMF_Q4D_NE 8
+#define NHMF_Q4D_THREADS 256
+#endif
+template <> struct Cfg<2, double> { static constexpr int NE = NHMF_Q2D_NE, THREADS = NHMF_Q2D_THREADS; };
 template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; };
-template <> struct Cfg<4, double> { static constexpr int NE = 8, THREADS = 256; };
+template <> struct Cfg<4, double> { static constexpr int NE = NHMF_Q4D_NE, THREADS = NHMF_Q4D_THREADS; };
 template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; };
 template <> struct Cfg<2, float> { static constexpr int NE = 32, THREADS = 288; };
 template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
