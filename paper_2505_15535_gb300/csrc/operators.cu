@@ -102,8 +102,8 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 
 // ------------------------------------------------------------------ tangent application
 template <int P, typename T, int STRAT>
-__global__ void __launch_bounds__(Cfg<P, T>::THREADS) k_apply(const OpArgs a) {
-  constexpr int n = P + 1, n3 = n * n * n, NE = Cfg<P, T>::NE, NI = NE * n3;
+__global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
+  constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sB = reinterpret_cast<T*>(smem_raw);
   T* sDc = sB + kMaxN * kMaxN;
@@ -538,9 +538,9 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
 
 // ------------------------------------------------------------------ residual
 template <int P>
-__global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_residual(const OpArgs a) {
+__global__ void __launch_bounds__(LaunchCfg<P, double, 0>::THREADS) k_residual(const OpArgs a) {
   using T = double;
-  constexpr int n = P + 1, n3 = n * n * n, NE = Cfg<P, T>::NE, NI = NE * n3;
+  constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, 0>::NE, NI = NE * n3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sB = reinterpret_cast<T*>(smem_raw);
   T* sDc = sB + kMaxN * kMaxN;
@@ -779,7 +779,7 @@ nhmf_status fix_rows(nhmf_ctx* c, const T* src, T* out, int mode, T value, cudaS
 template <int P, typename T, int STRAT>
 nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t s) {
   using S = typename Store<T>::type;
-  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, T>::NE, NI = NE * n3;
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
   OpArgs a = base_args(c);
   if (raw) a.bc = NHMF_BC_NONE;  // unconstrained operator K: no masking, no identity rows
   a.u64 = c->ubar;
@@ -797,7 +797,8 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   if constexpr (sizeof(T) == 4 && P <= 2)
     st = run_colours(c, k_apply_reg<P, STRAT>, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
   else
-    st = run_colours(c, k_apply<P, T, STRAT>, a, NE, Cfg<P, T>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
+    st = run_colours(c, k_apply<P, T, STRAT>, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply",
+                     NHMF_KIND_APPLY);
   if (st != NHMF_OK || raw) return st;
   return fix_rows<S>(c, static_cast<const S*>(du), static_cast<S*>(v), 0, S(0), s);
 }
@@ -832,14 +833,15 @@ nhmf_status cache_p(nhmf_ctx* c, cudaStream_t s) {
 
 template <int P>
 nhmf_status residual_p(nhmf_ctx* c, const double* u, double* r, cudaStream_t s) {
-  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = Cfg<P, double>::NE, NI = NE * n3;
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = LaunchCfg<P, double, 0>::NE, NI = NE * n3;
   OpArgs a = base_args(c);
   a.u64 = u;
   a.v = r;
   const size_t smem = (kTabSlots + 12 * (size_t)NI) * sizeof(double);
   if (cudaError_t e = cudaMemsetAsync(r, 0, sizeof(double) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "residual memset");
-  nhmf_status st = run_colours(c, k_residual<P>, a, NE, Cfg<P, double>::THREADS, smem, s, "residual", NHMF_KIND_RESIDUAL);
+  nhmf_status st =
+      run_colours(c, k_residual<P>, a, NE, LaunchCfg<P, double, 0>::THREADS, smem, s, "residual", NHMF_KIND_RESIDUAL);
   if (st != NHMF_OK) return st;
   return fix_rows<double>(c, nullptr, r, 1, 0.0, s);
 }

@@ -23,7 +23,7 @@ template <> struct Cfg<1, double> { static constexpr int NE = 32, THREADS = 256;
 #define NHMF_Q2D_THREADS 288
 #endif
 #ifndef NHMF_Q4D_NE
-#define NHMF_Q4D_NE 8
+#define NHMF_Q4D_NE 4
 #define NHMF_Q4D_THREADS 256
 #endif
 template <> struct Cfg<2, double> { static constexpr int NE = NHMF_Q2D_NE, THREADS = NHMF_Q2D_THREADS; };
@@ -35,6 +35,10 @@ template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; }
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
+// Shapes per strategy where they differ (measured on GB300): the on-the-fly FP64 Q2 apply (and
+// the residual, which has the same work) runs best with 8 elements on 216 threads.
+template <int P, typename T, int STRAT> struct LaunchCfg : Cfg<P, T> {};
+template <> struct LaunchCfg<2, double, 0> { static constexpr int NE = 8, THREADS = 216; };
 
 // Kernel arguments (by value; lives in the constant bank).
 struct OpArgs {
