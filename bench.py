@@ -40,6 +40,31 @@ FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+KERNEL_SOURCES = ["include/nhmf.h", "paper_2505_15535_gb300/csrc/operators.cu",
+                  "paper_2505_15535_gb300/csrc/sumfact.cuh", "paper_2505_15535_gb300/csrc/df64.cuh",
+                  "paper_2505_15535_gb300/csrc/internal.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_apply_fp64_cached_q2_64.traffic.json")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per apply of the FP64 cached Q2 64^3 kernel from the committed ncu capture,
+    or None when the kernel sources changed since that capture."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    return d.get("dram_bytes_per_apply") if d.get("source_sha256") == kernel_source_hash() else None
+
+
 def canonical_flops(w: inp.Workload, strategy: str) -> float:
     """Algorithmic FLOPs of one apply: 2 n^4 per 1D pass per scalar field per element
     (54 passes on the fly: 18 for u, 18 for du, 18 back; 36 cached) plus the point code
@@ -275,8 +300,10 @@ def run_gpu(args):
     # ---- roofline of the apply kernel (FP64 pipe)
     flops = canonical_flops(w, strategy)
     achieved = flops / (kernel_ms * 1e-3) / 1e12
+    traffic = measured_traffic() if (main == MAIN and strategy == "cached") else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "algorithmic_bytes": compulsory_bytes(w, strategy, 8),
                 "kernel": f"k_apply<2,double,{strategy}> (8 colour launches per apply)",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz (FMA loop measured 1.20)",
                 "flops_per_apply": flops}

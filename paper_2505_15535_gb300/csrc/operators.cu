@@ -15,7 +15,7 @@
 namespace nhmf {
 namespace {
 
-constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128;  // B, Dc, D tables + n^3 weights (+pad)
+constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128 + 32;  // B, Dc, D tables, n^3 weights, NE factors
 
 template <int P, typename T>
 __device__ __forceinline__ void load_tables(const OpArgs& a, T* sB, T* sDc, T* sD, T* sW, double wscale) {
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   T* sDc = sB + kMaxN * kMaxN;
   T* sD = sDc + kMaxN * kMaxN;
   T* sW = sD + kMaxN * kMaxN;
+  T* sF = sW + 128;                             // [NE] material factors of the block's elements
   T* U = sB + kTabSlots;                        // [3][NI] ubar at the points (on the fly)
   T* Vq = U + (STRAT == NHMF_ON_THE_FLY ? 3 * NI : 0);  // [3][NI] du at the points
   T* G = Vq + 3 * NI;                           // [9][NI] fluxes; G[0..2] doubles as gather buffer
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   const long long e0 = (long long)blockIdx.x * NE;
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
   const T invh = T(1.0 / a.h);
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) sF[e] = T(elem_factor(a, e0 + min(e, nvalid - 1)));
 
   if constexpr (STRAT == NHMF_ON_THE_FLY) {
     if (sizeof(T) == 8)
@@ -157,8 +159,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
       }
       T dH[9], g[9];
       colloc_grad<n, NI>(sDc, Vq, t, dH);
-      const T sf = a.factor ? sW[t % n3] * T(elem_factor(a, e0 + min(t / n3, nvalid - 1))) : sW[t % n3];
-      spatial_stress(Jc, tau, Fs, dH, sf, g);
+      spatial_stress(Jc, tau, Fs, dH, sW[t % n3] * sF[t / n3], g);
 #pragma unroll
       for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
       continue;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
     }
     T dH[9], g[9];
     colloc_grad<n, NI>(sDc, Vq, t, dH);
-    const T sf = a.factor ? sW[t % n3] * T(elem_factor(a, e0 + min(t / n3, nvalid - 1))) : sW[t % n3];
+    const T sf = sW[t % n3] * sF[t / n3];
     if constexpr (STRAT == NHMF_ON_THE_FLY)
       model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, sf, g);
     else

@@ -35,10 +35,8 @@ template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; }
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
-// Shapes per strategy where they differ (measured on GB300): the on-the-fly FP64 Q2 apply (and
-// the residual, which has the same work) runs best with 8 elements on 216 threads.
+// Launch shape per strategy (a hook for strategy-specific tuning; all use Cfg today).
 template <int P, typename T, int STRAT> struct LaunchCfg : Cfg<P, T> {};
-template <> struct LaunchCfg<2, double, 0> { static constexpr int NE = 8, THREADS = 216; };
 
 // Kernel arguments (by value; lives in the constant bank).
 struct OpArgs {
