@@ -101,7 +101,7 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 }
 
 // ------------------------------------------------------------------ tangent application
-template <int P, typename T, int STRAT>
+template <int P, typename T, int STRAT, int MODEL>
 __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
     T dH[9], g[9];
     colloc_grad<n, NI>(sDc, Vq, t, dH);
     const T sf = sW[t % n3] * sF[t / n3];
-    if constexpr (STRAT == NHMF_ON_THE_FLY)
-      model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, sf, g);
+    if constexpr (STRAT == NHMF_ON_THE_FLY && MODEL == NHMF_MODEL_SPLIT)
+      split_stress_dP(F, Fi, lnJ, Jm1, dH, mu, lam, sf, g);
     else
       linearised_stress(Fi, lnJ, dH, mu, lam, sf, g);
 #pragma unroll
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 // the Gauss points and the transposed-derivative accumulators stay in registers; every 1D pass
 // is fully unrolled, so its coefficients are compile-time-indexed kernel parameters (constant
 // bank operands of the FMAs) and no shared memory is touched.  For p <= 2.
-template <int P, int STRAT>
+template <int P, int STRAT, int MODEL>
 __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n;
   const long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
         }
         float dH[9], g[9];
         grad_at(qv, qx, qy, qz, dH);
-        if constexpr (STRAT == NHMF_ON_THE_FLY)
-          model_dP(a.model, F, Fi, lnJ, Jm1, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
+        if constexpr (STRAT == NHMF_ON_THE_FLY && MODEL == NHMF_MODEL_SPLIT)
+          split_stress_dP(F, Fi, lnJ, Jm1, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
         else
           linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
         // transposed collocation derivative: acc[c][point on the line through q] += Dc[q][m] g
@@ -795,11 +795,17 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
     return cuda_check(c, e, "apply memset");
   nhmf_status st;
-  if constexpr (sizeof(T) == 4 && P <= 2)
-    st = run_colours(c, k_apply_reg<P, STRAT>, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
-  else
-    st = run_colours(c, k_apply<P, T, STRAT>, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply",
-                     NHMF_KIND_APPLY);
+  // the energy model is a compile-time parameter of the on-the-fly point code (a runtime
+  // branch would charge the split model's registers to every model)
+  constexpr int SPLIT = STRAT == NHMF_ON_THE_FLY ? NHMF_MODEL_SPLIT : NHMF_MODEL_COMPRESSIBLE;
+  const bool split = STRAT == NHMF_ON_THE_FLY && c->prm.model == NHMF_MODEL_SPLIT;
+  if constexpr (sizeof(T) == 4 && P <= 2) {
+    auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
+    st = run_colours(c, k, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
+  } else {
+    auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;
+    st = run_colours(c, k, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
+  }
   if (st != NHMF_OK || raw) return st;
   return fix_rows<S>(c, static_cast<const S*>(du), static_cast<S*>(v), 0, S(0), s);
 }
