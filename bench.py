@@ -257,7 +257,9 @@ def run_gpu(args):
     prob = nhmf.Problem.from_workload(w)
     ut = torch.from_numpy(u).to(dev)
     t0 = time.perf_counter()
-    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
+    # the variants reuse this problem's FP32, double-float and Algorithm 2 caches
+    prob.set_linearization(ut, nhmf.NHMF_CACHE_FP64 if args.no_variants else
+                           nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64 |
                            nhmf.NHMF_CACHE_SPATIAL)
     torch.cuda.synchronize()
     cache_build_s = time.perf_counter() - t0

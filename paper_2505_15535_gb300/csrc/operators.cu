@@ -15,7 +15,10 @@
 namespace nhmf {
 namespace {
 
-constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128 + 32;  // B, Dc, D tables, n^3 weights, NE factors
+// Table slots ahead of the per-item arrays: B, Dc, D, n^3 weights and NE factors, or in the
+// apply B, Dc, BW, DcW, Dch, 3 even-odd sets and NE factors (whichever is larger).
+constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128 + 32;
+static_assert(5 * kMaxN * kMaxN + 3 * kEoSlots + 32 <= kTabSlots, "apply tables exceed the table slots");
 
 template <int P, typename T>
 __device__ __forceinline__ void load_tables(const OpArgs& a, T* sB, T* sDc, T* sD, T* sW, double wscale) {
@@ -29,11 +32,28 @@ __device__ __forceinline__ void load_tables(const OpArgs& a, T* sB, T* sDc, T* s
     sW[q] = T(a.w[q % n] * a.w[(q / n) % n] * a.w[q / (n * n)] * wscale);
 }
 
+// The apply's tables: B and Dc (forward), BW and DcW (transposed, carrying w, mu, h), Dch and
+// the even-odd coefficient sets, laid out as in k_apply.
+template <int P, typename T>
+__device__ __forceinline__ void load_apply_tables(const OpArgs& a, T* tab) {
+  constexpr int n = P + 1, S = kMaxN * kMaxN;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    tab[i] = T(a.B[i]);
+    tab[S + i] = T(a.Dc[i]);
+    tab[2 * S + i] = T(a.BW[i]);
+    tab[3 * S + i] = T(a.DcW[i]);
+    tab[4 * S + i] = T(a.Dch[i]);
+  }
+  for (int i = threadIdx.x; i < 3 * kEoSlots; i += blockDim.x)
+    tab[5 * S + i] = T(a.eo[i / kEoSlots][i % kEoSlots]);
+}
+
 // Gather three components of a global vector into dst[c][t] for the block's elements,
-// optionally zeroing constrained DoFs; items of absent elements are zero.
+// optionally zeroing constrained DoFs and scaling by a per-element factor fac[e]; items of
+// absent elements are zero.
 template <int P, int NI, typename TS, typename T>
 __device__ __forceinline__ void gather(const OpArgs& a, const TS* __restrict__ src, long long e0,
-                                       int nvalid, bool mask, T* dst) {
+                                       int nvalid, bool mask, T* dst, const T* fac = nullptr) {
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1);
   for (int t = threadIdx.x; t < NI; t += blockDim.x) {
     const int e = t / n3;
@@ -45,7 +65,7 @@ __device__ __forceinline__ void gather(const OpArgs& a, const TS* __restrict__ s
       for (int c = 0; c < 3; ++c) {
         T val = T(src[c * a.M3 + node]);
         if (mask && is_constrained(a.bc, c, gi, gk, a.M)) val = T(0);
-        dst[c * NI + t] = val;
+        dst[c * NI + t] = fac ? val * fac[e] : val;
       }
     } else {
 #pragma unroll
@@ -101,24 +121,37 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 }
 
 // ------------------------------------------------------------------ tangent application
+// The quadrature weight, mu and h ride on the transposed tables (BW, DcW) and the element's
+// material factor on the gathered du (the operator is linear in du), so the point code returns
+// dP / mu without any scaling.  For odd n (Q2, Q4) every non-accumulating pass (forward B,
+// forward collocation derivative, transposed B) runs one thread per line in even-odd form, and
+// the gradient of du reaches the point code through shared memory.
 template <int P, typename T, int STRAT, int MODEL>
 __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
+  constexpr int S = kMaxN * kMaxN;
+  constexpr bool EO = n % 2 == 1;
+  static_assert(NE <= 32, "the factor table holds 32 elements");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sB = reinterpret_cast<T*>(smem_raw);
-  T* sDc = sB + kMaxN * kMaxN;
-  T* sD = sDc + kMaxN * kMaxN;
-  T* sW = sD + kMaxN * kMaxN;
-  T* sF = sW + 128;                             // [NE] material factors of the block's elements
-  T* U = sB + kTabSlots;                        // [3][NI] ubar at the points (on the fly)
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  const T* sB = tab;
+  const T* sDc = tab + S;
+  const T* sBW = tab + 2 * S;
+  const T* sDcW = tab + 3 * S;
+  const T* sDch = tab + 4 * S;
+  const T* kB = tab + 5 * S;                    // even-odd coefficients of B, Dc, BW^T
+  const T* kDc = kB + kEoSlots;
+  const T* kBW = kDc + kEoSlots;
+  T* sF = tab + 5 * S + 3 * kEoSlots;          // [NE] material factors of the block's elements
+  T* U = tab + kTabSlots;                       // [3][NI] ubar at the points (on the fly)
   T* Vq = U + (STRAT == NHMF_ON_THE_FLY ? 3 * NI : 0);  // [3][NI] du at the points
-  T* G = Vq + 3 * NI;                           // [9][NI] fluxes; G[0..2] doubles as gather buffer
+  T* G = Vq + 3 * NI;                           // [9][NI] gradients, then fluxes; G[0..2] gathers
 
-  load_tables<P>(a, sB, sDc, sD, sW, a.h);
+  load_apply_tables<P>(a, tab);
   const long long e0 = (long long)blockIdx.x * NE;
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
-  const T invh = T(1.0 / a.h);
   for (int e = threadIdx.x; e < NE; e += blockDim.x) sF[e] = T(elem_factor(a, e0 + min(e, nvalid - 1)));
+  __syncthreads();
 
   if constexpr (STRAT == NHMF_ON_THE_FLY) {
     if (sizeof(T) == 8)
@@ -126,18 +159,48 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
     else
       gather<P, NI>(a, a.u32, e0, nvalid, false, G);
     __syncthreads();
-    to_points<n, NI>(sB, G, Vq, U);
+    if constexpr (EO) {
+      eo_pass<n, NI, 3, 0, false>(kB, G, Vq);
+      __syncthreads();
+      eo_pass<n, NI, 3, 1, false>(kB, Vq, G);
+      __syncthreads();
+      eo_pass<n, NI, 3, 2, false>(kB, G, U);
+      __syncthreads();
+    } else {
+      to_points<n, NI>(sB, G, Vq, U);
+    }
   }
-  gather<P, NI>(a, static_cast<const typename Store<T>::type*>(a.du), e0, nvalid, true, G);
+  gather<P, NI>(a, static_cast<const typename Store<T>::type*>(a.du), e0, nvalid, true, G,
+                a.factor ? (const T*)sF : nullptr);
   __syncthreads();
-  to_points<n, NI>(sB, G, Vq + 0, Vq);  // in-place target is fine: passes ping-pong via G
-  // (to_points(in=G, tmp=Vq, out=Vq): x: G->Vq, y: Vq->G, z: G->Vq)
+  if constexpr (EO) {
+    eo_pass<n, NI, 3, 0, false>(kB, G, Vq);
+    __syncthreads();
+    eo_pass<n, NI, 3, 1, false>(kB, Vq, G);
+    __syncthreads();
+    eo_pass<n, NI, 3, 2, false>(kB, G, Vq);
+    __syncthreads();
+    // reference gradient of du: G[3c+d] = Dc along d of du[c]
+    eo_pass<n, NI, 3, 0, true, 3, 0>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 1, true, 3, 1>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 2, true, 3, 2>(kDc, Vq, G);
+    __syncthreads();
+  } else {
+    to_points<n, NI>(sB, G, Vq + 0, Vq);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
+  }
 
-  const T mu = T(a.mu), lam = T(a.lam);
+  const T inv_mu = T(1.0 / a.mu), r2 = T(a.r2mu);
   const typename Store<T>::type* cache = static_cast<const typename Store<T>::type*>(a.cache);
   const long long cbase = (a.col.slot0 + e0) * n3;
   bool bad = false;
   for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+    T dH[9], g[9];
+    if constexpr (EO) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dH[k] = G[k * NI + t];
+    } else {
+      colloc_grad<n, NI>(sDc, Vq, t, dH);
+    }
     if constexpr (STRAT == NHMF_SPATIAL) {
       // Algorithm 2: J c, tau and F^-1 from the 36-value cache
       T Jc[21], tau[6], Fs[9];
@@ -157,9 +220,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 #pragma unroll
         for (int k = 0; k < 9; ++k) Fs[k] = (k % 4 == 0) ? T(1) : T(0);
       }
-      T dH[9], g[9];
-      colloc_grad<n, NI>(sDc, Vq, t, dH);
-      spatial_stress(Jc, tau, Fs, dH, sW[t % n3] * sF[t / n3], g);
+      spatial_stress(Jc, tau, Fs, dH, inv_mu, g);
 #pragma unroll
       for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
       continue;
@@ -167,9 +228,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
     T Fi[9], lnJ, Jm1 = T(0), F[9];
     if constexpr (STRAT == NHMF_ON_THE_FLY) {
       T H[9];
-      colloc_grad<n, NI>(sDc, U, t, H);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) H[k] *= invh;
+      colloc_grad<n, NI>(sDch, U, t, H);  // physical gradient: Dch = Dc / h
       Jm1 = kinematics(H, Fi, lnJ);
       bad |= !(Jm1 > T(-1));
 #pragma unroll
@@ -201,19 +260,27 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
         lnJ = T(0);
       }
     }
-    T dH[9], g[9];
-    colloc_grad<n, NI>(sDc, Vq, t, dH);
-    const T sf = sW[t % n3] * sF[t / n3];
     if constexpr (STRAT == NHMF_ON_THE_FLY && MODEL == NHMF_MODEL_SPLIT)
-      split_stress_dP(F, Fi, lnJ, Jm1, dH, mu, lam, sf, g);
+      split_stress_dP(F, Fi, lnJ, Jm1, dH, T(a.mu), T(a.lam), inv_mu, g);
     else
-      linearised_stress(Fi, lnJ, dH, mu, lam, sf, g);
+      linearised_stress_unit(Fi, lnJ, dH, r2, g);
 #pragma unroll
     for (int k = 0; k < 9; ++k) G[k * NI + t] = g[k];
   }
   if (bad) atomicOr(a.status, kStatusNonPosJ);
   __syncthreads();
-  from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
+  if constexpr (EO) {
+    colloc_grad_T<n, NI>(sDcW, G, Vq);
+    __syncthreads();
+    eo_pass<n, NI, 3, 0, false>(kBW, Vq, G);
+    __syncthreads();
+    eo_pass<n, NI, 3, 1, false>(kBW, G, Vq);
+    __syncthreads();
+    eo_pass<n, NI, 3, 2, false>(kBW, Vq, G + 3 * NI);
+    __syncthreads();
+  } else {
+    from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI);
+  }
   scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<typename Store<T>::type*>(a.v));
 }
 
@@ -708,6 +775,19 @@ __global__ void k_to_fp32(const double* x, float* y, long long n) {
 }
 
 // ------------------------------------------------------------------ host side
+// Even-odd coefficients (see eo_line) of the n x n row-major operator M, odd n.
+void eo_pack(const double* M, int n, double* k) {
+  const int h = n / 2, A0 = (h + 1) * h, C0 = 2 * (h + 1) * h;
+  for (int i = 0; i < kEoSlots; ++i) k[i] = 0.0;
+  for (int r = 0; r <= h; ++r) {
+    for (int m = 0; m < h; ++m) {
+      k[r * h + m] = 0.5 * (M[r * n + m] + M[r * n + n - 1 - m]);
+      k[A0 + r * h + m] = 0.5 * (M[r * n + m] - M[r * n + n - 1 - m]);
+    }
+    k[C0 + r] = M[r * n + h];
+  }
+}
+
 OpArgs base_args(nhmf_ctx* c) {
   OpArgs a{};
   a.N = c->g.N;
@@ -731,6 +811,22 @@ OpArgs base_args(nhmf_ctx* c) {
     }
     a.wf[q] = float(c->tab.w[q]);
   }
+  // tables of the tangent apply (see OpArgs)
+  double BWt[kMaxN * kMaxN];
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < n; ++i) {
+      const double wq = c->tab.w[q];
+      a.BW[q * n + i] = c->tab.B[q][i] * wq;
+      BWt[i * n + q] = a.BW[q * n + i];
+      a.DcW[q * n + i] = c->tab.Dc[q][i] * wq / c->tab.w[i] * c->prm.mu * c->g.h;
+      a.Dch[q * n + i] = c->tab.Dc[q][i] / c->g.h;
+    }
+  if (n % 2 == 1) {
+    eo_pack(a.B, n, a.eo[0]);
+    eo_pack(a.Dc, n, a.eo[1]);
+    eo_pack(BWt, n, a.eo[2]);
+  }
+  a.r2mu = 2.0 * c->prm.lambda / c->prm.mu;
   a.status = c->status;
   a.factor = c->factor;
   return a;

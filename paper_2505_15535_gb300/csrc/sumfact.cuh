@@ -24,7 +24,7 @@ template <> struct Cfg<1, double> { static constexpr int NE = 32, THREADS = 256;
 #endif
 #ifndef NHMF_Q4D_NE
 #define NHMF_Q4D_NE 4
-#define NHMF_Q4D_THREADS 256
+#define NHMF_Q4D_THREADS 320
 #endif
 template <> struct Cfg<2, double> { static constexpr int NE = NHMF_Q2D_NE, THREADS = NHMF_Q2D_THREADS; };
 template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; };
@@ -35,8 +35,15 @@ template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; }
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
-// Launch shape per strategy (a hook for strategy-specific tuning; all use Cfg today).
+template <> struct Cfg<4, df64> { static constexpr int NE = 4, THREADS = 256; };
+// Launch shape per strategy: Algorithm 2's point code (120 registers) keeps 256 threads at Q4
+// so that two blocks fit an SM.
 template <int P, typename T, int STRAT> struct LaunchCfg : Cfg<P, T> {};
+template <> struct LaunchCfg<4, double, NHMF_SPATIAL> { static constexpr int NE = 4, THREADS = 256; };
+
+// Coefficients of one n x n operator in even-odd form (odd n <= 5): S, A ((h+1) x h each) and C
+// (h+1), h = n / 2.
+constexpr int kEoSlots = 16;
 
 // Kernel arguments (by value; lives in the constant bank).
 struct OpArgs {
@@ -45,6 +52,13 @@ struct OpArgs {
   double h, mu, lam;
   Colour col;
   double B[kMaxN * kMaxN], Dc[kMaxN * kMaxN], D[kMaxN * kMaxN], w[kMaxN];
+  // Tables of the tangent apply, which carry the quadrature weight, mu and h so that its
+  // point code returns dP / mu unweighted:
+  //   BW[q][i] = B[q][i] w_q,  DcW[m][r] = Dc[m][r] w_m / w_r mu h,  Dch = Dc / h,
+  //   eo[0..2]: even-odd coefficients of B, Dc and BW^T (odd n, see eo_line), r2mu = 2 lambda / mu.
+  double BW[kMaxN * kMaxN], DcW[kMaxN * kMaxN], Dch[kMaxN * kMaxN];
+  double eo[3][kEoSlots];
+  double r2mu;
   float Bf[kMaxN * kMaxN], Dcf[kMaxN * kMaxN], wf[kMaxN];  // FP32 copies (register kernels)
   const double* u64;
   const float* u32;
@@ -117,6 +131,72 @@ __device__ __forceinline__ void sf_pass(const T* __restrict__ mat, const T* in, 
       else
         out[c * NI + t] = acc[c];
     }
+  }
+}
+
+// One line x[0..n-1] through a centro-symmetric operator (ANTI = false: M[n-1-r][n-1-m] =
+// M[r][m], as B and B^T w have) or an anti-centro-symmetric one (ANTI = true: = -M[r][m], as the
+// collocation derivative has), odd n, in even-odd form (h = n / 2, m < h, r < h):
+//   e_m = x_m + x_{n-1-m},  o_m = x_m - x_{n-1-m},
+//   E_r = C_r x_h + sum_m S_rm e_m,  O_r = sum_m A_rm o_m,
+//   y_r = E_r + O_r,  y_{n-1-r} = +-(E_r - O_r),  y_h = E_h (symmetric) or O_h (anti),
+// with S_rm = (M_rm + M_r,n-1-m) / 2, A_rm = (M_rm - M_r,n-1-m) / 2, C_r = M_rh.  n = 3 takes 8
+// (symmetric) or 7 (anti) operations per line instead of 9; n = 5 takes 21 or 20 instead of 25.
+template <int n, bool ANTI, typename T>
+__device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n], T (&y)[n]) {
+  constexpr int h = n / 2, A0 = (h + 1) * h, C0 = 2 * (h + 1) * h;
+  T e[h], o[h];
+#pragma unroll
+  for (int m = 0; m < h; ++m) {
+    e[m] = x[m] + x[n - 1 - m];
+    o[m] = x[m] - x[n - 1 - m];
+  }
+#pragma unroll
+  for (int r = 0; r < h; ++r) {
+    T E = k[C0 + r] * x[h];
+#pragma unroll
+    for (int m = 0; m < h; ++m) E = fma(k[r * h + m], e[m], E);
+    T yp = E, ym = ANTI ? -E : E;
+#pragma unroll
+    for (int m = 0; m < h; ++m) {
+      yp = fma(k[A0 + r * h + m], o[m], yp);
+      ym = fma(ANTI ? k[A0 + r * h + m] : -k[A0 + r * h + m], o[m], ym);
+    }
+    y[r] = yp;
+    y[n - 1 - r] = ym;
+  }
+  if constexpr (ANTI) {
+    T c = k[A0 + h * h] * o[0];
+#pragma unroll
+    for (int m = 1; m < h; ++m) c = fma(k[A0 + h * h + m], o[m], c);
+    y[h] = c;
+  } else {
+    T c = k[C0 + h] * x[h];
+#pragma unroll
+    for (int m = 0; m < h; ++m) c = fma(k[h * h + m], e[m], c);
+    y[h] = c;
+  }
+}
+
+// One 1D pass along DIR over NC fields with one thread per (field, line of n items), odd n:
+//   out[(c OS + OO)][line] = M in[c][line]
+// where M is given by its even-odd coefficients `coef` (see eo_line).
+template <int n, int NI, int NC, int DIR, bool ANTI, int OS = 1, int OO = 0, typename T>
+__device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* in, T* out) {
+  constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n;
+  T k[kEoSlots];
+#pragma unroll
+  for (int i = 0; i < kEoSlots; ++i) k[i] = coef[i];
+  for (int task = threadIdx.x; task < NC * NL; task += blockDim.x) {
+    const int c = task / NL, L = task - c * NL;
+    const int base = DIR == 0 ? L * n
+                   : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
+    T x[n], y[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) x[m] = in[c * NI + base + m * s];
+    eo_line<n, ANTI>(k, x, y);
+#pragma unroll
+    for (int m = 0; m < n; ++m) out[(c * OS + OO) * NI + base + m * s] = y[m];
   }
 }
 
@@ -221,6 +301,28 @@ __device__ __forceinline__ void linearised_stress(const T Fi[9], T lnJ, const T 
       // Q[j][i] = sum_c K[j][c] Fi[c][i]
       const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
       g[3 * i + j] = fma(smu, dH[3 * i + j], fma(sc1, Qji, sc2 * Fi[3 * j + i]));
+    }
+}
+
+// The same linearised stress divided by mu and without the point weight (the tangent apply
+// carries w_q, mu and h on its transposed tables), r = 2 lambda / mu:
+//   g = dH + (1 - r ln J) Q^T + r tr(K) F^-T.
+template <typename T>
+__device__ __forceinline__ void linearised_stress_unit(const T Fi[9], T lnJ, const T dH[9], T r, T g[9]) {
+  T K[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      K[3 * i + j] = fma(Fi[3 * i + 0], dH[j], fma(Fi[3 * i + 1], dH[3 + j], Fi[3 * i + 2] * dH[6 + j]));
+  const T c1 = fma(-r, lnJ, T(1));
+  const T c2 = r * (K[0] + K[4] + K[8]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T Qji = fma(K[3 * j + 0], Fi[i], fma(K[3 * j + 1], Fi[3 + i], K[3 * j + 2] * Fi[6 + i]));
+      g[3 * i + j] = fma(c1, Qji, fma(c2, Fi[3 * j + i], dH[3 * i + j]));
     }
 }
 
