@@ -129,9 +129,9 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 template <int P, typename T, int STRAT, int MODEL>
 __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
-  constexpr int S = kMaxN * kMaxN;
+  constexpr int S = kMaxN * kMaxN, TH = LaunchCfg<P, T, STRAT>::THREADS;
   constexpr bool EO = n % 2 == 1;
-  static_assert(NE <= 32, "the factor table holds 32 elements");
+  static_assert(5 * S + 3 * kEoSlots + NE <= kTabSlots, "the factor table exceeds the table slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);
   const T* sB = tab;
@@ -160,11 +160,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
       gather<P, NI>(a, a.u32, e0, nvalid, false, G);
     __syncthreads();
     if constexpr (EO) {
-      eo_pass<n, NI, 3, 0, false>(kB, G, Vq);
+      eo_pass<n, NI, 3, 0, false, TH>(kB, G, Vq);
       __syncthreads();
-      eo_pass<n, NI, 3, 1, false>(kB, Vq, G);
+      eo_pass<n, NI, 3, 1, false, TH>(kB, Vq, G);
       __syncthreads();
-      eo_pass<n, NI, 3, 2, false>(kB, G, U);
+      eo_pass<n, NI, 3, 2, false, TH>(kB, G, U);
       __syncthreads();
     } else {
       to_points<n, NI>(sB, G, Vq, U);
@@ -174,16 +174,16 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
                 a.factor ? (const T*)sF : nullptr);
   __syncthreads();
   if constexpr (EO) {
-    eo_pass<n, NI, 3, 0, false>(kB, G, Vq);
+    eo_pass<n, NI, 3, 0, false, TH>(kB, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false>(kB, Vq, G);
+    eo_pass<n, NI, 3, 1, false, TH>(kB, Vq, G);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false>(kB, G, Vq);
+    eo_pass<n, NI, 3, 2, false, TH>(kB, G, Vq);
     __syncthreads();
     // reference gradient of du: G[3c+d] = Dc along d of du[c]
-    eo_pass<n, NI, 3, 0, true, 3, 0>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 1, true, 3, 1>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 2, true, 3, 2>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 0, true, TH, 3, 0>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 1, true, TH, 3, 1>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 2, true, TH, 3, 2>(kDc, Vq, G);
     __syncthreads();
   } else {
     to_points<n, NI>(sB, G, Vq + 0, Vq);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
           }
           const float2 z = cdf[9 * a.nq + cbase + t];
           lnJ = T(z.x, z.y);
-        } else if (sizeof(typename Store<T>::type) == 8 || P > 2) {
+        } else if (sizeof(typename Store<T>::type) == 8 || P > kRegMaxP) {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
           lnJ = T(cache[9 * a.nq + cbase + t]);
@@ -272,11 +272,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   if constexpr (EO) {
     colloc_grad_T<n, NI>(sDcW, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 0, false>(kBW, Vq, G);
+    eo_pass<n, NI, 3, 0, false, TH>(kBW, Vq, G);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false>(kBW, G, Vq);
+    eo_pass<n, NI, 3, 1, false, TH>(kBW, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false>(kBW, Vq, G + 3 * NI);
+    eo_pass<n, NI, 3, 2, false, TH>(kBW, Vq, G + 3 * NI);
     __syncthreads();
   } else {
     from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI);
@@ -288,7 +288,10 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 // One thread per element: the element's three components (3 (p+1)^3 values), their values at
 // the Gauss points and the transposed-derivative accumulators stay in registers; every 1D pass
 // is fully unrolled, so its coefficients are compile-time-indexed kernel parameters (constant
-// bank operands of the FMAs) and no shared memory is touched.  For p <= 2.
+// bank operands of the FMAs) and no shared memory is touched.  For p <= 2.  As in k_apply, w_q,
+// mu and h ride on the transposed tables and the material factor on du.  The on-the-fly kernel
+// runs its B and B^T passes in even-odd form at odd n; the cached kernel keeps the matrix form,
+// whose unrolled code fits its registers without spilling.
 template <int P, int STRAT, int MODEL>
 __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n;
@@ -304,68 +307,50 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
   auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
   auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
 
-  // sum-factorised interpolation of three components to the points, in place
+  // one 1D pass over the n^2 lines of direction DIR of f[c]: even-odd coefficients `eo` (odd
+  // n) or the matrix Mat(r, m) = mat[r n + m] (TR = false) / mat[m n + r] (TR = true)
+  auto pass = [&](float (&f)[n3], int dir, const float (&eo)[kEoSlots], const float* mat, bool tr) {
+    const int st = dir == 0 ? 1 : (dir == 1 ? n : n * n);
+#pragma unroll
+    for (int b = 0; b < n * n; ++b) {
+      const int base = dir == 0 ? b * n : (dir == 1 ? (b % n) + (b / n) * n * n : b);
+      float x[n], y[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) x[m] = f[base + m * st];
+      if constexpr (n % 2 == 1 && STRAT == NHMF_ON_THE_FLY) {
+        eo_line<n, false>(eo, x, y);
+      } else {
+#pragma unroll
+        for (int r = 0; r < n; ++r) {
+          float s = (tr ? mat[r] : mat[r * n]) * x[0];
+#pragma unroll
+          for (int m = 1; m < n; ++m) s = fmaf(tr ? mat[m * n + r] : mat[r * n + m], x[m], s);
+          y[r] = s;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < n; ++m) f[base + m * st] = y[m];
+    }
+  };
   auto to_points = [&](float (&f)[3][n3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          float t[n];
-#pragma unroll
-          for (int r = 0; r < n; ++r) {
-            float s = a.Bf[r * n] * f[c][idx(0, j, k)];
-#pragma unroll
-            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(m, j, k)], s);
-            t[r] = s;
-          }
-#pragma unroll
-          for (int r = 0; r < n; ++r) f[c][idx(r, j, k)] = t[r];
-        }
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-          float t[n];
-#pragma unroll
-          for (int r = 0; r < n; ++r) {
-            float s = a.Bf[r * n] * f[c][idx(i, 0, k)];
-#pragma unroll
-            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(i, m, k)], s);
-            t[r] = s;
-          }
-#pragma unroll
-          for (int r = 0; r < n; ++r) f[c][idx(i, r, k)] = t[r];
-        }
-#pragma unroll
-      for (int j = 0; j < n; ++j)
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-          float t[n];
-#pragma unroll
-          for (int r = 0; r < n; ++r) {
-            float s = a.Bf[r * n] * f[c][idx(i, j, 0)];
-#pragma unroll
-            for (int m = 1; m < n; ++m) s = fmaf(a.Bf[r * n + m], f[c][idx(i, j, m)], s);
-            t[r] = s;
-          }
-#pragma unroll
-          for (int r = 0; r < n; ++r) f[c][idx(i, j, r)] = t[r];
-        }
+      pass(f[c], 0, a.eof[0], a.Bf, false);
+      pass(f[c], 1, a.eof[0], a.Bf, false);
+      pass(f[c], 2, a.eof[0], a.Bf, false);
     }
   };
-  auto grad_at = [&](const float (&f)[3][n3], int qx, int qy, int qz, float g[9]) {
+  auto grad_at = [&](const float* Dc, const float (&f)[3][n3], int qx, int qy, int qz, float g[9]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float gx = a.Dcf[qx * n] * f[c][idx(0, qy, qz)];
-      float gy = a.Dcf[qy * n] * f[c][idx(qx, 0, qz)];
-      float gz = a.Dcf[qz * n] * f[c][idx(qx, qy, 0)];
+      float gx = Dc[qx * n] * f[c][idx(0, qy, qz)];
+      float gy = Dc[qy * n] * f[c][idx(qx, 0, qz)];
+      float gz = Dc[qz * n] * f[c][idx(qx, qy, 0)];
 #pragma unroll
       for (int m = 1; m < n; ++m) {
-        gx = fmaf(a.Dcf[qx * n + m], f[c][idx(m, qy, qz)], gx);
-        gy = fmaf(a.Dcf[qy * n + m], f[c][idx(qx, m, qz)], gy);
-        gz = fmaf(a.Dcf[qz * n + m], f[c][idx(qx, qy, m)], gz);
+        gx = fmaf(Dc[qx * n + m], f[c][idx(m, qy, qz)], gx);
+        gy = fmaf(Dc[qy * n + m], f[c][idx(qx, m, qz)], gy);
+        gz = fmaf(Dc[qz * n + m], f[c][idx(qx, qy, m)], gz);
       }
       g[3 * c + 0] = gx;
       g[3 * c + 1] = gy;
@@ -385,6 +370,13 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
           const bool fixed = is_constrained(a.bc, c, gi0 + i, gk0 + k, a.M);
           qv[c][idx(i, j, k)] = fixed ? 0.f : du[c * a.M3 + node(i, j, k)];
         }
+  if (a.factor) {
+    const float fac = float(elem_factor(a, ec));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < n3; ++q) qv[c][q] *= fac;
+  }
   to_points(qv);
   float ub[STRAT == NHMF_ON_THE_FLY ? 3 : 1][STRAT == NHMF_ON_THE_FLY ? n3 : 1];
   if constexpr (STRAT == NHMF_ON_THE_FLY) {
@@ -403,8 +395,7 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int q = 0; q < n3; ++q) acc[c][q] = 0.f;
-  const float mu = float(a.mu), lam = float(a.lam), invh = float(1.0 / a.h);
-  const float h = float(a.h * elem_factor(a, ec));  // the material factor rides on the point weight
+  const float r2 = float(a.r2mu), inv_mu = float(1.0 / a.mu);
   const float* __restrict__ cache = static_cast<const float*>(a.cache);
   bool bad = false;
 #pragma unroll
@@ -417,9 +408,7 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
         float Fi[9], lnJ, Jm1 = 0.f, F[9];
         if constexpr (STRAT == NHMF_ON_THE_FLY) {
           float H[9];
-          grad_at(ub, qx, qy, qz, H);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) H[k] *= invh;
+          grad_at(a.Dchf, ub, qx, qy, qz, H);  // physical gradient: Dch = Dc / h
           Jm1 = kinematics(H, Fi, lnJ);
           bad |= !(Jm1 > -1.f);
 #pragma unroll
@@ -430,70 +419,29 @@ __global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
           lnJ = __ldg(cache + (9 * n3 + q) * E + slot);
         }
         float dH[9], g[9];
-        grad_at(qv, qx, qy, qz, dH);
+        grad_at(a.Dcf, qv, qx, qy, qz, dH);
         if constexpr (STRAT == NHMF_ON_THE_FLY && MODEL == NHMF_MODEL_SPLIT)
-          split_stress_dP(F, Fi, lnJ, Jm1, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
+          split_stress_dP(F, Fi, lnJ, Jm1, dH, float(a.mu), float(a.lam), inv_mu, g);
         else
-          linearised_stress(Fi, lnJ, dH, mu, lam, a.wf[qx] * a.wf[qy] * a.wf[qz] * h, g);
-        // transposed collocation derivative: acc[c][point on the line through q] += Dc[q][m] g
+          linearised_stress_unit(Fi, lnJ, dH, r2, g);
+        // transposed collocation derivative with the weights, mu and h:
+        //   acc[c][point on the line through q] += DcW[q][m] g
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int m = 0; m < n; ++m) {
-            acc[c][idx(m, qy, qz)] = fmaf(a.Dcf[qx * n + m], g[3 * c + 0], acc[c][idx(m, qy, qz)]);
-            acc[c][idx(qx, m, qz)] = fmaf(a.Dcf[qy * n + m], g[3 * c + 1], acc[c][idx(qx, m, qz)]);
-            acc[c][idx(qx, qy, m)] = fmaf(a.Dcf[qz * n + m], g[3 * c + 2], acc[c][idx(qx, qy, m)]);
+            acc[c][idx(m, qy, qz)] = fmaf(a.DcWf[qx * n + m], g[3 * c + 0], acc[c][idx(m, qy, qz)]);
+            acc[c][idx(qx, m, qz)] = fmaf(a.DcWf[qy * n + m], g[3 * c + 1], acc[c][idx(qx, m, qz)]);
+            acc[c][idx(qx, qy, m)] = fmaf(a.DcWf[qz * n + m], g[3 * c + 2], acc[c][idx(qx, qy, m)]);
           }
       }
   if (bad) atomicOr(a.status, kStatusNonPosJ);
-  // transposed interpolation back to the nodes: out[i] = sum_q B[q][i] acc[q] per direction
+  // transposed weighted interpolation back to the nodes: out[i] = sum_q B[q][i] w_q acc[q]
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int j = 0; j < n; ++j) {
-        float t[n];
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          float s = a.Bf[r] * acc[c][idx(0, j, k)];
-#pragma unroll
-          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(m, j, k)], s);
-          t[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < n; ++r) acc[c][idx(r, j, k)] = t[r];
-      }
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        float t[n];
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          float s = a.Bf[r] * acc[c][idx(i, 0, k)];
-#pragma unroll
-          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(i, m, k)], s);
-          t[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < n; ++r) acc[c][idx(i, r, k)] = t[r];
-      }
-#pragma unroll
-    for (int j = 0; j < n; ++j)
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        float t[n];
-#pragma unroll
-        for (int r = 0; r < n; ++r) {
-          float s = a.Bf[r] * acc[c][idx(i, j, 0)];
-#pragma unroll
-          for (int m = 1; m < n; ++m) s = fmaf(a.Bf[m * n + r], acc[c][idx(i, j, m)], s);
-          t[r] = s;
-        }
-#pragma unroll
-        for (int r = 0; r < n; ++r) acc[c][idx(i, j, r)] = t[r];
-      }
+    pass(acc[c], 0, a.eof[2], a.BWf, true);
+    pass(acc[c], 1, a.eof[2], a.BWf, true);
+    pass(acc[c], 2, a.eof[2], a.BWf, true);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -586,7 +534,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       a.cachedf_out[9 * a.nq + cbase + t] = split(lnJ);
     }
     if (a.cache32_out) {
-      if (P <= 2) {
+      if (P <= kRegMaxP) {
         // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
         // elements of a colour are contiguous
         const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
@@ -827,6 +775,13 @@ OpArgs base_args(nhmf_ctx* c) {
     eo_pack(BWt, n, a.eo[2]);
   }
   a.r2mu = 2.0 * c->prm.lambda / c->prm.mu;
+  for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    a.BWf[i] = float(a.BW[i]);
+    a.DcWf[i] = float(a.DcW[i]);
+    a.Dchf[i] = float(a.Dch[i]);
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < kEoSlots; ++i) a.eof[k][i] = float(a.eo[k][i]);
   a.status = c->status;
   a.factor = c->factor;
   return a;
@@ -895,7 +850,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   // branch would charge the split model's registers to every model)
   constexpr int SPLIT = STRAT == NHMF_ON_THE_FLY ? NHMF_MODEL_SPLIT : NHMF_MODEL_COMPRESSIBLE;
   const bool split = STRAT == NHMF_ON_THE_FLY && c->prm.model == NHMF_MODEL_SPLIT;
-  if constexpr (sizeof(T) == 4 && P <= 2) {
+  if constexpr (sizeof(T) == 4 && P <= kRegMaxP) {
     auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
     st = run_colours(c, k, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
   } else {

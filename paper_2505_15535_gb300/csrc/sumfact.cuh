@@ -9,6 +9,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace nhmf {
@@ -30,9 +32,19 @@ template <> struct Cfg<2, double> { static constexpr int NE = NHMF_Q2D_NE, THREA
 template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; };
 template <> struct Cfg<4, double> { static constexpr int NE = NHMF_Q4D_NE, THREADS = NHMF_Q4D_THREADS; };
 template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; };
-template <> struct Cfg<2, float> { static constexpr int NE = 32, THREADS = 288; };
+#ifndef NHMF_Q2F_NE
+#define NHMF_Q2F_NE 32
+#define NHMF_Q2F_THREADS 288
+#endif
+template <> struct Cfg<2, float> { static constexpr int NE = NHMF_Q2F_NE, THREADS = NHMF_Q2F_THREADS; };
 template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
+// FP32 applies up to this degree use the one-element-per-thread register kernel (and its
+// [10][n^3][E] point-cache layout); higher degrees use the shared-memory kernel.
+#ifndef NHMF_REG_MAXP
+#define NHMF_REG_MAXP 2
+#endif
+constexpr int kRegMaxP = NHMF_REG_MAXP;
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
 template <> struct Cfg<4, df64> { static constexpr int NE = 4, THREADS = 256; };
@@ -59,6 +71,7 @@ struct OpArgs {
   double BW[kMaxN * kMaxN], DcW[kMaxN * kMaxN], Dch[kMaxN * kMaxN];
   double eo[3][kEoSlots];
   double r2mu;
+  float BWf[kMaxN * kMaxN], DcWf[kMaxN * kMaxN], Dchf[kMaxN * kMaxN], eof[3][kEoSlots];  // FP32 copies
   float Bf[kMaxN * kMaxN], Dcf[kMaxN * kMaxN], wf[kMaxN];  // FP32 copies (register kernels)
   const double* u64;
   const float* u32;
@@ -181,13 +194,20 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 // One 1D pass along DIR over NC fields with one thread per (field, line of n items), odd n:
 //   out[(c OS + OO)][line] = M in[c][line]
 // where M is given by its even-odd coefficients `coef` (see eo_line).
-template <int n, int NI, int NC, int DIR, bool ANTI, int OS = 1, int OO = 0, typename T>
-__device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* in, T* out) {
-  constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n;
+// TH is the block size; the task loop is unrolled so that independent lines interleave (not for
+// double-float, whose unrolled lines would cost an SM its second block).
+template <int n, int NI, int NC, int DIR, bool ANTI, int TH, int OS = 1, int OO = 0, typename T>
+__device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __restrict__ in,
+                                        T* __restrict__ out) {
+  constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n, ITER = (NC * NL + TH - 1) / TH;
+  constexpr int UNROLL = std::is_same<T, df64>::value ? 1 : ITER;
   T k[kEoSlots];
 #pragma unroll
   for (int i = 0; i < kEoSlots; ++i) k[i] = coef[i];
-  for (int task = threadIdx.x; task < NC * NL; task += blockDim.x) {
+#pragma unroll UNROLL
+  for (int it = 0; it < ITER; ++it) {
+    const int task = threadIdx.x + it * TH;
+    if (ITER * TH != NC * NL && task >= NC * NL) break;
     const int c = task / NL, L = task - c * NL;
     const int base = DIR == 0 ? L * n
                    : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
