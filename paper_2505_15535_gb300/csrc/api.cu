@@ -129,6 +129,7 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
   if (h & kStatusNonPosJ) return fail(c, NHMF_ERR_NONPOS_J, "det F <= 0 at a quadrature point");
   if (h & kStatusNonFinite) return fail(c, NHMF_ERR_NONFINITE, "non-finite value");
   if (h & kStatusBreakdown) return fail(c, NHMF_ERR_BREAKDOWN, "Krylov breakdown: p^T A p <= 0");
+  if (h & kStatusTcTimeout) return fail(c, NHMF_ERR_CUDA, "tensor-core completion wait timed out");
   return NHMF_OK;
 }
 

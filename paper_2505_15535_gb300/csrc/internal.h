@@ -92,7 +92,7 @@ struct nhmf_ctx {
 
 namespace nhmf {
 
-enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u };
+enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u, kStatusTcTimeout = 8u };
 void free_work(nhmf_ctx* c);
 nhmf_status ensure_work(nhmf_ctx* c);
 

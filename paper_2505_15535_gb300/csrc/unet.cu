@@ -16,6 +16,7 @@
 //   channels of the gathered operand; partial sums per block, reduced in a fixed order.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -373,22 +374,336 @@ const int kLayerCin[11] = {3, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
 const int kLayerCout[11] = {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 3};
 enum { L_IN = 0, L_E0, L_D1, L_E1, L_D2, L_M2, L_U1, L_T1, L_U0, L_T0, L_OUT };
 
+// ------------------------------------------------------------------ stride-1 conv on tcgen05
+// Implicit GEMM on the fifth-generation tensor cores with the accumulator in tensor memory.
+// A tile is 128 consecutive positions p of one z-plane in x-padded row order (row length
+// R = m + 2, p = y R + x + 1; positions on the two pad columns are computed and dropped), so
+// that tap (dx, dy, dz) reads a contiguous 128-row window of the staged plane z + dz: rows
+// (p - p0) + R + 1 + dx + dy R of the padded positions p0 - 1 .. p0 + 128 + 2R (L = 130 + 2R
+// rows, zero outside the grid).  A staged plane is kept as two arrays of 16-byte halves
+// (channels 0-7, then 8-15, L rows apart), so that 8 consecutive rows form one canonical
+// K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of kTcZ tiles along z
+// with a ring of four plane slots: while the 27 MMAs of tile z (M = 128 positions, N = 16
+// output channels, K = 16 input channels, BF16 -> FP32, one per tap) run, its threads stage
+// plane z + 2 for the next tile; the MMAs are committed to an mbarrier and the four warps read
+// their 32 accumulator rows back from tensor memory.
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 32;                   // TMEM columns allocated per block (N = 16 used)
+constexpr int kTcZ = 8;                       // tiles per block column along z
+constexpr int kTcBlocksPerSM = 3;
+constexpr unsigned kTcSpinLimit = 1u << 22;   // bounded wait for the MMAs of one tile
+// instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading byte offset (between core
+// matrices along K), stride byte offset (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// D[tmem] (+)= A B for one 128 x 16 x 16 tile; issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"((uint32_t)accumulate) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for the phase `parity` of an mbarrier; returns whether it completed.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (unsigned it = 0; it < kTcSpinLimit && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Block setup: weights [27][16 co][16 ci] to the canonical per-tap layout (co, ci) at
+// (co % 8) 16 + (co / 8) 128 + (ci % 8) 2 + (ci / 8) 256, `cols` TMEM columns, the mbarrier.
+__device__ __forceinline__ uint32_t tc_setup(const __nv_bfloat16* w, unsigned char* sB, uint32_t* tslot,
+                                             uint32_t bar, uint32_t cols) {
+  const uint4* wg = reinterpret_cast<const uint4*>(w);
+  for (int i = threadIdx.x; i < 27 * 16 * 2; i += blockDim.x) {
+    const int tap = i >> 5, co = (i >> 1) & 15, hf = i & 1;
+    *reinterpret_cast<uint4*>(sB + tap * 512 + (co & 7) * 16 + (co >> 3) * 128 + hf * 256) = wg[i];
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_sync();
+  return *tslot;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t cols, bool timed_out, unsigned* status) {
+  tc_sync();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+  if (timed_out && threadIdx.x == 0) atomicOr(status, kStatusTcTimeout);
+}
+
+// Epilogue of one output voxel v from its 16 FP32 accumulators: + bias + add, ReLU, mask, store.
+__device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long long nvox, const uint32_t (&r)[16]) {
+  float o[16];
+#pragma unroll
+  for (int ch = 0; ch < 16; ++ch) o[ch] = __uint_as_float(r[ch]) + (a.bias ? a.bias[ch] : 0.f);
+  if (a.add) {
+#pragma unroll
+    for (int ch = 0; ch < 16; ch += 2) {
+      const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(a.add + v * kC + ch);
+      o[ch] += __low2float(ad);
+      o[ch + 1] += __high2float(ad);
+    }
+  }
+  if (a.relu) {
+#pragma unroll
+    for (int ch = 0; ch < 16; ++ch) o[ch] = fmaxf(o[ch], 0.f);
+  }
+  if (a.mask) {
+#pragma unroll
+    for (int ch = 0; ch < 16; ch += 2) {
+      const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kC + ch);
+      if (!(__low2float(mk) > 0.f)) o[ch] = 0.f;
+      if (!(__high2float(mk) > 0.f)) o[ch + 1] = 0.f;
+    }
+  }
+  if (a.out_planar) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) a.out_planar[ch * nvox + v] = o[ch];
+  } else {
+    uint32_t pk[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(o[2 * h], o[2 * h + 1]);
+      pk[h] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(a.out + v * kC);
+    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  }
+}
+
+size_t conv_tc_smem(int m) { return 27 * 512 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 16; }
+
+// Stage positions base .. base + L - 1 of plane zz in a padded row order of length R with the
+// grid at x in [xo, xo + m), y in [yo, yo + m) (zeros elsewhere) into `slot` (two halves L rows apart).
+__device__ __forceinline__ void tc_stage(const __nv_bfloat16* __restrict__ in, int m, int R, int L, int base,
+                                         int xo, int yo, int zz, unsigned char* slot) {
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    const int pp = base + j;
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    if (pp >= 0 && zz >= 0 && zz < m) {
+      const int y = pp / R - yo, x = pp % R - xo;
+      if (y >= 0 && y < m && x >= 0 && x < m) {
+        const uint4* src = reinterpret_cast<const uint4*>(in) + 2 * (x + (long long)m * (y + (long long)m * zz));
+        lo = __ldg(src);
+        hi = __ldg(src + 1);
+      }
+    }
+    *reinterpret_cast<uint4*>(slot + j * 16) = lo;
+    *reinterpret_cast<uint4*>(slot + (L + j) * 16) = hi;
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, unsigned* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
+  unsigned char* sB = sm;                                  // [27][512 B] weights, canonical
+  unsigned char* sA = sm + 27 * 512;                       // [4 slots][2 halves][L][16 B]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 8 * L * 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const uint32_t s_bar = smem_u32(bar);
+  const int warp = threadIdx.x >> 5;
+  auto slot = [&](int plane) { return sA + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
+  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kTcCols);
+
+  const int per_plane = (m * R + 127) / 128, nzc = (m + kTcZ - 1) / kTcZ;
+  const long long nunits = (long long)per_plane * nzc, nvox = (long long)m * m * m;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
+    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * kTcZ, ze = min(m, zb + kTcZ);
+    // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
+    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    for (int z = zb; z < ze; ++z) {
+      if (threadIdx.x == 0) {
+        const uint32_t b0 = smem_u32(sB);
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+          const int j0 = R + 1 + dx + dy * R;  // rows j0 .. j0 + 127 < L of plane z + dz
+          tc_mma(tmem, tc_desc(smem_u32(slot(z + dz)) + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
+                 tc_desc(b0 + (uint32_t)tap * 512u, 256u, 128u), tap > 0);
+        }
+        tc_commit(s_bar);
+      }
+      // plane z + 2 (for the next tile) goes to the slot of plane z - 2, which no MMA in flight reads
+      if (z + 1 < ze) {
+        tc_stage(a.in, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      const bool done = tc_wait(s_bar, phase);
+      phase ^= 1u;
+      timed_out = __syncthreads_or(!done) != 0;
+      if (timed_out) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r[16];
+      tc_ld16(tmem + ((32u * (uint32_t)warp) << 16), r);
+      const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
+      if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * z), nvox, r);
+      tc_sync();  // the next tile's MMAs overwrite the accumulator and read the plane staged above
+    }
+  }
+  tc_teardown(tmem, kTcCols, timed_out, status);
+}
+
+// ------------------------------------------------------------------ transposed stride-2 conv on tcgen05
+// out[o] = sum over taps d with o - d even of W_d in[(o - d) / 2], per direction.  Writing
+// o = 2c + q (q = 0, 1), class q = 0 takes tap d = 0 (source c) and q = 1 takes d = -1 (source
+// c + 1) and d = +1 (source c): the 8 parity classes are convolutions on the coarse grid with
+// 1, 2, 4 or 8 taps of source shifts in {0, 1}^3, 27 taps in all.  A tile is 128 consecutive
+// coarse positions p = y R + x (R = m_in + 1, x = m_in is a zero pad column) of coarse plane
+// c_z; shift (sx, sy) reads rows (p - p0) + sx + sy R of the staged plane c_z + sz (L = 129 + R
+// rows).  The 8 classes accumulate in 8 groups of 16 TMEM columns; one commit covers the 27
+// MMAs and the epilogue writes the 8 fine voxels of each coarse position.  Planes c_z, c_z + 1
+// are staged in a ring of three slots, c_z + 2 while the MMAs of c_z run.
+constexpr int kUpCols = 128;
+constexpr size_t kUpSmemMin = 52 * 1024;  // at most 4 blocks (4 x 128 TMEM columns) per SM
+
+size_t up_tc_smem(int mi) {
+  const size_t need = 27 * 512 + 3 * 2 * (size_t)(129 + mi + 1) * 16 + 16;
+  return std::max(need, kUpSmemMin);
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, unsigned* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int mi = a.m_in, mo = a.m_out, R = mi + 1, L = 129 + R;
+  unsigned char* sB = sm;
+  unsigned char* sA = sm + 27 * 512;                       // [3 slots][2 halves][L][16 B]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 6 * L * 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const uint32_t s_bar = smem_u32(bar);
+  const int warp = threadIdx.x >> 5;
+  auto slot = [&](int plane) { return sA + (plane % 3) * 2 * L * 16; };  // plane >= 0
+  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kUpCols);
+
+  const int per_plane = (mi * R + 127) / 128, nzc = (mi + kTcZ - 1) / kTcZ;
+  const long long nunits = (long long)per_plane * nzc, nvox = (long long)mo * mo * mo;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
+    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * kTcZ, ze = min(mi, zb + kTcZ);
+    // staged row j of a plane is coarse position p0 + j = y R + x
+    for (int pl = zb; pl <= zb + 1; ++pl) tc_stage(a.in, mi, R, L, p0, 0, 0, pl, slot(pl));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    for (int cz = zb; cz < ze; ++cz) {
+      if (threadIdx.x == 0) {
+        const uint32_t b0 = smem_u32(sB);
+        for (int cl = 0; cl < 8; ++cl) {
+          const int qx = cl & 1, qy = (cl >> 1) & 1, qz = cl >> 2;
+          int k = 0;
+          for (int sz = 0; sz <= qz; ++sz)
+            for (int sy = 0; sy <= qy; ++sy)
+              for (int sx = 0; sx <= qx; ++sx, ++k) {
+                // d = 0 for q = 0; for q = 1, shift 1 <-> d = -1 and shift 0 <-> d = +1
+                const int dx = qx ? (sx ? -1 : 1) : 0, dy = qy ? (sy ? -1 : 1) : 0, dz = qz ? (sz ? -1 : 1) : 0;
+                const int tap = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                const int j0 = sx + sy * R;  // rows j0 .. j0 + 127 < L of plane cz + sz
+                tc_mma(tmem + (uint32_t)(16 * cl),
+                       tc_desc(smem_u32(slot(cz + sz)) + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
+                       tc_desc(b0 + (uint32_t)tap * 512u, 256u, 128u), k > 0);
+              }
+        }
+        tc_commit(s_bar);
+      }
+      if (cz + 1 < ze) {  // plane cz + 2 goes to the slot of plane cz - 1
+        tc_stage(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      const bool done = tc_wait(s_bar, phase);
+      phase ^= 1u;
+      timed_out = __syncthreads_or(!done) != 0;
+      if (timed_out) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int p = p0 + threadIdx.x, y = p / R, x = p % R;  // row threadIdx.x is coarse position p
+      const bool ok = p < mi * R && x < mi;
+      for (int cl = 0; cl < 8; ++cl) {
+        const int qx = cl & 1, qy = (cl >> 1) & 1, qz = cl >> 2;
+        uint32_t r[16];
+        tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + (uint32_t)(16 * cl), r);
+        if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1))
+          tc_emit(a, (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz)), nvox, r);
+      }
+      tc_sync();
+    }
+  }
+  tc_teardown(tmem, kUpCols, timed_out, status);
+}
+
 template <int G>
 void conv_launch(const ConvArgs& a, cudaStream_t s) {
   k_conv<G><<<kConvBlocks, 256, 0, s>>>(a);
 }
 
+// stride-1 convolution on the tensor cores (tcgen05); 3 blocks per SM
+void up_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
+  const size_t smem = up_tc_smem(a.m_in);
+  cudaFuncSetAttribute(k_up_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long long mi = a.m_in, nunits = ((mi * (mi + 1) + 127) / 128) * ((mi + kTcZ - 1) / kTcZ);
+  k_up_tc<<<(int)std::min<long long>(nunits, 4 * 152), kTcThreads, smem, s>>>(a, status);
+}
+
+void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
+  const size_t smem = conv_tc_smem(a.m_out);
+  cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long long m = a.m_out, nunits = ((m * (m + 2) + 127) / 128) * ((m + kTcZ - 1) / kTcZ);
+  k_conv_tc<<<(int)std::min<long long>(nunits, kTcBlocksPerSM * 152), kTcThreads, smem, s>>>(a, status);
+}
+
 // out = act(conv_G(in; w) + bias + add) * mask
 void conv(int gather, const __nv_bfloat16* in, int m_in, const __nv_bfloat16* w, const float* bias,
           const __nv_bfloat16* add, const __nv_bfloat16* mask, bool relu, __nv_bfloat16* out, float* out_planar,
-          int m_out, cudaStream_t s) {
+          int m_out, cudaStream_t s, unsigned* status) {
   ConvArgs a{in, m_in, w, bias, add, mask, relu ? 1 : 0, out, out_planar, m_out};
   if (gather == S1)
-    conv_launch<S1>(a, s);
+    conv_tc_launch(a, status, s);
   else if (gather == DOWN2)
     conv_launch<DOWN2>(a, s);
   else
-    conv_launch<UP2>(a, s);
+    up_tc_launch(a, status, s);
 }
 
 void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
@@ -418,6 +733,7 @@ nhmf_status unet_alloc(nhmf_ctx* c, int cap) {
   if (c->unet) return fail(c, NHMF_ERR_STATE, "unet: already created");
   UNet* u = new UNet();
   c->unet = u;
+  u->status = c->status;
   u->M0 = c->g.M;
   u->M1 = (u->M0 - 1) / 2 + 1;
   u->M2 = (u->M1 - 1) / 2 + 1;
@@ -490,17 +806,17 @@ void unet_forward(UNet& u, cudaStream_t s) {
   const float* P = u.params;
   auto B = [&](int l) { return P + u.L[l].boff; };
   const int M0 = u.M0, M1 = u.M1, M2 = u.M2;
-  conv(S1, u.x16, M0, u.L[L_IN].wf, B(L_IN), nullptr, nullptr, true, u.a0, nullptr, M0, s);
-  conv(S1, u.a0, M0, u.L[L_E0].wf, B(L_E0), nullptr, nullptr, true, u.s0, nullptr, M0, s);
-  conv(DOWN2, u.s0, M0, u.L[L_D1].wf, B(L_D1), nullptr, nullptr, true, u.d1, nullptr, M1, s);
-  conv(S1, u.d1, M1, u.L[L_E1].wf, B(L_E1), nullptr, nullptr, true, u.s1, nullptr, M1, s);
-  conv(DOWN2, u.s1, M1, u.L[L_D2].wf, B(L_D2), nullptr, nullptr, true, u.d2, nullptr, M2, s);
-  conv(S1, u.d2, M2, u.L[L_M2].wf, B(L_M2), nullptr, nullptr, true, u.m2, nullptr, M2, s);
-  conv(UP2, u.m2, M2, u.L[L_U1].wf, B(L_U1), u.s1, nullptr, true, u.u1, nullptr, M1, s);
-  conv(S1, u.u1, M1, u.L[L_T1].wf, B(L_T1), nullptr, nullptr, true, u.t1, nullptr, M1, s);
-  conv(UP2, u.t1, M1, u.L[L_U0].wf, B(L_U0), u.s0, nullptr, true, u.u0, nullptr, M0, s);
-  conv(S1, u.u0, M0, u.L[L_T0].wf, B(L_T0), nullptr, nullptr, true, u.t0, nullptr, M0, s);
-  conv(S1, u.t0, M0, u.L[L_OUT].wf, B(L_OUT), nullptr, nullptr, false, nullptr, u.y, M0, s);
+  conv(S1, u.x16, M0, u.L[L_IN].wf, B(L_IN), nullptr, nullptr, true, u.a0, nullptr, M0, s, u.status);
+  conv(S1, u.a0, M0, u.L[L_E0].wf, B(L_E0), nullptr, nullptr, true, u.s0, nullptr, M0, s, u.status);
+  conv(DOWN2, u.s0, M0, u.L[L_D1].wf, B(L_D1), nullptr, nullptr, true, u.d1, nullptr, M1, s, u.status);
+  conv(S1, u.d1, M1, u.L[L_E1].wf, B(L_E1), nullptr, nullptr, true, u.s1, nullptr, M1, s, u.status);
+  conv(DOWN2, u.s1, M1, u.L[L_D2].wf, B(L_D2), nullptr, nullptr, true, u.d2, nullptr, M2, s, u.status);
+  conv(S1, u.d2, M2, u.L[L_M2].wf, B(L_M2), nullptr, nullptr, true, u.m2, nullptr, M2, s, u.status);
+  conv(UP2, u.m2, M2, u.L[L_U1].wf, B(L_U1), u.s1, nullptr, true, u.u1, nullptr, M1, s, u.status);
+  conv(S1, u.u1, M1, u.L[L_T1].wf, B(L_T1), nullptr, nullptr, true, u.t1, nullptr, M1, s, u.status);
+  conv(UP2, u.t1, M1, u.L[L_U0].wf, B(L_U0), u.s0, nullptr, true, u.u0, nullptr, M0, s, u.status);
+  conv(S1, u.u0, M0, u.L[L_T0].wf, B(L_T0), nullptr, nullptr, true, u.t0, nullptr, M0, s, u.status);
+  conv(S1, u.t0, M0, u.L[L_OUT].wf, B(L_OUT), nullptr, nullptr, false, nullptr, u.y, M0, s, u.status);
 }
 
 // Backward pass from dy16 (in u.g0a) to u.grads (after unet_forward on the same input).
@@ -511,34 +827,34 @@ void unet_backward(UNet& u, cudaStream_t s) {
   __nv_bfloat16 *dm2 = u.g2a, *dd2 = u.g2b;
   wgrad(u, L_OUT, S1, dy, M0, u.t0, M0, s);
   bgrad(u, L_OUT, dy, u.N0, s);
-  conv(S1, dy, M0, u.L[L_OUT].wb, nullptr, nullptr, u.t0, false, dt0, nullptr, M0, s);
+  conv(S1, dy, M0, u.L[L_OUT].wb, nullptr, nullptr, u.t0, false, dt0, nullptr, M0, s, u.status);
   wgrad(u, L_T0, S1, dt0, M0, u.u0, M0, s);
   bgrad(u, L_T0, dt0, u.N0, s);
-  conv(S1, dt0, M0, u.L[L_T0].wb, nullptr, nullptr, u.u0, false, du0, nullptr, M0, s);
+  conv(S1, dt0, M0, u.L[L_T0].wb, nullptr, nullptr, u.u0, false, du0, nullptr, M0, s, u.status);
   wgrad(u, L_U0, DOWN2, u.t1, M1, du0, M0, s);  // dU[c][o] = sum t1[c] du0[o](2v'+d)
   bgrad(u, L_U0, du0, u.N0, s);
-  conv(DOWN2, du0, M0, u.L[L_U0].wb, nullptr, nullptr, u.t1, false, dt1, nullptr, M1, s);
+  conv(DOWN2, du0, M0, u.L[L_U0].wb, nullptr, nullptr, u.t1, false, dt1, nullptr, M1, s, u.status);
   wgrad(u, L_T1, S1, dt1, M1, u.u1, M1, s);
   bgrad(u, L_T1, dt1, u.N1, s);
-  conv(S1, dt1, M1, u.L[L_T1].wb, nullptr, nullptr, u.u1, false, du1, nullptr, M1, s);
+  conv(S1, dt1, M1, u.L[L_T1].wb, nullptr, nullptr, u.u1, false, du1, nullptr, M1, s, u.status);
   wgrad(u, L_U1, DOWN2, u.m2, M2, du1, M1, s);
   bgrad(u, L_U1, du1, u.N1, s);
-  conv(DOWN2, du1, M1, u.L[L_U1].wb, nullptr, nullptr, u.m2, false, dm2, nullptr, M2, s);
+  conv(DOWN2, du1, M1, u.L[L_U1].wb, nullptr, nullptr, u.m2, false, dm2, nullptr, M2, s, u.status);
   wgrad(u, L_M2, S1, dm2, M2, u.d2, M2, s);
   bgrad(u, L_M2, dm2, u.N2, s);
-  conv(S1, dm2, M2, u.L[L_M2].wb, nullptr, nullptr, u.d2, false, dd2, nullptr, M2, s);
+  conv(S1, dm2, M2, u.L[L_M2].wb, nullptr, nullptr, u.d2, false, dd2, nullptr, M2, s, u.status);
   wgrad(u, L_D2, DOWN2, dd2, M2, u.s1, M1, s);
   bgrad(u, L_D2, dd2, u.N2, s);
-  conv(UP2, dd2, M2, u.L[L_D2].wb, nullptr, du1, u.s1, false, ds1, nullptr, M1, s);  // + skip grad, ReLU mask
+  conv(UP2, dd2, M2, u.L[L_D2].wb, nullptr, du1, u.s1, false, ds1, nullptr, M1, s, u.status);  // + skip grad, ReLU mask
   wgrad(u, L_E1, S1, ds1, M1, u.d1, M1, s);
   bgrad(u, L_E1, ds1, u.N1, s);
-  conv(S1, ds1, M1, u.L[L_E1].wb, nullptr, nullptr, u.d1, false, dd1, nullptr, M1, s);
+  conv(S1, ds1, M1, u.L[L_E1].wb, nullptr, nullptr, u.d1, false, dd1, nullptr, M1, s, u.status);
   wgrad(u, L_D1, DOWN2, dd1, M1, u.s0, M0, s);
   bgrad(u, L_D1, dd1, u.N1, s);
-  conv(UP2, dd1, M1, u.L[L_D1].wb, nullptr, du0, u.s0, false, ds0, nullptr, M0, s);
+  conv(UP2, dd1, M1, u.L[L_D1].wb, nullptr, du0, u.s0, false, ds0, nullptr, M0, s, u.status);
   wgrad(u, L_E0, S1, ds0, M0, u.a0, M0, s);
   bgrad(u, L_E0, ds0, u.N0, s);
-  conv(S1, ds0, M0, u.L[L_E0].wb, nullptr, nullptr, u.a0, false, dt0, nullptr, M0, s);  // da0 in dt0's buffer
+  conv(S1, ds0, M0, u.L[L_E0].wb, nullptr, nullptr, u.a0, false, dt0, nullptr, M0, s, u.status);  // da0 in dt0's buffer
   wgrad(u, L_IN, S1, dt0, M0, u.x16, M0, s);
   bgrad(u, L_IN, dt0, u.N0, s);
 }

@@ -29,6 +29,7 @@ struct UNet {
   double* sc = nullptr;        // device scalars
   float* pairs = nullptr;      // [cap][2][3][N0]: normalised input, normalised target
   int cap = 0, npairs = 0;
+  unsigned* status = nullptr;  // the context's device status word
 };
 
 }  // namespace nhmf
