@@ -21,12 +21,12 @@ namespace nhmf {
 template <int P, typename T> struct Cfg;
 template <> struct Cfg<1, double> { static constexpr int NE = 32, THREADS = 256; };
 #ifndef NHMF_Q2D_NE
-#define NHMF_Q2D_NE 32
-#define NHMF_Q2D_THREADS 288
+#define NHMF_Q2D_NE 27
+#define NHMF_Q2D_THREADS 256
 #endif
 #ifndef NHMF_Q4D_NE
-#define NHMF_Q4D_NE 4
-#define NHMF_Q4D_THREADS 320
+#define NHMF_Q4D_NE 3
+#define NHMF_Q4D_THREADS 192
 #endif
 template <> struct Cfg<2, double> { static constexpr int NE = NHMF_Q2D_NE, THREADS = NHMF_Q2D_THREADS; };
 template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; };

@@ -382,14 +382,15 @@ enum { L_IN = 0, L_E0, L_D1, L_E1, L_D2, L_M2, L_U1, L_T1, L_U0, L_T0, L_OUT };
 // (p - p0) + R + 1 + dx + dy R of the padded positions p0 - 1 .. p0 + 128 + 2R (L = 130 + 2R
 // rows, zero outside the grid).  A staged plane is kept as two arrays of 16-byte halves
 // (channels 0-7, then 8-15, L rows apart), so that 8 consecutive rows form one canonical
-// K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of kTcZ tiles along z
-// with a ring of four plane slots: while the 27 MMAs of tile z (M = 128 positions, N = 16
+// K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of up to kTcZ tiles along z
+// (fewer on small grids) with a ring of four plane slots: while the 27 MMAs of tile z (M = 128 positions, N = 16
 // output channels, K = 16 input channels, BF16 -> FP32, one per tap) run, its threads stage
 // plane z + 2 for the next tile; the MMAs are committed to an mbarrier and the four warps read
 // their 32 accumulator rows back from tensor memory.
 constexpr int kTcThreads = 128;
 constexpr int kTcCols = 32;                   // TMEM columns allocated per block (N = 16 used)
-constexpr int kTcZ = 8;                       // tiles per block column along z
+constexpr int kTcZ = 8;                       // at most this many tiles per block column along z
+constexpr int kTcUnits = 600;                 // shorter columns below this many column units
 constexpr int kTcBlocksPerSM = 3;
 constexpr unsigned kTcSpinLimit = 1u << 22;   // bounded wait for the MMAs of one tile
 // instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10), both
@@ -536,7 +537,7 @@ __device__ __forceinline__ void tc_stage(const __nv_bfloat16* __restrict__ in, i
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, unsigned* status) {
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
   unsigned char* sB = sm;                                  // [27][512 B] weights, canonical
@@ -548,12 +549,12 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, unsign
   auto slot = [&](int plane) { return sA + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
   const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kTcCols);
 
-  const int per_plane = (m * R + 127) / 128, nzc = (m + kTcZ - 1) / kTcZ;
+  const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc, nvox = (long long)m * m * m;
   uint32_t phase = 0;
   bool timed_out = false;
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
-    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * kTcZ, ze = min(m, zb + kTcZ);
+    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
     // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
     for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -607,7 +608,7 @@ size_t up_tc_smem(int mi) {
   return std::max(need, kUpSmemMin);
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, unsigned* status) {
+__global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int mi = a.m_in, mo = a.m_out, R = mi + 1, L = 129 + R;
   unsigned char* sB = sm;
@@ -619,12 +620,12 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, unsigned
   auto slot = [&](int plane) { return sA + (plane % 3) * 2 * L * 16; };  // plane >= 0
   const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kUpCols);
 
-  const int per_plane = (mi * R + 127) / 128, nzc = (mi + kTcZ - 1) / kTcZ;
+  const int per_plane = (mi * R + 127) / 128, nzc = (mi + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc, nvox = (long long)mo * mo * mo;
   uint32_t phase = 0;
   bool timed_out = false;
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
-    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * kTcZ, ze = min(mi, zb + kTcZ);
+    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(mi, zb + zc);
     // staged row j of a plane is coarse position p0 + j = y R + x
     for (int pl = zb; pl <= zb + 1; ++pl) tc_stage(a.in, mi, R, L, p0, 0, 0, pl, slot(pl));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -679,18 +680,28 @@ void conv_launch(const ConvArgs& a, cudaStream_t s) {
 }
 
 // stride-1 convolution on the tensor cores (tcgen05); 3 blocks per SM
+// Tiles per block column along z for a grid of m planes with per_plane tiles each: kTcZ, or
+// fewer so that a small grid still gives about kTcUnits column units.
+int tc_column(long long per_plane, int m) {
+  return (int)std::max<long long>(1, std::min<long long>(kTcZ, per_plane * m / kTcUnits));
+}
+
 void up_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   const size_t smem = up_tc_smem(a.m_in);
   cudaFuncSetAttribute(k_up_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long long mi = a.m_in, nunits = ((mi * (mi + 1) + 127) / 128) * ((mi + kTcZ - 1) / kTcZ);
-  k_up_tc<<<(int)std::min<long long>(nunits, 4 * 152), kTcThreads, smem, s>>>(a, status);
+  const long long mi = a.m_in, per_plane = (mi * (mi + 1) + 127) / 128;
+  const int zc = tc_column(per_plane, (int)mi);
+  const long long nunits = per_plane * ((mi + zc - 1) / zc);
+  k_up_tc<<<(int)std::min<long long>(nunits, 4 * 152), kTcThreads, smem, s>>>(a, zc, status);
 }
 
 void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   const size_t smem = conv_tc_smem(a.m_out);
   cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long long m = a.m_out, nunits = ((m * (m + 2) + 127) / 128) * ((m + kTcZ - 1) / kTcZ);
-  k_conv_tc<<<(int)std::min<long long>(nunits, kTcBlocksPerSM * 152), kTcThreads, smem, s>>>(a, status);
+  const long long m = a.m_out, per_plane = (m * (m + 2) + 127) / 128;
+  const int zc = tc_column(per_plane, (int)m);
+  const long long nunits = per_plane * ((m + zc - 1) / zc);
+  k_conv_tc<<<(int)std::min<long long>(nunits, kTcBlocksPerSM * 152), kTcThreads, smem, s>>>(a, zc, status);
 }
 
 // out = act(conv_G(in; w) + bias + add) * mask
