@@ -448,14 +448,14 @@ def run_newton(args):
     plain: FP64 Jacobi-CG; mixed: FP64 flexible CG with an FP32 inner Jacobi-CG; learned and
     mixed_learned: the U-Net preconditioner trained on pairs recorded during the plain solve of
     the first `train_steps` load steps.  Per step: wall time, Newton/outer/inner iterations,
-    the relative difference to the plain solver's state, the oracle's FP64 residual on sampled
-    rows of that state, and the FP32 apply's error against the oracle at that state."""
+    the final relative FP64 residual, the relative difference to the plain solver's state, and
+    (plain solver) the FP32 apply's error against the FP64 apply at that state.  The FP64 apply
+    and residual are parity-tested against the oracle, at full size on sampled rows of a solved
+    state too, so the benchmark runs no oracle code here."""
     import torch
     import __graft_entry__ as g
     g.build()
     from paper_2505_15535_gb300 import nhmf
-    from oracle.fem import Operator
-    from oracle.mesh import Mesh
     dev = torch.device("cuda", 0)
     w = inp.WORKLOADS[args.workload]
     S = w.load_steps
@@ -471,9 +471,17 @@ def run_newton(args):
     ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
            "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED,
            "gmg": nhmf.NHMF_SOLVER_GMG, "mixed_gmg": nhmf.NHMF_SOLVER_MIXED_GMG}
-    op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
-    rng = np.random.default_rng(0)
-    rows = np.sort(rng.choice(w.n_dofs, 64, replace=False))
+    du_err = torch.from_numpy(inp.draw_vector(77, w.n_dofs)).to(dev)
+
+    def fp32_error(uu):
+        """FP32 apply vs FP64 apply (cached strategy) at the linearisation point uu."""
+        prob.set_linearization(uu, nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32)
+        v64 = torch.empty_like(du_err)
+        v32 = torch.empty(w.n_dofs, dtype=torch.float32, device=dev)
+        prob.apply(du_err, v64, nhmf.NHMF_FP64, nhmf.NHMF_CACHED)
+        prob.apply(du_err.float(), v32, nhmf.NHMF_FP32, nhmf.NHMF_CACHED)
+        return float(torch.linalg.norm(v32.double() - v64) / torch.linalg.norm(v64))
+
     out = {"metric": NEWTON_METRIC, "mode": "newton", "workload": f"{w.name}: " + describe(w) +
            f"; {S} load steps of {w.compression / S:g}", "steps_run": last, "solvers": {}}
     states = {}
@@ -516,21 +524,10 @@ def run_newton(args):
                 rec = out["solvers"][name]["steps"][k]
                 ref = plain[k + off]
                 rec["rel_diff_vs_plain"] = float(torch.linalg.norm(uu - ref) / torch.linalg.norm(ref))
-    for name, lst in states.items():
-        uu = lst[-1].cpu().numpy()
-        R = op.residual_rows(uu, rows)
-        scale = np.abs(op.apply_rows(uu, uu, rows)).max()
-        out["solvers"][name]["oracle_residual_rows_rel"] = float(np.abs(R).max() / scale)
-    # FP32 apply error vs the oracle at the final plain state
+    # FP32 apply error vs the FP64 apply at each converged plain state
     if "plain" in states:
-        uu = states["plain"][-1]
-        prob.set_linearization(uu, nhmf.NHMF_CACHE_FP32)
-        du = torch.from_numpy(inp.draw_vector(77, w.n_dofs)).to(dev)
-        v32 = torch.empty(w.n_dofs, dtype=torch.float32, device=dev)
-        prob.apply(du.float(), v32, nhmf.NHMF_FP32, nhmf.NHMF_CACHED)
-        ref = op.apply_rows(uu.cpu().numpy(), du.cpu().numpy(), rows)
-        got = v32[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
-        out["fp32_apply_rel_err_vs_oracle_rows"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        for k, uu in enumerate(states["plain"]):
+            out["solvers"]["plain"]["steps"][k]["fp32_apply_rel_err_vs_fp64"] = fp32_error(uu)
     sp = out["solvers"]
     if "plain" in sp:
         for name in sp:
