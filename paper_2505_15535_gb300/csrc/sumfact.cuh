@@ -52,6 +52,13 @@ template <> struct Cfg<4, df64> { static constexpr int NE = 4, THREADS = 256; };
 // so that two blocks fit an SM.
 template <int P, typename T, int STRAT> struct LaunchCfg : Cfg<P, T> {};
 template <> struct LaunchCfg<4, double, NHMF_SPATIAL> { static constexpr int NE = 4, THREADS = 256; };
+#ifndef NHMF_Q2D_OTF_NE
+#define NHMF_Q2D_OTF_NE NHMF_Q2D_NE
+#define NHMF_Q2D_OTF_THREADS NHMF_Q2D_THREADS
+#endif
+template <> struct LaunchCfg<2, double, NHMF_ON_THE_FLY> {
+  static constexpr int NE = NHMF_Q2D_OTF_NE, THREADS = NHMF_Q2D_OTF_THREADS;
+};
 
 // Coefficients of one n x n operator in even-odd form (odd n <= 5): S, A ((h+1) x h each) and C
 // (h+1), h = n / 2.

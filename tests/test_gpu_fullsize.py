@@ -1,6 +1,8 @@
-"""Parity at the full Q2 64^3 and Q4 32^3 sizes (6,440,067 DoFs each), in the launch
-configuration the benchmark times, on sampled output rows the oracle computes one by one
-(its apply_rows/residual_rows touch only the elements around each sampled DoF)."""
+"""Parity at the full sizes of the benchmark workloads — Q2 64^3 and Q4 32^3 (6,440,067 DoFs
+each), Q3 48^3 (9,145,875) and Q4 64^3 (50,923,779), the last two near-incompressible
+(lambda 49) with the compression boundary conditions — in the launch configuration the
+benchmark times, on sampled output rows the oracle computes one by one (its
+apply_rows/residual_rows touch only the elements around each sampled DoF)."""
 import numpy as np
 import pytest
 
@@ -22,7 +24,7 @@ def sample_rows(w, count=400, seed=5):
     return np.array(sorted(set(int(r) for r in rows)))
 
 
-@pytest.mark.parametrize("name", ["q2_64_clamp", "q4_32_clamp"])
+@pytest.mark.parametrize("name", ["q2_64_clamp", "q4_32_clamp", "q3_48_compress", "q4_64_compress"])
 def test_fullsize_sampled_rows(name):
     import torch
     nhmf = lib_or_fail()
