@@ -27,7 +27,9 @@
  * Errors: calls return an nhmf_status; no call aborts the process or traps on the device.
  * Kernels that meet det F <= 0 or a non-finite value record it in a device status word that
  * nhmf_check_status() (and every synchronising call) turns into NHMF_ERR_NONPOS_J /
- * NHMF_ERR_NONFINITE.  nhmf_last_error() returns a text description of the last failure.
+ * NHMF_ERR_NONFINITE.  Every device-side wait is bounded: a tensor-core convolution whose
+ * completion wait runs out records that too (NHMF_ERR_CUDA, "tensor-core completion wait
+ * timed out") and returns.  nhmf_last_error() returns a text description of the last failure.
  */
 #ifndef NHMF_H
 #define NHMF_H
@@ -133,7 +135,8 @@ nhmf_status nhmf_diagonal(nhmf_ctx* ctx, double* d, void* stream);
 nhmf_status nhmf_set_material_factors(nhmf_ctx* ctx, const double* factors, void* stream);
 
 /* Synchronise `stream`, read and clear the device status word.  Returns NHMF_OK,
- * NHMF_ERR_NONPOS_J or NHMF_ERR_NONFINITE. */
+ * NHMF_ERR_NONPOS_J, NHMF_ERR_NONFINITE, NHMF_ERR_BREAKDOWN or NHMF_ERR_CUDA (a bounded
+ * tensor-core wait ran out). */
 nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------ solvers
@@ -255,7 +258,9 @@ nhmf_status nhmf_linear_solve_noalloc(nhmf_ctx* ctx, int strategy, double rtol, 
  * A 3-level convolutional U-Net on the nodal grid (16 channels, 3x3x3 convolutions, ReLU,
  * stride-2 down and transposed-convolution up paths with additive skips; 3 input and 3
  * output channels = the displacement components), BF16 weights and activations with FP32
- * accumulation on the tensor cores, FP32 master weights trained by Adam.  It maps a
+ * accumulation on the tensor cores (tcgen05 for the stride-1 and transposed stride-2
+ * convolutions, mma.sync for the stride-2 down convolution and the weight gradients), FP32
+ * master weights trained by Adam.  It maps a
  * residual r (scaled to unit RMS) to a correction; as a preconditioner z = N(r) scaled back
  * and zeroed on constrained DoFs.  Requires p*N divisible by 4.
  * Parameters: a flat FP32 array, layer by layer (in, e0, d1, e1, d2, m2, u1, t1, u0, t0,
