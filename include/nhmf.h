@@ -118,6 +118,14 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mas
 nhmf_status nhmf_tangent_apply(nhmf_ctx* ctx, int precision, int strategy, const void* du,
                                void* v, void* stream);
 
+/* Tangent application at a given linearisation point (Algorithm 1: given u and du, return
+ * W): v = A(u) du, on the fly in FP64, reading u directly.  u, du, v: device FP64
+ * [3][M^3], u as in nhmf_set_linearization, du and v as in nhmf_tangent_apply.  No point
+ * cache is built and the stored linearisation point (if any) is neither needed nor changed.
+ * Asynchronous on `stream`; det F <= 0 at a point is recorded in the status word
+ * (nhmf_check_status).  NHMF_ERR_ARG for null pointers or v aliasing u or du. */
+nhmf_status nhmf_tangent_apply_at(nhmf_ctx* ctx, const double* u, const double* du, double* v, void* stream);
+
 /* r = R(u) (Eq. F, no traction) in FP64 for the device vector u; rows on D are zero.
  * Synchronises and returns NHMF_ERR_NONPOS_J / NHMF_ERR_NONFINITE on failure. */
 nhmf_status nhmf_residual(nhmf_ctx* ctx, const double* u, double* r, void* stream);

@@ -186,6 +186,16 @@ nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const v
   return launch_apply(c, precision, strategy, du, v, as_stream(stream));
 }
 
+nhmf_status nhmf_tangent_apply_at(nhmf_ctx* c, const double* u, const double* du, double* v, void* stream) {
+  if (!c) return NHMF_ERR_ARG;
+  if (!u || !du || !v || (const void*)du == (void*)v || (const void*)u == (void*)v)
+    return fail(c, NHMF_ERR_ARG, "tangent_apply_at: bad argument");
+  c->u_at = u;
+  const nhmf_status st = launch_apply(c, NHMF_FP64, NHMF_ON_THE_FLY, du, v, as_stream(stream));
+  c->u_at = nullptr;
+  return st;
+}
+
 nhmf_status nhmf_residual(nhmf_ctx* c, const double* u, double* r, void* stream) {
   if (!c) return NHMF_ERR_ARG;
   if (!u || !r || (const void*)u == (void*)r) return fail(c, NHMF_ERR_ARG, "residual: bad argument");

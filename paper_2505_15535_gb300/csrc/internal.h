@@ -80,6 +80,7 @@ struct nhmf_ctx {
   double* factor = nullptr;   // [E] per-element material factors (natural order), or null
   unsigned* status = nullptr; // device status word: bit 0 det F <= 0, bit 1 non-finite
   bool have_lin = false;
+  const double* u_at = nullptr;  // set only while nhmf_tangent_apply_at launches its apply
   std::string err;
   // kernel timing (nhmf_profile_enable): event pairs per operator kind
   bool profiling = false;

@@ -834,7 +834,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
   OpArgs a = base_args(c);
   if (raw) a.bc = NHMF_BC_NONE;  // unconstrained operator K: no masking, no identity rows
-  a.u64 = c->ubar;
+  a.u64 = c->u_at ? c->u_at : c->ubar;
   a.u32 = c->ubar32;
   a.du = du;
   a.v = v;

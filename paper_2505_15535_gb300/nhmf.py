@@ -80,6 +80,7 @@ _SIGS = {
     "nhmf_last_error": (ctypes.c_char_p, [_P]),
     "nhmf_set_linearization": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "nhmf_tangent_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "nhmf_tangent_apply_at": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nhmf_residual": (ctypes.c_int, [_P, _P, _P, _P]),
     "nhmf_diagonal": (ctypes.c_int, [_P, _P, _P]),
     "nhmf_check_status": (ctypes.c_int, [_P, _P]),
@@ -174,6 +175,10 @@ def nhmf_set_linearization(ctx, u, cache_mask=0, stream=None):
 
 def nhmf_tangent_apply(ctx, precision, strategy, du, v, stream=None):
     _check(ctx, lib().nhmf_tangent_apply(ctx, precision, strategy, _ptr(du), _ptr(v), _stream(stream)))
+
+
+def nhmf_tangent_apply_at(ctx, u, du, v, stream=None):
+    _check(ctx, lib().nhmf_tangent_apply_at(ctx, _ptr(u), _ptr(du), _ptr(v), _stream(stream)))
 
 
 def nhmf_residual(ctx, u, r, stream=None):
@@ -332,6 +337,11 @@ class Problem:
 
     def apply(self, du, v, precision=NHMF_FP64, strategy=NHMF_ON_THE_FLY):
         nhmf_tangent_apply(self.ctx, precision, strategy, du, v)
+        return v
+
+    def apply_at(self, u, du, v):
+        """v = A(u) du on the fly in FP64 at the given u (no stored linearisation needed)."""
+        nhmf_tangent_apply_at(self.ctx, u, du, v)
         return v
 
     def residual(self, u, r):

@@ -30,8 +30,9 @@ def library():
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
-    for required in ["nhmf_create", "nhmf_destroy", "nhmf_tangent_apply", "nhmf_residual",
-                     "nhmf_diagonal", "nhmf_set_linearization"]:
+    for required in ["nhmf_create", "nhmf_destroy", "nhmf_num_dofs", "nhmf_tangent_apply",
+                     "nhmf_tangent_apply_at", "nhmf_residual", "nhmf_diagonal", "nhmf_set_linearization",
+                     "nhmf_solve", "nhmf_unet_train", "nhmf_last_error"]:
         assert required in names
 
 

@@ -52,6 +52,37 @@ def test_fp64_apply_both_strategies(nhmf, p, n_el, bc):
     prob.close()
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("model", [0, 1])
+def test_apply_at_given_point(nhmf, p, model):
+    """nhmf_tangent_apply_at (Algorithm 1 with u given): equals the oracle at that u without a
+    stored linearisation point, leaves a stored one untouched, and is bitwise the same as
+    setting u and applying on the fly."""
+    w, u, du = case(3, p, 1)
+    lam = w.lam if model == 0 else 5.0
+    op = Operator(Mesh(3, p), w.mu, lam, 1, model=model)
+    prob = nhmf.Problem(3, p, w.mu, lam, 1, model=model)
+    ut, dut = cuda(u), cuda(du)
+    v_at = cuda(np.zeros_like(u))
+    prob.apply_at(ut, dut, v_at)                  # no set_linearization before
+    assert rel_l2(host(v_at), op.apply(u, du)) <= FP64_TOL
+    u2 = 0.5 * u
+    prob.set_linearization(cuda(u2))
+    v2 = cuda(np.zeros_like(u))
+    prob.apply_at(ut, dut, v2)
+    assert np.array_equal(host(v2), host(v_at))
+    v_stored = cuda(np.zeros_like(u))
+    prob.apply(dut, v_stored, nhmf.NHMF_FP64, nhmf.NHMF_ON_THE_FLY)   # still linearised at u2
+    assert rel_l2(host(v_stored), op.apply(u2, du)) <= FP64_TOL
+    prob.set_linearization(ut)
+    v_set = cuda(np.zeros_like(u))
+    prob.apply(dut, v_set, nhmf.NHMF_FP64, nhmf.NHMF_ON_THE_FLY)
+    assert np.array_equal(host(v_set), host(v_at))
+    with pytest.raises(nhmf.NhmfError):
+        prob.apply_at(ut, dut, dut)                   # v aliasing du
+    prob.close()
+
+
 def test_q1_8_clamp_workload(nhmf):
     w = inp.WORKLOADS["q1_8_clamp"]
     u, du = inp.draw_u(w), inp.draw_du(w)
