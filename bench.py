@@ -249,6 +249,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     strategy = args.strategy
+    if strategy == "spatial":
+        raise SystemExit("--strategy spatial is measured by --mode kernel (and reported as a variant)")
     strat = nhmf.NHMF_CACHED if strategy == "cached" else nhmf.NHMF_ON_THE_FLY
 
     main = args.apply_workload
@@ -471,6 +473,38 @@ def he_init_flat(seed=5000):
 NEWTON_METRIC = "Newton time to 1e-8 (mixed FP32-inner / learned vs plain FP64 Jacobi-CG)"
 
 
+def run_kernel(args):
+    """One apply kernel alone (for profiling the variants): `--precision` x `--strategy` on
+    `--apply-workload`, only the point cache it reads built, `--warmup` + `--steps` applies;
+    prints the mean device time per apply."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2505_15535_gb300 import nhmf
+    dev = torch.device("cuda", 0)
+    w = inp.WORKLOADS[args.apply_workload]
+    prec = {"fp64": nhmf.NHMF_FP64, "fp32": nhmf.NHMF_FP32, "df64": nhmf.NHMF_DF64}[args.precision]
+    strat = {"cached": nhmf.NHMF_CACHED, "otf": nhmf.NHMF_ON_THE_FLY, "spatial": nhmf.NHMF_SPATIAL}[args.strategy]
+    mask = {nhmf.NHMF_FP64: nhmf.NHMF_CACHE_FP64, nhmf.NHMF_FP32: nhmf.NHMF_CACHE_FP32,
+            nhmf.NHMF_DF64: nhmf.NHMF_CACHE_DF64}[prec]
+    if strat == nhmf.NHMF_SPATIAL:
+        mask = nhmf.NHMF_CACHE_SPATIAL
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(torch.from_numpy(inp.draw_u(w)).to(dev), mask if strat != nhmf.NHMF_ON_THE_FLY else 0)
+    dt = torch.float32 if prec == nhmf.NHMF_FP32 else torch.float64
+    du = torch.from_numpy(inp.draw_du(w)).to(dev).to(dt)
+    v = torch.empty_like(du)
+    for _ in range(args.warmup):
+        prob.apply(du, v, prec, strat)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    step_ms, kernel_ms, launches = time_applies(torch, prob, nhmf, du, v, prec, strat, args.steps, flush)
+    print(json.dumps({"mode": "kernel", "workload": w.name, "precision": args.precision, "strategy": args.strategy,
+                      "steps": args.steps, "kernel_ms": kernel_ms, "step_ms": step_ms,
+                      "gdofs": w.n_dofs / (step_ms * 1e-3) / 1e9}), flush=True)
+    prob.close()
+    return 0
+
+
 def run_newton(args):
     """Load steps of the compression workload, one solve call per step, for each solver.
 
@@ -645,12 +679,15 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--strategy", choices=["cached", "otf"], default="cached")
+    ap.add_argument("--strategy", choices=["cached", "otf", "spatial"], default="cached",
+                    help="apply and kernel modes (spatial: kernel mode only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["apply", "newton", "unet"], default="apply")
+    ap.add_argument("--mode", choices=["apply", "newton", "unet", "kernel"], default="apply")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64",
+                    help="kernel mode: arithmetic of the apply")
     ap.add_argument("--workload", default="q2_64_compress")
     ap.add_argument("--apply-workload", default=MAIN)
     ap.add_argument("--solvers", default="plain,mixed,learned,mixed_learned")
@@ -667,6 +704,8 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "kernel":
+        return run_kernel(args)
     if args.mode == "newton":
         return run_newton(args)
     if args.mode == "unet":

@@ -292,8 +292,13 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 // mu and h ride on the transposed tables and the material factor on du.  The on-the-fly kernel
 // runs its B and B^T passes in even-odd form at odd n; the cached kernel keeps the matrix form,
 // whose unrolled code fits its registers without spilling.
+#ifndef NHMF_REG_THREADS
+#define NHMF_REG_THREADS 128
+#endif
+constexpr int kRegThreads = NHMF_REG_THREADS;  // threads (= elements) per block
+
 template <int P, int STRAT, int MODEL>
-__global__ void __launch_bounds__(128) k_apply_reg(const OpArgs a) {
+__global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n;
   const long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (ec >= a.col.count) return;
@@ -852,7 +857,7 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   const bool split = STRAT == NHMF_ON_THE_FLY && c->prm.model == NHMF_MODEL_SPLIT;
   if constexpr (sizeof(T) == 4 && P <= kRegMaxP) {
     auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
-    st = run_colours(c, k, a, 128, 128, 0, s, "apply", NHMF_KIND_APPLY);
+    st = run_colours(c, k, a, kRegThreads, kRegThreads, 0, s, "apply", NHMF_KIND_APPLY);
   } else {
     auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;
     st = run_colours(c, k, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
