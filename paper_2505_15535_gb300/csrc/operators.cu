@@ -160,11 +160,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
       gather<P, NI>(a, a.u32, e0, nvalid, false, G);
     __syncthreads();
     if constexpr (EO) {
-      eo_pass<n, NI, 3, 0, false, TH>(kB, G, Vq);
+      eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq);
       __syncthreads();
-      eo_pass<n, NI, 3, 1, false, TH>(kB, Vq, G);
+      eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G);
       __syncthreads();
-      eo_pass<n, NI, 3, 2, false, TH>(kB, G, U);
+      eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, U);
       __syncthreads();
     } else {
       to_points<n, NI>(sB, G, Vq, U);
@@ -174,16 +174,16 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
                 a.factor ? (const T*)sF : nullptr);
   __syncthreads();
   if constexpr (EO) {
-    eo_pass<n, NI, 3, 0, false, TH>(kB, G, Vq);
+    eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, TH>(kB, Vq, G);
+    eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, TH>(kB, G, Vq);
+    eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, Vq);
     __syncthreads();
     // reference gradient of du: G[3c+d] = Dc along d of du[c]
-    eo_pass<n, NI, 3, 0, true, TH, 3, 0>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 1, true, TH, 3, 1>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 2, true, TH, 3, 2>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 3, 0>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 3, 1>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 3, 2>(kDc, Vq, G);
     __syncthreads();
   } else {
     to_points<n, NI>(sB, G, Vq + 0, Vq);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
@@ -272,11 +272,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   if constexpr (EO) {
     colloc_grad_T<n, NI>(sDcW, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 0, false, TH>(kBW, Vq, G);
+    eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, TH>(kBW, G, Vq);
+    eo_pass<n, NI, 3, 1, false, kEoCentreCol, TH>(kBW, G, Vq);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, TH>(kBW, Vq, G + 3 * NI);
+    eo_pass<n, NI, 3, 2, false, kEoCentreCol, TH>(kBW, Vq, G + 3 * NI);
     __syncthreads();
   } else {
     from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI);
@@ -315,6 +315,8 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
   // one 1D pass over the n^2 lines of direction DIR of f[c]: even-odd coefficients `eo` (odd
   // n) or the matrix Mat(r, m) = mat[r n + m] (TR = false) / mat[m n + r] (TR = true)
   auto pass = [&](float (&f)[n3], int dir, const float (&eo)[kEoSlots], const float* mat, bool tr) {
+    // tr = false: the forward B (centre row e_h); tr = true: the transposed B^T w (centre
+    // column zero off the centre) -- see eo_line
     const int st = dir == 0 ? 1 : (dir == 1 ? n : n * n);
 #pragma unroll
     for (int b = 0; b < n * n; ++b) {
@@ -323,7 +325,10 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
 #pragma unroll
       for (int m = 0; m < n; ++m) x[m] = f[base + m * st];
       if constexpr (n % 2 == 1 && STRAT == NHMF_ON_THE_FLY) {
-        eo_line<n, false>(eo, x, y);
+        if (tr)
+          eo_line<n, false, kEoCentreCol>(eo, x, y);
+        else
+          eo_line<n, false, kEoCentreRow>(eo, x, y);
       } else {
 #pragma unroll
         for (int r = 0; r < n; ++r) {

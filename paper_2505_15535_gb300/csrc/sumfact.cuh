@@ -162,7 +162,11 @@ __device__ __forceinline__ void sf_pass(const T* __restrict__ mat, const T* in, 
 //   y_r = E_r + O_r,  y_{n-1-r} = +-(E_r - O_r),  y_h = E_h (symmetric) or O_h (anti),
 // with S_rm = (M_rm + M_r,n-1-m) / 2, A_rm = (M_rm - M_r,n-1-m) / 2, C_r = M_rh.  n = 3 takes 8
 // (symmetric) or 7 (anti) operations per line instead of 9; n = 5 takes 21 or 20 instead of 25.
-template <int n, bool ANTI, typename T>
+// FORM uses that the middle Gauss point is the middle GLL node (x = 1/2) for odd n:
+//   kEoCentreRow:  the centre row of M is e_h (M = B): y_h = x_h, 2 (n = 3) or 3 (n = 5) fewer;
+//   kEoCentreCol:  the centre column of M vanishes off the centre (M = B^T w): C_r = 0 for r < h.
+enum { kEoGeneral = 0, kEoCentreRow = 1, kEoCentreCol = 2 };
+template <int n, bool ANTI, int FORM, typename T>
 __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n], T (&y)[n]) {
   constexpr int h = n / 2, A0 = (h + 1) * h, C0 = 2 * (h + 1) * h;
   T e[h], o[h];
@@ -173,9 +177,16 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
   }
 #pragma unroll
   for (int r = 0; r < h; ++r) {
-    T E = k[C0 + r] * x[h];
+    T E;
+    if constexpr (FORM == kEoCentreCol) {
+      E = k[r * h] * e[0];
 #pragma unroll
-    for (int m = 0; m < h; ++m) E = fma(k[r * h + m], e[m], E);
+      for (int m = 1; m < h; ++m) E = fma(k[r * h + m], e[m], E);
+    } else {
+      E = k[C0 + r] * x[h];
+#pragma unroll
+      for (int m = 0; m < h; ++m) E = fma(k[r * h + m], e[m], E);
+    }
     T yp = E, ym = ANTI ? -E : E;
 #pragma unroll
     for (int m = 0; m < h; ++m) {
@@ -190,6 +201,8 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 #pragma unroll
     for (int m = 1; m < h; ++m) c = fma(k[A0 + h * h + m], o[m], c);
     y[h] = c;
+  } else if constexpr (FORM == kEoCentreRow) {
+    y[h] = x[h];
   } else {
     T c = k[C0 + h] * x[h];
 #pragma unroll
@@ -203,7 +216,7 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 // where M is given by its even-odd coefficients `coef` (see eo_line).
 // TH is the block size; the task loop is unrolled so that independent lines interleave (not for
 // double-float, whose unrolled lines would cost an SM its second block).
-template <int n, int NI, int NC, int DIR, bool ANTI, int TH, int OS = 1, int OO = 0, typename T>
+template <int n, int NI, int NC, int DIR, bool ANTI, int FORM, int TH, int OS = 1, int OO = 0, typename T>
 __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __restrict__ in,
                                         T* __restrict__ out) {
   constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n, ITER = (NC * NL + TH - 1) / TH;
@@ -221,7 +234,7 @@ __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __r
     T x[n], y[n];
 #pragma unroll
     for (int m = 0; m < n; ++m) x[m] = in[c * NI + base + m * s];
-    eo_line<n, ANTI>(k, x, y);
+    eo_line<n, ANTI, FORM>(k, x, y);
 #pragma unroll
     for (int m = 0; m < n; ++m) out[(c * OS + OO) * NI + base + m * s] = y[m];
   }
