@@ -514,7 +514,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     };
     st = fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
     if (st != NHMF_ERR_BREAKDOWN) return st;
-    // a breakdown left: solve with Jacobi-CG from scratch (the judge of the method)
+    // a breakdown left: solve with Jacobi-CG from scratch (the reference solver of the method)
     *fallbacks += 1;
     cudaMemsetAsync(x.c->status, 0, sizeof(unsigned), x.s);
     return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
