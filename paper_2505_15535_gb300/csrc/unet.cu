@@ -674,6 +674,92 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
   tc_teardown(tmem, kUpCols, timed_out, status);
 }
 
+// Weight gradient of the stride-1 gather, tiled: G[tap][a][b] = sum_v P[v][a] Q[v + d_tap][b].
+// A block takes tiles of 128 consecutive positions of one z-plane in x-padded row order (as
+// k_conv_tc) along a column in z.  It stages the tile's P rows and a ring of Q planes (the
+// z - 1 .. z + 1 windows of all taps, zero outside the grid) as 16-byte channel halves, so
+// that every 8 x 8 block of a fragment is one ldmatrix: per chunk of 16 positions one
+// ldmatrix.x4.trans gives the A fragment (P^T, channels a x positions) for all the warp's
+// taps, and one per tap gives the B fragments (positions x channels b) of both n-tiles.
+// 9 warps, warp w owns taps 3w..3w+2; per-block partials as in k_wgrad.
+constexpr int kWgThreads = 288;
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+size_t wgrad_s1_smem(int m) { return 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16; }
+
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __restrict__ P,
+                                                         const __nv_bfloat16* __restrict__ Q, int m, int zc,
+                                                         float* partial) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int R = m + 2, L = 130 + 2 * R;
+  unsigned char* sP = sm;                       // [2 halves][128][16 B]
+  unsigned char* sQ = sm + 2 * 128 * 16;        // [4 slots][2 halves][L][16 B]
+  auto slot = [&](int plane) { return sQ + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
+  const long long nunits = (long long)per_plane * nzc;
+  float acc[3][2][4] = {};
+  // ldmatrix row of this lane: matrix lane / 8, row lane % 8
+  const int lm = lane >> 3, lr = lane & 7;
+  for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
+    tc_stage(Q, m, R, L, p0 - 1, 1, 1, zb - 1, slot(zb - 1));
+    tc_stage(Q, m, R, L, p0 - 1, 1, 1, zb, slot(zb));
+    for (int z = zb; z < ze; ++z) {
+      tc_stage(Q, m, R, L, p0 - 1, 1, 1, z + 1, slot(z + 1));
+      // P rows: position p0 + j = y R + x + 1 of plane z (zero on the pad columns and past the plane)
+      for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+        const int p = p0 + j, y = p / R, x = p % R - 1;
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if (p < m * R && x >= 0 && x < m) {
+          const uint4* src = reinterpret_cast<const uint4*>(P) + 2 * (x + (long long)m * (y + (long long)m * z));
+          lo = __ldg(src);
+          hi = __ldg(src + 1);
+        }
+        *reinterpret_cast<uint4*>(sP + j * 16) = lo;
+        *reinterpret_cast<uint4*>(sP + (128 + j) * 16) = hi;
+      }
+      __syncthreads();
+      const uint32_t sp = smem_u32(sP);
+      for (int c = 0; c < 8; ++c) {
+        // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * 128 + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
+#pragma unroll
+        for (int jt = 0; jt < 3; ++jt) {
+          const int tap = 3 * warp + jt;
+          const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+          const int row = R + 1 + dx + dy * R + 16 * c;  // staged row of position 16c of plane z + dz
+          // B: matrices (k 0-7, b lo), (k 8-15, b lo), (k 0-7, b hi), (k 8-15, b hi)
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4_trans(smem_u32(slot(z + dz)) + (uint32_t)(((lm >> 1) * L + row + (lm & 1) * 8 + lr) * 16), b0, b1,
+                        b2, b3);
+          mma16816(acc[jt][0], a0, a1, a2, a3, b0, b1);
+          mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  float* out = partial + (long long)blockIdx.x * 27 * 256;
+#pragma unroll
+  for (int jt = 0; jt < 3; ++jt) {
+    const int tap = 3 * warp + jt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = 8 * h + 2 * t;
+      out[tap * 256 + g * 16 + b] = acc[jt][h][0];
+      out[tap * 256 + g * 16 + b + 1] = acc[jt][h][1];
+      out[tap * 256 + (g + 8) * 16 + b] = acc[jt][h][2];
+      out[tap * 256 + (g + 8) * 16 + b + 1] = acc[jt][h][3];
+    }
+  }
+}
+
 template <int G>
 void conv_launch(const ConvArgs& a, cudaStream_t s) {
   k_conv<G><<<kConvBlocks, 256, 0, s>>>(a);
@@ -719,12 +805,19 @@ void conv(int gather, const __nv_bfloat16* in, int m_in, const __nv_bfloat16* w,
 
 void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
            cudaStream_t s) {
-  const long long nks = ((long long)mp * mp * mp + 15) / 16;
-  const int blocks = (int)std::min<long long>(kWgBlocks, nks);
-  if (gather == S1)
-    k_wgrad<S1><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
-  else
+  int blocks;
+  if (gather == S1) {  // stride 1: P and Q on the same grid (mp == mq)
+    const size_t smem = wgrad_s1_smem(mp);
+    cudaFuncSetAttribute(k_wgrad_s1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long per_plane = ((long long)mp * (mp + 2) + 127) / 128;
+    const int zc = tc_column(per_plane, mp);
+    blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
+    k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, u.partial);
+  } else {
+    const long long nks = ((long long)mp * mp * mp + 15) / 16;
+    blocks = (int)std::min<long long>(kWgBlocks, nks);
     k_wgrad<DOWN2><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
+  }
   const UNetLayer& L = u.L[layer];
   k_wgrad_reduce<<<(27 * 256 + 255) / 256, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
 }
