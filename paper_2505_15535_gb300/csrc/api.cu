@@ -1,4 +1,5 @@
 // C ABI of the library (declarations and contracts in include/nhmf.h).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -63,6 +64,9 @@ nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
   c->prm = *prm;
   build_geometry(*prm, &c->g);
   build_tables(prm->degree, &c->tab);
+  long long min_colour = c->g.colour[0].count;
+  for (int k = 1; k < 8; ++k) min_colour = std::min<long long>(min_colour, c->g.colour[k].count);
+  c->reg32 = prm->degree <= kRegMaxP && min_colour >= kRegMinColour;
   cudaGetDevice(&c->device);
   nhmf_status st = cuda_check(c, cudaMalloc(&c->status, sizeof(unsigned)), "status alloc");
   if (st == NHMF_OK) st = cuda_check(c, cudaMemset(c->status, 0, sizeof(unsigned)), "status clear");

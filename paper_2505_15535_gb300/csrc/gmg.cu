@@ -81,6 +81,26 @@ __global__ void k_mul(long long n, const double* __restrict__ a, double* __restr
     x[i] *= a[i];
 }
 
+// x *= 1 / *nrm (x stays as it is when *nrm is not positive)
+template <typename T>
+__global__ void k_scale_inv(long long n, const double* __restrict__ nrm, T* __restrict__ x) {
+  const double s = *nrm > 0.0 ? 1.0 / *nrm : 1.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = T(x[i] * s);
+}
+
+template <typename T>
+__global__ void k_mul_t(long long n, const T* __restrict__ a, T* __restrict__ x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= a[i];
+}
+
+template <typename T>
+__global__ void k_to(long long n, const double* __restrict__ x, T* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = T(x[i]);
+}
+
 __global__ void k_scale(long long n, double s, double* __restrict__ x) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] *= s;
@@ -301,8 +321,35 @@ nhmf_status gmg_build(nhmf_ctx* c) {
   return NHMF_OK;
 }
 
+// Power iteration for the largest eigenvalue of D^-1 A on level L in precision T (12 steps).
+// The vector is normalised on the device; the host reads the two norms once at the end.
+template <typename T>
+nhmf_status power_iteration(nhmf_ctx* c, GmgLevel& L, int strategy, cudaStream_t s) {
+  T* x = Buf<T>::x(L);
+  T* q = Buf<T>::q(L);
+  const T* dinv = Buf<T>::dinv(L);
+  double* sc = L.ctx->work->sc;
+  nhmf_status st;
+  k_start<<<kB, kT, 0, s>>>(L.n, L.x);
+  if constexpr (sizeof(T) == 4) k_to<float><<<kB, kT, 0, s>>>(L.n, L.x, L.x32);
+  for (int it = 0; it < 12; ++it) {
+    if ((st = launch_apply(L.ctx, sizeof(T) == 8 ? NHMF_FP64 : NHMF_FP32, strategy, x, q, s)) != NHMF_OK) return st;
+    k_mul_t<T><<<kB, kT, 0, s>>>(L.n, dinv, q);
+    norm2(L.n, x, sc + 40, L.ctx->work->partials, s);
+    norm2(L.n, q, sc + 41, L.ctx->work->partials, s);
+    cudaMemcpyAsync(x, q, L.n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    k_scale_inv<T><<<kB, kT, 0, s>>>(L.n, sc + 41, x);
+  }
+  double h[2];
+  cudaMemcpyAsync(h, sc + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if ((st = cuda_check(c, cudaStreamSynchronize(s), "gmg power iteration")) != NHMF_OK) return st;
+  L.lmax = (h[0] > 0.0 && h[1] > 0.0) ? h[1] / h[0] : 2.0;
+  return NHMF_OK;
+}
+
 // Level linearisation points, diagonals and eigenvalue estimates at the fine point c->ubar.
-nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero) {
+nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero,
+                        const double* fine_diag) {
   nhmf_status st = gmg_build(c);
   if (st != NHMF_OK) return st;
   Gmg& G = *c->gmg;
@@ -321,28 +368,16 @@ nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bo
   }
   for (int l = 0; l < nl; ++l) {
     GmgLevel& L = G.L[l];
-    if ((st = launch_diagonal(L.ctx, L.diag, s)) != NHMF_OK) return st;
+    if (l == nl - 1 && fine_diag)  // the fine level's diagonal, computed by the caller
+      cudaMemcpyAsync(L.diag, fine_diag, L.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else if ((st = launch_diagonal(L.ctx, L.diag, s)) != NHMF_OK)
+      return st;
     reciprocal(L.n, L.diag, L.dinv, L.dinv32, s);
     if (l == 0) continue;  // the coarsest level is solved, not smoothed
-    // power iteration for the largest eigenvalue of D^-1 A (FP64, 12 steps)
-    const int strat64 = strategy;
-    k_start<<<kB, kT, 0, s>>>(L.n, L.x);
-    double nv = 0.0, nw = 0.0;
-    for (int it = 0; it < 12; ++it) {
-      if ((st = launch_apply(L.ctx, NHMF_FP64, strat64, L.x, L.q, s)) != NHMF_OK) return st;
-      k_mul<<<kB, kT, 0, s>>>(L.n, L.dinv, L.q);
-      norm2(L.n, L.x, L.ctx->work->sc + 40, L.ctx->work->partials, s);
-      norm2(L.n, L.q, L.ctx->work->sc + 41, L.ctx->work->partials, s);
-      double h[2];
-      cudaMemcpyAsync(h, L.ctx->work->sc + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-      if ((st = cuda_check(c, cudaStreamSynchronize(s), "gmg power iteration")) != NHMF_OK) return st;
-      nv = h[0];
-      nw = h[1];
-      if (!(nw > 0.0)) break;
-      cudaMemcpyAsync(L.x, L.q, L.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-      k_scale<<<kB, kT, 0, s>>>(L.n, 1.0 / nw, L.x);
-    }
-    L.lmax = nv > 0.0 ? nw / nv : 2.0;
+    // in the precision of the V-cycle (Algorithm 2 has no FP32 apply)
+    st = (fp32 && strategy != NHMF_SPATIAL) ? power_iteration<float>(c, L, strategy, s)
+                                            : power_iteration<double>(c, L, strategy, s);
+    if (st != NHMF_OK) return st;
   }
   return cuda_check(c, cudaGetLastError(), "gmg prepare");
 }

@@ -36,7 +36,9 @@ void gmg_free(nhmf_ctx* c);
 nhmf_status gmg_build(nhmf_ctx* c);
 // Level linearisation points (interpolated from the fine one, or zero on the coarse levels),
 // diagonals and eigenvalue estimates.
-nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero);
+// fine_diag: the fine operator's diagonal if the caller has it (else it is computed).
+nhmf_status gmg_prepare(nhmf_ctx* c, int strategy, bool fp32, cudaStream_t s, bool coarse_at_zero,
+                        const double* fine_diag = nullptr);
 // per-level buffers by precision
 template <typename T> struct Buf;
 template <> struct Buf<double> {

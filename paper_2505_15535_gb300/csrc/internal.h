@@ -11,6 +11,19 @@ namespace nhmf {
 
 constexpr int kMaxN = 5;  // p + 1 for p <= 4
 
+// FP32 applies up to degree kRegMaxP use the one-element-per-thread register kernel (with its
+// [10][n^3][E] point-cache layout) when every colour class has at least kRegMinColour
+// elements; smaller meshes (coarse multigrid levels) and higher degrees use the shared-memory
+// kernel, whose latency per launch does not grow with the element's work.
+#ifndef NHMF_REG_MAXP
+#define NHMF_REG_MAXP 2
+#endif
+#ifndef NHMF_REG_MIN_COLOUR
+#define NHMF_REG_MIN_COLOUR 32768
+#endif
+constexpr int kRegMaxP = NHMF_REG_MAXP;
+constexpr long long kRegMinColour = NHMF_REG_MIN_COLOUR;
+
 // 1D tables of the Q_p element on [0, 1] (Section 2.2, 2.4), FP64.
 //   B[q][i]  = l_i(x_q): GLL Lagrange basis at the Gauss points
 //   Dc[q][r] = derivative of the Lagrange basis on the Gauss points, at Gauss point q
@@ -80,6 +93,7 @@ struct nhmf_ctx {
   double* factor = nullptr;   // [E] per-element material factors (natural order), or null
   unsigned* status = nullptr; // device status word: bit 0 det F <= 0, bit 1 non-finite
   bool have_lin = false;
+  bool reg32 = false;  // FP32 applies on the register kernel (see kRegMinColour)
   const double* u_at = nullptr;  // set only while nhmf_tangent_apply_at launches its apply
   std::string err;
   // kernel timing (nhmf_profile_enable): event pairs per operator kind

@@ -97,26 +97,26 @@ __device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long 
 
 // Forward interpolation of three components to the points: in -> out (tmp is clobbered).
 template <int n, int NI, typename T>
-__device__ __forceinline__ void to_points(const T* sB, T* in, T* tmp, T* out) {
-  sf_pass<n, NI, 3, 0, false, false>(sB, in, tmp);
+__device__ __forceinline__ void to_points(const T* sB, T* in, T* tmp, T* out, int nitems) {
+  sf_pass<n, NI, 3, 0, false, false>(sB, in, tmp, nitems);
   __syncthreads();
-  sf_pass<n, NI, 3, 1, false, false>(sB, tmp, in);
+  sf_pass<n, NI, 3, 1, false, false>(sB, tmp, in, nitems);
   __syncthreads();
-  sf_pass<n, NI, 3, 2, false, false>(sB, in, out);
+  sf_pass<n, NI, 3, 2, false, false>(sB, in, out, nitems);
   __syncthreads();
 }
 
 // Transposed integration of the nine point fluxes G[3c+d] to nodal values in `out`
 // (`tmp` clobbered; G's first three slots are reused).
 template <int n, int NI, typename T>
-__device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* tmp, T* out) {
-  colloc_grad_T<n, NI>(sDc, G, tmp);
+__device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* tmp, T* out, int nitems) {
+  colloc_grad_T<n, NI>(sDc, G, tmp, nitems);
   __syncthreads();
-  sf_pass<n, NI, 3, 0, true, false>(sB, tmp, G);
+  sf_pass<n, NI, 3, 0, true, false>(sB, tmp, G, nitems);
   __syncthreads();
-  sf_pass<n, NI, 3, 1, true, false>(sB, G, tmp);
+  sf_pass<n, NI, 3, 1, true, false>(sB, G, tmp, nitems);
   __syncthreads();
-  sf_pass<n, NI, 3, 2, true, false>(sB, tmp, out);
+  sf_pass<n, NI, 3, 2, true, false>(sB, tmp, out, nitems);
   __syncthreads();
 }
 
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   load_apply_tables<P>(a, tab);
   const long long e0 = (long long)blockIdx.x * NE;
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
+  const int nitems = nvalid * n3, nlines = nvalid * n * n;  // items / lines of present elements
   for (int e = threadIdx.x; e < NE; e += blockDim.x) sF[e] = T(elem_factor(a, e0 + min(e, nvalid - 1)));
   __syncthreads();
 
@@ -160,40 +161,40 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
       gather<P, NI>(a, a.u32, e0, nvalid, false, G);
     __syncthreads();
     if constexpr (EO) {
-      eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq);
+      eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
       __syncthreads();
-      eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G);
+      eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines);
       __syncthreads();
-      eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, U);
+      eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, U, nlines);
       __syncthreads();
     } else {
-      to_points<n, NI>(sB, G, Vq, U);
+      to_points<n, NI>(sB, G, Vq, U, nitems);
     }
   }
   gather<P, NI>(a, static_cast<const typename Store<T>::type*>(a.du), e0, nvalid, true, G,
                 a.factor ? (const T*)sF : nullptr);
   __syncthreads();
   if constexpr (EO) {
-    eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq);
+    eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G);
+    eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, Vq);
+    eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
     __syncthreads();
     // reference gradient of du: G[3c+d] = Dc along d of du[c]
-    eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 3, 0>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 3, 1>(kDc, Vq, G);
-    eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 3, 2>(kDc, Vq, G);
+    eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 3, 0>(kDc, Vq, G, nlines);
+    eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 3, 1>(kDc, Vq, G, nlines);
+    eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 3, 2>(kDc, Vq, G, nlines);
     __syncthreads();
   } else {
-    to_points<n, NI>(sB, G, Vq + 0, Vq);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
+    to_points<n, NI>(sB, G, Vq + 0, Vq, nitems);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
   }
 
   const T inv_mu = T(1.0 / a.mu), r2 = T(a.r2mu);
   const typename Store<T>::type* cache = static_cast<const typename Store<T>::type*>(a.cache);
   const long long cbase = (a.col.slot0 + e0) * n3;
   bool bad = false;
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     T dH[9], g[9];
     if constexpr (EO) {
 #pragma unroll
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
           }
           const float2 z = cdf[9 * a.nq + cbase + t];
           lnJ = T(z.x, z.y);
-        } else if (sizeof(typename Store<T>::type) == 8 || P > kRegMaxP) {
+        } else if (sizeof(typename Store<T>::type) == 8 || P > kRegMaxP || !a.reg32) {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
           lnJ = T(cache[9 * a.nq + cbase + t]);
@@ -270,16 +271,16 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   if (bad) atomicOr(a.status, kStatusNonPosJ);
   __syncthreads();
   if constexpr (EO) {
-    colloc_grad_T<n, NI>(sDcW, G, Vq);
+    colloc_grad_T<n, NI>(sDcW, G, Vq, nitems);
     __syncthreads();
-    eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G);
+    eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G, nlines);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, kEoCentreCol, TH>(kBW, G, Vq);
+    eo_pass<n, NI, 3, 1, false, kEoCentreCol, TH>(kBW, G, Vq, nlines);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, kEoCentreCol, TH>(kBW, Vq, G + 3 * NI);
+    eo_pass<n, NI, 3, 2, false, kEoCentreCol, TH>(kBW, Vq, G + 3 * NI, nlines);
     __syncthreads();
   } else {
-    from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI);
+    from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI, nitems);
   }
   scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<typename Store<T>::type*>(a.v));
 }
@@ -480,12 +481,11 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
   gather<P, NI>(a, a.u64, e0, nvalid, false, A);
   __syncthreads();
-  to_points<n, NI>(sB, A, Vq, Vq);
+  to_points<n, NI>(sB, A, Vq, Vq, nvalid * n3);
   const double invh = 1.0 / a.h;
   const long long cbase = (a.col.slot0 + e0) * n3;
   bool bad = false;
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
-    if (t / n3 >= nvalid) continue;
+  for (int t = threadIdx.x; t < nvalid * n3; t += blockDim.x) {
     double H[9], Fi[9], lnJ;
     colloc_grad<n, NI>(sDc, Vq, t, H);
 #pragma unroll
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       a.cachedf_out[9 * a.nq + cbase + t] = split(lnJ);
     }
     if (a.cache32_out) {
-      if (P <= kRegMaxP) {
+      if (P <= kRegMaxP && a.reg32) {
         // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
         // elements of a colour are contiguous
         const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
@@ -579,10 +579,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, double, 0>::THREADS) k_residual(c
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
   gather<P, NI>(a, a.u64, e0, nvalid, false, G);
   __syncthreads();
-  to_points<n, NI>(sB, G, Vq, Vq);
+  const int nitems = nvalid * n3;
+  to_points<n, NI>(sB, G, Vq, Vq, nitems);
   const double invh = 1.0 / a.h;
   unsigned flags = 0;
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     double H[9], Fi[9], lnJ;
     colloc_grad<n, NI>(sDc, Vq, t, H);
 #pragma unroll
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, double, 0>::THREADS) k_residual(c
   }
   if (flags) atomicOr(a.status, flags);
   __syncthreads();
-  from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI);
+  from_points<n, NI>(sB, sDc, G, Vq, G + 3 * NI, nitems);
   scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<double*>(a.v));
 }
 
@@ -640,9 +641,10 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
   gather<P, NI>(a, a.u64, e0, nvalid, false, S);
   __syncthreads();
-  to_points<n, NI>(sB, S, tmp, tmp);
+  const int nitems = nvalid * n3;
+  to_points<n, NI>(sB, S, tmp, tmp, nitems);
   const double invh = 1.0 / a.h;
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     double H[9], Fi[9], lnJ;
     colloc_grad<n, NI>(sDc, tmp, t, H);
 #pragma unroll
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
   __syncthreads();
   for (int d = 0; d < 3; ++d)
     for (int l = d; l < 3; ++l) {
-      for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+      for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
         const double s = sW[t % n3] * (d == l ? 1.0 : 2.0) * elem_factor(a, e0 + min(t / n3, nvalid - 1));
         if (a.model == NHMF_MODEL_SPLIT) {
           // L_cdcl = mu a d_dl - 2/3 mu a (F_cd Fi_lc + Fi_dc F_cl) + (2/9 mu a I1 + kappa J^2
@@ -693,11 +695,11 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_diagonal(const OpAr
       const T* mx = (d == 0 && l == 0) ? sDD : ((d == 0 || l == 0) ? sBD : sBB);
       const T* my = (d == 1 && l == 1) ? sDD : ((d == 1 || l == 1) ? sBD : sBB);
       const T* mz = (d == 2 && l == 2) ? sDD : ((d == 2 || l == 2) ? sBD : sBB);
-      sf_pass<n, NI, 3, 0, true, false>(mx, S, tmp);
+      sf_pass<n, NI, 3, 0, true, false>(mx, S, tmp, nitems);
       __syncthreads();
-      sf_pass<n, NI, 3, 1, true, false>(my, tmp, S);
+      sf_pass<n, NI, 3, 1, true, false>(my, tmp, S, nitems);
       __syncthreads();
-      sf_pass<n, NI, 3, 2, true, true>(mz, S, R);
+      sf_pass<n, NI, 3, 2, true, true>(mz, S, R, nitems);
       __syncthreads();
     }
   scatter_add<P, NI>(a, R, e0, nvalid, static_cast<double*>(a.v));
@@ -785,6 +787,7 @@ OpArgs base_args(nhmf_ctx* c) {
     eo_pack(BWt, n, a.eo[2]);
   }
   a.r2mu = 2.0 * c->prm.lambda / c->prm.mu;
+  a.reg32 = c->reg32 ? 1 : 0;
   for (int i = 0; i < kMaxN * kMaxN; ++i) {
     a.BWf[i] = float(a.BW[i]);
     a.DcWf[i] = float(a.DcW[i]);
@@ -860,9 +863,13 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   // branch would charge the split model's registers to every model)
   constexpr int SPLIT = STRAT == NHMF_ON_THE_FLY ? NHMF_MODEL_SPLIT : NHMF_MODEL_COMPRESSIBLE;
   const bool split = STRAT == NHMF_ON_THE_FLY && c->prm.model == NHMF_MODEL_SPLIT;
-  if constexpr (sizeof(T) == 4 && P <= kRegMaxP) {
-    auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
-    st = run_colours(c, k, a, kRegThreads, kRegThreads, 0, s, "apply", NHMF_KIND_APPLY);
+  bool reg = false;
+  if constexpr (sizeof(T) == 4 && P <= kRegMaxP) reg = c->reg32;
+  if (reg) {
+    if constexpr (sizeof(T) == 4 && P <= kRegMaxP) {
+      auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
+      st = run_colours(c, k, a, kRegThreads, kRegThreads, 0, s, "apply", NHMF_KIND_APPLY);
+    }
   } else {
     auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;
     st = run_colours(c, k, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);

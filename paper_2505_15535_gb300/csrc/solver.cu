@@ -479,8 +479,8 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
   }
   if (o.solver == NHMF_SOLVER_GMG || o.solver == NHMF_SOLVER_MIXED_GMG) {
     const bool f32 = o.solver == NHMF_SOLVER_MIXED_GMG;
-    nhmf_status st = gmg_prepare(x.c, o.strategy, f32, x.s, false);
-    if (st == NHMF_ERR_NONPOS_J) st = gmg_prepare(x.c, o.strategy, f32, x.s, true);  // folded coarse state
+    nhmf_status st = gmg_prepare(x.c, o.strategy, f32, x.s, false, w.diag);
+    if (st == NHMF_ERR_NONPOS_J) st = gmg_prepare(x.c, o.strategy, f32, x.s, true, w.diag);  // folded coarse state
     if (st != NHMF_OK) return st;
     {
       // SPD probe of the coarsest level: Jacobi-CG on a fixed right-hand side.  If the coarse
@@ -495,7 +495,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
         nhmf_status ps = pcg<double>(cx, o.strategy, C0.b, C0.x, C0.dinv, C0.r, C0.d, C0.t1, C0.t2, 1e-6, 300, 10, RZ0,
                                      &it, &rel);
         if (ps == NHMF_ERR_BREAKDOWN) {
-          if ((st = gmg_prepare(x.c, o.strategy, f32, x.s, true)) != NHMF_OK) return st;
+          if ((st = gmg_prepare(x.c, o.strategy, f32, x.s, true, w.diag)) != NHMF_OK) return st;
         } else if (ps != NHMF_OK) {
           return ps;
         }

@@ -39,12 +39,6 @@ template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; 
 template <> struct Cfg<2, float> { static constexpr int NE = NHMF_Q2F_NE, THREADS = NHMF_Q2F_THREADS; };
 template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
 template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
-// FP32 applies up to this degree use the one-element-per-thread register kernel (and its
-// [10][n^3][E] point-cache layout); higher degrees use the shared-memory kernel.
-#ifndef NHMF_REG_MAXP
-#define NHMF_REG_MAXP 2
-#endif
-constexpr int kRegMaxP = NHMF_REG_MAXP;
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
 template <> struct Cfg<4, df64> { static constexpr int NE = 4, THREADS = 256; };
@@ -78,6 +72,7 @@ struct OpArgs {
   double BW[kMaxN * kMaxN], DcW[kMaxN * kMaxN], Dch[kMaxN * kMaxN];
   double eo[3][kEoSlots];
   double r2mu;
+  int reg32;  // FP32 point cache in the register kernel's [10][n^3][E] layout (see kRegMaxP)
   float BWf[kMaxN * kMaxN], DcWf[kMaxN * kMaxN], Dchf[kMaxN * kMaxN], eof[3][kEoSlots];  // FP32 copies
   float Bf[kMaxN * kMaxN], Dcf[kMaxN * kMaxN], wf[kMaxN];  // FP32 copies (register kernels)
   const double* u64;
@@ -126,10 +121,11 @@ __device__ __forceinline__ double elem_factor(const OpArgs& a, long long e_in_co
 // One 1D pass along direction DIR over NC arrays of NI items:
 //   out[c][t] (+)= sum_m Mat(r, m) in[c][t with coordinate r along DIR replaced by m]
 // with Mat(r, m) = mat[r][m] (TR = false) or mat[m][r] (TR = true).
+// Items t >= nitems (those of absent elements, which come last) are skipped.
 template <int n, int NI, int NC, int DIR, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void sf_pass(const T* __restrict__ mat, const T* in, T* out) {
+__device__ __forceinline__ void sf_pass(const T* __restrict__ mat, const T* in, T* out, int nitems = NI) {
   constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n);
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     const int r = (t / s) % n;
     const int base = t - r * s;
     T acc[NC];
@@ -216,9 +212,10 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 // where M is given by its even-odd coefficients `coef` (see eo_line).
 // TH is the block size; the task loop is unrolled so that independent lines interleave (not for
 // double-float, whose unrolled lines would cost an SM its second block).
+// Lines of absent elements (line index >= nlines; they come last) are skipped.
 template <int n, int NI, int NC, int DIR, bool ANTI, int FORM, int TH, int OS = 1, int OO = 0, typename T>
 __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __restrict__ in,
-                                        T* __restrict__ out) {
+                                        T* __restrict__ out, int nlines = NI / n) {
   constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n, ITER = (NC * NL + TH - 1) / TH;
   constexpr int UNROLL = std::is_same<T, df64>::value ? 1 : ITER;
   T k[kEoSlots];
@@ -229,6 +226,7 @@ __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __r
     const int task = threadIdx.x + it * TH;
     if (ITER * TH != NC * NL && task >= NC * NL) break;
     const int c = task / NL, L = task - c * NL;
+    if (L >= nlines) continue;
     const int base = DIR == 0 ? L * n
                    : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
     T x[n], y[n];
@@ -266,8 +264,8 @@ __device__ __forceinline__ void colloc_grad(const T* __restrict__ Dc, const T* v
 
 // Combined transposed collocation pass: y[c][t] = sum_d sum_m Dc[m][r_d] G[3c+d][t_d(m)].
 template <int n, int NI, typename T>
-__device__ __forceinline__ void colloc_grad_T(const T* __restrict__ Dc, const T* G, T* y) {
-  for (int t = threadIdx.x; t < NI; t += blockDim.x) {
+__device__ __forceinline__ void colloc_grad_T(const T* __restrict__ Dc, const T* G, T* y, int nitems = NI) {
+  for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     const int rx = t % n, ry = (t / n) % n, rz = (t / (n * n)) % n;
     const int bx = t - rx, by = t - ry * n, bz = t - rz * n * n;
 #pragma unroll
