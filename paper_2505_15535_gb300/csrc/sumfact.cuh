@@ -33,8 +33,8 @@ template <> struct Cfg<3, double> { static constexpr int NE = 8, THREADS = 256; 
 template <> struct Cfg<4, double> { static constexpr int NE = NHMF_Q4D_NE, THREADS = NHMF_Q4D_THREADS; };
 template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; };
 #ifndef NHMF_Q2F_NE
-#define NHMF_Q2F_NE 32
-#define NHMF_Q2F_THREADS 288
+#define NHMF_Q2F_NE 8
+#define NHMF_Q2F_THREADS 224
 #endif
 template <> struct Cfg<2, float> { static constexpr int NE = NHMF_Q2F_NE, THREADS = NHMF_Q2F_THREADS; };
 template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
