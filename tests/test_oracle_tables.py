@@ -52,3 +52,30 @@ def test_element_tables_shapes_and_symmetry(p):
     assert np.allclose(B[::-1, ::-1], B, atol=1e-14)
     assert np.allclose(D[::-1, ::-1], -D, atol=1e-12)
     assert abs(wq.sum() - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_mirror_structure_used_by_the_even_odd_passes(p):
+    """The GLL nodes and the Gauss points are symmetric about 1/2, so the interpolation B and
+    the weighted transpose B^T w are centro-symmetric (M[n-1-r][n-1-m] = M[r][m]) and the
+    collocation derivative Dc at the Gauss points is anti-centro-symmetric; for odd n the
+    middle Gauss point is the middle GLL node x = 1/2, so B's centre row is e_h and the centre
+    column of B^T w vanishes off the centre.  The GPU passes in even-odd form rely on these."""
+    n = p + 1
+    xq, wq = gauss_legendre(n)
+    nodes = gll_nodes(p)
+    B = lagrange_values(nodes, xq)          # B[q][i] = l_i(x_q)
+    Dc = lagrange_derivatives(xq, xq)       # Dc[q][m] = l^G_m'(x_q)
+    BWt = (B * wq[:, None]).T               # (B^T w)[i][q] = B[q][i] w_q
+    flip = lambda M: M[::-1, ::-1]
+    assert np.allclose(flip(B), B, atol=1e-14)
+    assert np.allclose(flip(BWt), BWt, atol=1e-14)
+    assert np.allclose(flip(Dc), -Dc, atol=1e-12)
+    assert np.allclose(Dc.sum(axis=1), 0.0, atol=1e-12)          # derivative of a constant
+    if n % 2 == 1:
+        h = n // 2
+        assert abs(xq[h] - 0.5) <= 1e-15 and abs(nodes[h] - 0.5) <= 1e-15
+        e = np.zeros(n)
+        e[h] = 1.0
+        assert np.allclose(B[h], e, atol=1e-15)
+        assert np.allclose(np.delete(BWt[:, h], h), 0.0, atol=1e-15)
