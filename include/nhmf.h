@@ -99,7 +99,8 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * order 11, 22, 33, 23, 13, 12 as the upper triangle of a 6x6 matrix (21), tau (6, Voigt),
  * F^-1 (9, row-major); layout [36][E*(p+1)^3]); 10*E*(p+1)^3 values
  * each, layout [10][E*(p+1)^3] with elements in colour-major order (the FP32 cache of p <= 2
- * is [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
+ * on meshes of N >= 64, whose colour classes hold at least 32768 elements, is
+ * [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
  * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
 nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
 
@@ -270,7 +271,7 @@ nhmf_status nhmf_linear_solve_noalloc(nhmf_ctx* ctx, int strategy, double rtol, 
  * convolutions, mma.sync for the stride-2 down convolution and the weight gradients), FP32
  * master weights trained by Adam.  It maps a
  * residual r (scaled to unit RMS) to a correction; as a preconditioner z = N(r) scaled back
- * and zeroed on constrained DoFs.  Requires p*N divisible by 4.
+ * and zeroed on constrained DoFs.  Requires p*N divisible by 4 and at most 784.
  * Parameters: a flat FP32 array, layer by layer (in, e0, d1, e1, d2, m2, u1, t1, u0, t0,
  * out), each weight tensor then its bias; conv/down weights W[out][in][3][3][3], up
  * weights U[in][out][3][3][3] (taps ordered dz, dy, dx from -1).

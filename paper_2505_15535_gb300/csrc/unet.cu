@@ -834,6 +834,9 @@ void bgrad(UNet& u, int layer, const __nv_bfloat16* P, long long nvox, cudaStrea
 // ------------------------------------------------------------------ host API pieces
 nhmf_status unet_alloc(nhmf_ctx* c, int cap) {
   if ((c->g.M - 1) % 4 != 0) return fail(c, NHMF_ERR_ARG, "unet: p*N must be divisible by 4 (two stride-2 levels)");
+  // the stride-1 tensor-core convolution stages a ring of padded planes of the finest grid in
+  // shared memory: 27 * 512 + 8 (130 + 2 (M + 2)) 16 + 16 bytes <= 227 KB
+  if (c->g.M > 785) return fail(c, NHMF_ERR_ARG, "unet: at most 785 nodes per direction (p*N <= 784)");
   if (c->unet) return fail(c, NHMF_ERR_STATE, "unet: already created");
   UNet* u = new UNet();
   c->unet = u;
