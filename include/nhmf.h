@@ -173,8 +173,9 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *                          p > 1; level operators at the linearisation point interpolated
  *                          to each level, Chebyshev smoothing on the inverse diagonal
  *                          (smoother_degree steps on [lmax/smoother_range, 1.2 lmax], lmax from
- *                          12 power iterations), transfer by interpolation and its transpose,
- *                          Jacobi-CG to 1e-10 on the coarsest level;
+ *                          12 power iterations in the V-cycle's precision), transfer by
+ *                          interpolation and its transpose, Jacobi-CG on the coarsest level
+ *                          (to 1e-6 in an FP64 V-cycle, 1e-4 in an FP32 one);
  *   NHMF_SOLVER_MIXED_GMG  the same V-cycle in FP32 (FP32 applies, smoothers, transfers)
  *                          inside FP64 flexible CG. */
 enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2,
