@@ -77,7 +77,10 @@ typedef struct {
 } nhmf_params;
 
 /* Create a context for one mesh/material on the current CUDA device.  Allocates the
- * context's own device buffers (linearisation copy, status word).  Synchronous. */
+ * context's own device buffers (linearisation copy, status word) and, on the first context
+ * of a device, resolves the device address of the static scratch array of
+ * nhmf_linear_solve_noalloc, which loads that array (6.3 MB) on the device until the process
+ * exits.  Synchronous. */
 nhmf_status nhmf_create(const nhmf_params* params, nhmf_ctx** out);
 
 /* Free the context and every device buffer it owns.  Synchronises the device. */
@@ -250,17 +253,18 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* ctx, const nhmf_solve_opts* opts, const 
  * after start-up.  The context must already exist and hold a linearisation point (and an
  * FP64 point cache for NHMF_CACHED); both of those may allocate, at set-up time.
  *   Scratch: one file-scope device array of 6.3 MB (six FP64 vectors of up to 131,072
- *   entries, reduction partials, scalars), held by every GPU that loads the library until
- *   the process exits.  Problems with more than 131,072 DoFs are rejected with
- *   NHMF_ERR_ARG and a message naming the limit.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ *   entries, reduction partials, scalars).  nhmf_create looks up its device address
+ *   (cudaGetSymbolAddress) on the first context of each device, with that device current,
+ *   which loads the array there; it stays until the process exits.  A call must run with
+ *   the context's device current (NHMF_ERR_STATE otherwise).  Problems with more than
+ *   131,072 DoFs are rejected with NHMF_ERR_ARG and a message naming the limit.
  *   Every call shares the array and it keeps the last call's contents (the call clears
  *   what must start at zero): calls that overlap on the GPU, from any context or stream,
  *   race and must be serialised by the caller.
  * Arguments: strategy NHMF_ON_THE_FLY or NHMF_CACHED; rtol > 0 relative to ||b||; max_iter
- * >= 1; b, x device FP64 arrays of 3*M^3; iters and rel_res (the true relative residual,
- * recomputed with an FP64 apply) are host outputs.  Synchronises. */
+ * >= 1; b, x distinct device FP64 arrays of 3*M^3 (x == b is NHMF_ERR_ARG); iters and
+ * rel_res (the true relative residual, recomputed with an FP64 apply) are host outputs.
+ * Synchronises. */
 nhmf_status nhmf_linear_solve_noalloc(nhmf_ctx* ctx, int strategy, double rtol, int max_iter, const double* b,
                                       double* x, long long* iters, double* rel_res, void* stream);
 

@@ -72,6 +72,7 @@ nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
   if (st == NHMF_OK) st = cuda_check(c, cudaMemset(c->status, 0, sizeof(unsigned)), "status clear");
   if (st == NHMF_OK) st = cuda_check(c, cudaMalloc(&c->ubar, sizeof(double) * 3 * c->g.M3), "ubar alloc");
   if (st == NHMF_OK) st = cuda_check(c, cudaMalloc(&c->ubar32, sizeof(float) * 3 * c->g.M3), "ubar32 alloc");
+  if (st == NHMF_OK) st = noalloc_setup(c);
   if (st != NHMF_OK) {
     nhmf_destroy(c);
     return st;

@@ -140,4 +140,8 @@ nhmf_status launch_to_fp32(const double* x, float* y, long long n, cudaStream_t 
 nhmf_status fail(nhmf_ctx* c, nhmf_status st, const std::string& msg);
 nhmf_status cuda_check(nhmf_ctx* c, cudaError_t e, const char* what);
 
+// Resolves, once per device, the device address of the allocation-free solve's static
+// scratch array (noalloc.cu); called by nhmf_create with the context's device current.
+nhmf_status noalloc_setup(nhmf_ctx* c);
+
 }  // namespace nhmf

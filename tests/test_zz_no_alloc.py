@@ -38,6 +38,37 @@ def test_noalloc_solve_matches_allocating_solve_twice():
         assert abs(rel - rel_ref) <= 1e-12
 
 
+def test_noalloc_solve_allocates_no_device_memory():
+    """Free device memory is unchanged across two calls on a context whose size no allocating
+    solve has used (the allocating solve first runs on another size, so that every kernel the
+    calls launch is already loaded), and an x that aliases b is rejected."""
+    import torch
+    nhmf = lib_or_fail()
+    warm = inp.small(inp.WORKLOADS["q2_64_clamp"], 5)
+    pw = nhmf.Problem.from_workload(warm)
+    pw.set_linearization(cuda(inp.draw_u(warm)), nhmf.NHMF_CACHE_FP64)
+    opts = nhmf.nhmf_solve_opts_default(solver=nhmf.NHMF_SOLVER_JACOBI_CG, linear_rtol=1e-8,
+                                        linear_max_iter=2000, check_every=10)
+    for strat in (nhmf.NHMF_CACHED, nhmf.NHMF_ON_THE_FLY):
+        opts.strategy = strat
+        nhmf.nhmf_linear_solve(pw.ctx, opts, cuda(inp.draw_vector(93, warm.n_dofs)), cuda(np.zeros(warm.n_dofs)))
+    w = inp.small(inp.WORKLOADS["q2_64_clamp"], 7)          # Q2 7^3: 10,125 DoFs
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(inp.draw_u(w)), nhmf.NHMF_CACHE_FP64)
+    b = cuda(inp.draw_vector(94, w.n_dofs))
+    x = cuda(np.zeros(w.n_dofs))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for strat in (nhmf.NHMF_CACHED, nhmf.NHMF_ON_THE_FLY):
+        it, rel = nhmf.nhmf_linear_solve_noalloc(prob.ctx, strat, 1e-8, 2000, b, x)
+        assert rel <= 1e-8 and it > 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, strat
+    with pytest.raises(nhmf.NhmfError) as ei:
+        nhmf.nhmf_linear_solve_noalloc(prob.ctx, nhmf.NHMF_CACHED, 1e-8, 10, b, b)
+    assert ei.value.status == 1
+
+
 def test_noalloc_rejects_problems_beyond_the_scratch_limit():
     nhmf = lib_or_fail()
     w = inp.small(inp.WORKLOADS["q2_64_clamp"], 20)         # 206,763 DoFs > 131,072
