@@ -170,6 +170,22 @@ class Operator:
         out[self.fixed[dofs]] = 0.0
         return out
 
+    def diagonal_rows(self, u, dofs) -> np.ndarray:
+        """Rows `dofs` of diag(A), touching only the elements around those DoFs."""
+        mesh = self.mesh
+        dofs = np.asarray(dofs)
+        nodes = dofs % mesh.n_nodes
+        elems = np.array(sorted({e for nd in np.unique(nodes) for e in mesh.elements_of_node(int(nd))}), dtype=np.int64)
+        conn = mesh.element_nodes(elems)
+        F = np.eye(3) + self.gradients(u, conn)
+        L = tangent_moduli(F, self.mu, self.lam, self.model)
+        de = np.einsum("eqcdcl,qal,qad,q->eca", L, self.G, self.G, self.vol) * self._f(elems, 2)
+        d = np.zeros(mesh.n_dofs)
+        self._scatter(d, conn, de)
+        out = d[dofs]
+        out[self.fixed[dofs]] = 1.0
+        return out
+
     def element_matrix(self, u, e: int) -> np.ndarray:
         """K_e[(c,a), (k,b)] = sum_q L_{c d k l} G[q,b,l] G[q,a,d] w_q h^3 (raw, no Dirichlet)."""
         conn = self.mesh.element_nodes(np.array([e]))

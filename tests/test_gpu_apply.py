@@ -154,6 +154,47 @@ def test_bitwise_determinism(nhmf):
                 assert torch.equal(o, outs[0])
 
 
+def test_bitwise_determinism_fp32_register_kernel(nhmf):
+    """Q2 64^3: the one-thread-per-element FP32 kernel and the node gather, 10 applies each."""
+    import torch
+    w = inp.WORKLOADS["q2_64_clamp"]
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(inp.draw_u(w)), nhmf.NHMF_CACHE_FP32)
+    dut = cuda(inp.draw_du(w).astype(np.float32))
+    for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+        first = torch.empty_like(dut)
+        prob.apply(dut, first, nhmf.NHMF_FP32, strat)
+        for _ in range(9):
+            v = torch.empty_like(dut)
+            prob.apply(dut, v, nhmf.NHMF_FP32, strat)
+            assert torch.equal(v, first)
+    prob.close()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_fp32_error_near_incompressibility(nhmf, p):
+    """lambda = 49 under 10 % compression (J ~ 0.9, so 2 lambda / mu ln J ~ -10): the FP32 on-the-fly
+    apply forms J - 1 and ln J in FP32 from the FP32 displacement gradient, the cached one reads
+    them computed in FP64.  Both stay within the FP32 bar; their errors are printed."""
+    n_el = 6
+    w = inp.Workload(f"c{p}", n_el, p, 1.0, 49.0, inp.BC_COMPRESSION, "scaled", 0.02, "normal", 1.0, 5100 + p, 5200 + p)
+    m = Mesh(n_el, p)
+    X = m.node_coords()
+    u = inp.draw_u(w) + np.concatenate([0.0 * X[:, 0], 0.0 * X[:, 1], -0.1 * X[:, 2]])
+    du = inp.draw_du(w)
+    ref = Operator(m, w.mu, w.lam, w.bc).apply(u, du)
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP32)
+    errs = {}
+    for name, strat in (("otf", nhmf.NHMF_ON_THE_FLY), ("cached", nhmf.NHMF_CACHED)):
+        v32 = cuda(np.zeros(u.size, dtype=np.float32))
+        prob.apply(cuda(du.astype(np.float32)), v32, nhmf.NHMF_FP32, strat)
+        errs[name] = rel_l2(host(v32), ref)
+    print(f"FP32 apply error at lambda 49, 10 % compression, Q{p}: {errs}")
+    assert max(errs.values()) <= FP32_TOL, errs
+    prob.close()
+
+
 def test_strategies_agree(nhmf):
     w, u, du = case(5, 3, 2, lam=49.0)
     prob = nhmf.Problem.from_workload(w)

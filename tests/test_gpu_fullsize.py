@@ -2,7 +2,7 @@
 each), Q3 48^3 (9,145,875) and Q4 64^3 (50,923,779), the last two near-incompressible
 (lambda 49) with the compression boundary conditions — in the launch configuration the
 benchmark times, on sampled output rows the oracle computes one by one (its
-apply_rows/residual_rows touch only the elements around each sampled DoF)."""
+apply_rows/residual_rows/diagonal_rows touch only the elements around each sampled DoF)."""
 import numpy as np
 import pytest
 
@@ -60,6 +60,8 @@ def test_fullsize_sampled_rows(name):
     d = torch.empty_like(dut)
     prob.diagonal(d)
     assert torch.isfinite(d).all()
+    dref = op.diagonal_rows(u, rows)
+    assert np.linalg.norm(host(d[idx]) - dref) <= 1e-12 * np.linalg.norm(dref)
     prob.close()
 
 

@@ -8,10 +8,17 @@ Two kinds of parity:
   then reproduce the oracle bit for bit (this pins every gather, stride and transposition);
 * rounded: He-initialised weights and normal inputs.  The GPU stores weights, activations
   and activation gradients in BF16; the oracle (quant=True) rounds at the same places in
-  FP64.  One-ulp rounding differences (2^-8) cascade through the 11 layers, so two valid
-  BF16 evaluations differ by about sqrt(11) * 2^-9 ~ 2e-3 to 3e-3 relative (each is about
-  7.5e-3 from the exact FP64 network); the bars are 1e-2 on the output and loss and 8e-2 on
-  each gradient tensor (the coarsest grids sum over 125 to 729 voxels only)."""
+  FP64, so the two differ only where FP32 and FP64 accumulation put a value on different
+  sides of a BF16 rounding boundary.  Each such flip perturbs the next layer by a fraction of
+  an ulp and flips further roundings there, so the differences cascade until every rounding
+  site is an independent +-half-ulp draw (RMS 2^-9 / sqrt(3) relative): two valid evaluations
+  then differ by about sqrt(2 k / 3) 2^-9 after k rounding stages, 5.3e-3 for the output
+  (k = 11) and 7.5e-3 for an activation gradient (k = 22).  Measured on this hardware: output
+  2.4e-3 to 2.7e-3 and loss at most 2.6e-5 relative (17^3 to 65^3); parameter gradients, sums
+  over the voxels of a level, reach 4.4e-2 on the stride-2 layers of the 5^3 and 9^3
+  coarsest grids (few terms, no averaging) and 1.9e-2 once that grid is 17^3 (65^3).  Bars:
+  5e-3 on the output, 1e-4 on the loss, 5e-2 on each gradient tensor, 2.5e-2 from 65^3 up."""
+"""
 import numpy as np
 import pytest
 
@@ -19,43 +26,18 @@ import nhmf_inputs as inp
 from oracle import unet as ounet
 from oracle.mesh import Mesh
 from tests.gpu_util import cuda, host, lib_or_fail, rel_l2
+from tests.unet_cases import exact_inputs, flat_params, he_params, rounded_inputs, ternary_params, unflat
 
 pytestmark = pytest.mark.gpu
 
-
-def flat_params(params):
-    out = []
-    for name, kind, cin, cout in ounet.LAYERS:
-        out.append(params[name + ".w"].reshape(-1))
-        out.append(params[name + ".b"].reshape(-1))
-    return np.concatenate(out)
+OUT_BAR = 5e-3      # output, relative l2
+LOSS_BAR = 1e-4     # loss, relative
 
 
-def unflat(vec):
-    out, k = {}, 0
-    for name, kind, cin, cout in ounet.LAYERS:
-        shape = ounet.weight_shape(kind, cin, cout)
-        n = int(np.prod(shape))
-        out[name + ".w"] = vec[k:k + n].reshape(shape); k += n
-        out[name + ".b"] = vec[k:k + cout]; k += cout
-    return out
-
-
-def he_params(seed=5000, bias_scale=0.05):
-    p = ounet.init_params(lambda k, n: inp.normal(seed + k, n))
-    for i, (name, _, _, cout) in enumerate(ounet.LAYERS):
-        p[name + ".b"] = bias_scale * inp.normal(seed + 100 + i, cout)
-    return p
-
-
-def ternary_params(seed=7000, density=0.006):
-    p = {}
-    for i, (name, kind, cin, cout) in enumerate(ounet.LAYERS):
-        shape = ounet.weight_shape(kind, cin, cout)
-        u = inp.uniform01(seed + i, int(np.prod(shape)))
-        p[name + ".w"] = np.where(u < density / 2, -1.0, np.where(u < density, 1.0, 0.0)).reshape(shape)
-        p[name + ".b"] = np.minimum(np.floor(inp.uniform01(seed + 50 + i, cout) * 3.0), 1.0)
-    return p
+def grad_bar(M):
+    """Bar on each parameter-gradient tensor (relative l2): coarsest grid of 9^3 or fewer
+    voxels, or of 17^3 and more (M >= 65)."""
+    return 2.5e-2 if M >= 65 else 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -78,13 +60,15 @@ def run_gpu(nhmf, n_el, p, bc, params, x, e):
     return host(y), loss, unflat(g.astype(np.float64))
 
 
-@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0)])
+# 65^3 (Q2 on 32^3 elements) runs the tensor-core convolutions as on the production grid:
+# z-columns of three tiles through the plane-slot ring and 770 column units looped over the
+# 456-block grid of the stride-1 convolution (and its weight gradient); 17^3 and 33^3 have
+# one-tile columns and one unit per block.
+@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0), (32, 2, 2)])
 def test_exact_arithmetic_bit_parity(nhmf, n_el, p, bc):
     M = p * n_el + 1
     params = ternary_params()
-    x = np.floor(inp.uniform01(123, 3 * M ** 3) * 3.0 - 1.0)
-    e = np.zeros(3 * M ** 3)
-    e[M ** 3 + (M // 2) * (1 + M + M * M)] = 4.0          # ||f e||^2 = 16: dy is dyadic
+    x, e = exact_inputs(M)
     y, loss, g = run_gpu(nhmf, n_el, p, bc, params, x, e)
     xo, eo = x.reshape(3, M, M, M), e.reshape(3, M, M, M)
     free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
@@ -97,27 +81,27 @@ def test_exact_arithmetic_bit_parity(nhmf, n_el, p, bc):
     assert sum(np.count_nonzero(go[k]) for k in go if k.endswith(".w")) > 5000
 
 
-@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0)])
+@pytest.mark.parametrize("n_el,p,bc", [(8, 2, 2), (16, 2, 1), (8, 4, 0), (32, 2, 1)])
 def test_rounded_parity(nhmf, n_el, p, bc):
     M = p * n_el + 1
     params = he_params()
-    x = inp.normal(11, 3 * M ** 3).astype(np.float32).astype(np.float64)
-    e = inp.normal(12, 3 * M ** 3).astype(np.float32).astype(np.float64)
+    x, e = rounded_inputs(M)
     y, loss, g = run_gpu(nhmf, n_el, p, bc, params, x, e)
     xo, eo = x.reshape(3, M, M, M), e.reshape(3, M, M, M)
     yo, acts = ounet.forward(params, xo, quant=True)
     assert np.mean(acts["t0"] > 0) > 0.2                    # the network is alive
-    assert rel_l2(y, yo.reshape(-1)) <= 1e-2
+    assert rel_l2(y, yo.reshape(-1)) <= OUT_BAR
     free = (~Mesh(n_el, p).constrained(bc)).astype(np.float64).reshape(3, M, M, M)
     lo = ounet.loss(yo, eo, free)
-    assert abs(loss - lo) <= 1e-2 * lo
+    assert abs(loss - lo) <= LOSS_BAR * lo
     go = ounet.backward(params, acts, yo, eo, free, quant=True)
     errs = {k: rel_l2(g[k].reshape(-1), go[k].reshape(-1)) for k in go}
-    assert max(errs.values()) <= 8e-2, errs
+    assert max(errs.values()) <= grad_bar(M), errs
 
 
-def test_adam_step_matches_oracle(nhmf):
-    n_el, p, bc = 8, 2, 2
+@pytest.mark.parametrize("n_el", [8, 32])
+def test_adam_step_matches_oracle(nhmf, n_el):
+    p, bc = 2, 2
     M = p * n_el + 1
     prob = nhmf.Problem(n_el, p, 1.0, 1.5, bc)
     nhmf.nhmf_unet_create(prob.ctx, 4)
@@ -134,7 +118,7 @@ def test_adam_step_matches_oracle(nhmf):
     eo = (e * np.sqrt(e.size) / np.linalg.norm(e)).reshape(3, M, M, M)
     fo = free.reshape(3, M, M, M).astype(float)
     yo, acts = ounet.forward(params, xo, quant=True)
-    assert abs(l0 - ounet.loss(yo, eo, fo)) <= 1e-2 * l0
+    assert abs(l0 - ounet.loss(yo, eo, fo)) <= LOSS_BAR * l0
     go = ounet.backward(params, acts, yo, eo, fo, quant=True)
     p2 = {k: v.copy() for k, v in params.items()}
     ounet.adam_step(p2, go, {}, lr=lr)

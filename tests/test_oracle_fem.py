@@ -252,3 +252,12 @@ def test_element_factors_scale_contributions():
     # a uniform factor scales the operator
     op2 = Operator(mesh, 1.0, 1.5, bc=0, factors=np.full(mesh.n_elements, 3.0))
     assert np.allclose(op2.apply(u, du), 3.0 * Operator(mesh, 1.0, 1.5, bc=0).apply(u, du), rtol=1e-13, atol=1e-13)
+
+
+def test_diagonal_rows_match_full_diagonal():
+    """The row-restricted diagonal (used at full size on sampled rows) equals rows of the full one."""
+    w = inp.small(inp.WORKLOADS["q3_48_compress"], 3)
+    u = inp.uniform_pm(77, w.n_dofs, 0.02)
+    op = Operator(Mesh(w.n_el, w.degree), w.mu, w.lam, w.bc)
+    rows = np.array([0, 5, 100, w.n_dofs // 2, w.n_dofs - 1, 2 * w.n_dofs // 3 + 7])
+    assert np.allclose(op.diagonal_rows(u, rows), op.diagonal(u)[rows], rtol=1e-14, atol=0)
