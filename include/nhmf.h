@@ -101,10 +101,12 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * value) and/or the 36-value FP64 cache of NHMF_SPATIAL (NHMF_CACHE_SPATIAL: J c in Voigt
  * order 11, 22, 33, 23, 13, 12 as the upper triangle of a 6x6 matrix (21), tau (6, Voigt),
  * F^-1 (9, row-major); layout [36][E*(p+1)^3]); 10*E*(p+1)^3 values
- * each, layout [10][E*(p+1)^3] with elements in colour-major order (the FP32 cache of p <= 2
- * on meshes of N >= 64, whose colour classes hold at least 32768 elements, is
- * [10][(p+1)^3][E] instead, for the one-thread-per-element kernel).  Synchronises and
- * returns NHMF_ERR_NONPOS_J if det F <= 0 anywhere. */
+ * each, layout [10][E*(p+1)^3] with elements in colour-major order, except the FP32 cache,
+ * whose elements are in natural order ex + N (ey + N ez) (the FP32 apply runs over all
+ * elements at once), and which for p <= 2 on meshes of N >= 64 is [10][(p+1)^3][E], for the
+ * one-thread-per-element kernel.  Also allocates the FP32 apply's element-local result buffer
+ * (3*E*(p+1)^3 floats) on first call.  Synchronises and returns NHMF_ERR_NONPOS_J if
+ * det F <= 0 anywhere. */
 nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
 
 /* v = A(u) du with u the current linearisation point.  Strategies: NHMF_ON_THE_FLY
@@ -304,8 +306,8 @@ nhmf_status nhmf_unet_train(nhmf_ctx* ctx, int epochs, double lr, double* loss_f
                             void* stream);
 
 /* Kernel timing.  While enabled, every operator call records a CUDA event pair on its
- * stream around its element kernels (the eight colour launches, not the vector memset or
- * the Dirichlet-row fix).  nhmf_profile_read() synchronises those events, returns the summed
+ * stream around its element kernels (FP64 and double-float: the eight colour launches, not the
+ * vector memset or the Dirichlet-row fix; FP32: the element-local launch and the node gather).  nhmf_profile_read() synchronises those events, returns the summed
  * elapsed milliseconds and the number of element-kernel launches recorded for one operator
  * kind (NHMF_KIND_*), and clears that kind's record. */
 enum { NHMF_KIND_APPLY = 0, NHMF_KIND_CACHE = 1, NHMF_KIND_RESIDUAL = 2, NHMF_KIND_DIAGONAL = 3 };

@@ -40,8 +40,10 @@ static void build_geometry(const nhmf_params& p, Geometry* g) {
     c.nz = (p.n_el - c.cz + 1) / 2;
     c.count = c.nx * c.ny * c.nz;
     c.slot0 = slot;
+    c.stride = 2;
     slot += c.count;
   }
+  g->all = Colour{0, 0, 0, p.n_el, p.n_el, p.n_el, (int)g->E, 0, 1};
 }
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -93,6 +95,7 @@ void nhmf_destroy(nhmf_ctx* c) {
   cudaFree(c->ubar32);
   cudaFree(c->cache64);
   cudaFree(c->cache32);
+  cudaFree(c->vloc);
   cudaFree(c->cachedf);
   cudaFree(c->cachesp);
   gmg_free(c);
@@ -150,6 +153,10 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
   if ((st = launch_to_fp32(c->ubar, c->ubar32, (long long)n, s)) != NHMF_OK)
     return fail(c, st, "ubar fp32 copy");
   const size_t cache_elems = 10 * (size_t)c->g.nq;
+  // element-local results of the FP32 apply (allocated here, before any solver captures an
+  // FP32 apply in a CUDA graph)
+  if (!c->vloc)
+    if ((st = cuda_check(c, cudaMalloc(&c->vloc, 3 * (size_t)c->g.nq * sizeof(float)), "vloc alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP64) && !c->cache64)
     if ((st = cuda_check(c, cudaMalloc(&c->cache64, cache_elems * sizeof(double)), "cache64 alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP32) && !c->cache32)

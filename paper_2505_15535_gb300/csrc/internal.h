@@ -37,12 +37,15 @@ struct Tables1D {
 };
 void build_tables(int p, Tables1D* t);
 
-// Geometry of one element colour class: elements (cx + 2 ix, cy + 2 iy, cz + 2 iz).
+// Geometry of one element colour class: elements (cx + s ix, cy + s iy, cz + s iz), s = stride:
+// 2 for the eight classes of the colour-by-colour scatter, 1 for the class of all elements
+// (natural order), which the element-local FP32 apply uses.
 struct Colour {
   int cx, cy, cz;
   int nx, ny, nz;
   int count;        // nx * ny * nz
   long long slot0;  // first colour-major element slot of this class
+  int stride;
 };
 
 struct Geometry {
@@ -52,6 +55,7 @@ struct Geometry {
   long long nq;      // quadrature points, E * n^3
   double h;
   Colour colour[8];
+  Colour all;        // every element, natural order ex + N (ey + N ez)
 };
 
 }  // namespace nhmf
@@ -87,7 +91,8 @@ struct nhmf_ctx {
   double* ubar = nullptr;     // linearisation point, FP64
   float* ubar32 = nullptr;    // its FP32 copy (FP32 on-the-fly apply)
   double* cache64 = nullptr;  // [10][nq]
-  float* cache32 = nullptr;   // [10][nq]
+  float* cache32 = nullptr;   // [10][nq], elements in natural order
+  float* vloc = nullptr;      // [3][(p+1)^3][E] element-local results of the FP32 apply
   float2* cachedf = nullptr;  // [10][nq] (hi, lo) double-float pairs
   double* cachesp = nullptr;  // [36][nq] J c (21), tau (6), F^-1 (9): Algorithm 2
   double* factor = nullptr;   // [E] per-element material factors (natural order), or null

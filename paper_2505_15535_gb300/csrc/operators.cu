@@ -95,6 +95,19 @@ __device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long 
   }
 }
 
+// Element-local results of the block's elements (launched on the class of all elements, so the
+// slot is the natural element index) into vloc[c][q][E]: consecutive threads write
+// consecutive elements of one (c, q) row.
+template <int P, int NE>
+__device__ __forceinline__ void store_local(const OpArgs& a, const float* src, long long e0, int nvalid) {
+  constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NI = NE * n3;
+  const long long E = a.nq / n3, slot = a.col.slot0 + e0;
+  for (int t = threadIdx.x; t < 3 * n3 * NE; t += blockDim.x) {
+    const int e = t % NE, cq = t / NE;
+    if (e < nvalid) a.vloc[cq * E + slot + e] = src[(cq / n3) * NI + e * n3 + cq % n3];
+  }
+}
+
 // Forward interpolation of three components to the points: in -> out (tmp is clobbered).
 template <int n, int NI, typename T>
 __device__ __forceinline__ void to_points(const T* sB, T* in, T* tmp, T* out, int nitems) {
@@ -282,6 +295,12 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   } else {
     from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI, nitems);
   }
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.vloc) {
+      store_local<P, NE>(a, G + 3 * NI, e0, nvalid);
+      return;
+    }
+  }
   scatter_add<P, NI>(a, G + 3 * NI, e0, nvalid, static_cast<typename Store<T>::type*>(a.v));
 }
 
@@ -291,8 +310,9 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 // is fully unrolled, so its coefficients are compile-time-indexed kernel parameters (constant
 // bank operands of the FMAs) and no shared memory is touched.  For p <= 2.  As in k_apply, w_q,
 // mu and h ride on the transposed tables and the material factor on du.  The on-the-fly kernel
-// runs its B and B^T passes in even-odd form at odd n; the cached kernel keeps the matrix form,
-// whose unrolled code fits its registers without spilling.
+// runs its B and B^T passes in even-odd form at odd n; the cached kernel keeps the matrix form.
+// Launched once over the class of all elements; each thread writes its element's results to
+// vloc[c][q][E] (consecutive threads, consecutive addresses) for k_gather_local.
 #ifndef NHMF_REG_THREADS
 #define NHMF_REG_THREADS 128
 #endif
@@ -305,11 +325,12 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
   if (ec >= a.col.count) return;
   const Colour& col = a.col;
   const int ix = int(ec % col.nx), iy = int((ec / col.nx) % col.ny), iz = int(ec / ((long long)col.nx * col.ny));
-  const int gi0 = P * (col.cx + 2 * ix), gj0 = P * (col.cy + 2 * iy), gk0 = P * (col.cz + 2 * iz);
+  const int gi0 = P * (col.cx + col.stride * ix), gj0 = P * (col.cy + col.stride * iy),
+            gk0 = P * (col.cz + col.stride * iz);
   const long long M = a.M;
   const long long slot = col.slot0 + ec, E = a.nq / n3;
   const float* __restrict__ du = static_cast<const float*>(a.du);
-  float* __restrict__ v = static_cast<float*>(a.v);
+  float* __restrict__ vloc = a.vloc;
   auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
   auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
 
@@ -457,11 +478,56 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+    for (int q = 0; q < n3; ++q) vloc[(c * n3 + q) * E + slot] = acc[c][q];
+}
+
+// ------------------------------------------------------------------ element-local gather
+// v[c][node] = sum of vloc[c][q][e] over the elements e whose closure holds the node (1, 2, 4
+// or 8 of them; q the node's local index in e), always in increasing (ez, ey, ex) order, so
+// the result is bitwise deterministic without atomics.  Dirichlet rows (unless raw):
+// v = du there.  One thread per node.
+template <int P>
+__global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ vloc, const float* __restrict__ du,
+                                                     float* __restrict__ v, int N, int M, int bc) {
+  constexpr int n = P + 1, n3 = n * n * n;
+  const long long M3 = (long long)M * M * M, node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= M3) return;
+  const int g[3] = {int(node % M), int((node / M) % M), int(node / ((long long)M * M))};
+  const long long E = (long long)N * N * N;
+  // per direction: the element below the node (local index P), if any, then the element at or
+  // above it (local index g % P)
+  int el[3][2], lo[3][2];
+  bool has[3][2];
 #pragma unroll
-      for (int j = 0; j < n; ++j)
+  for (int d = 0; d < 3; ++d) {
+    const bool shared = g[d] % P == 0;
+    has[d][0] = shared && g[d] > 0;
+    el[d][0] = g[d] / P - 1;
+    lo[d][0] = P;
+    has[d][1] = !shared || g[d] < M - 1;
+    el[d][1] = g[d] / P;
+    lo[d][1] = g[d] % P;
+  }
 #pragma unroll
-        for (int i = 0; i < n; ++i) v[c * a.M3 + node(i, j, k)] += acc[c][idx(i, j, k)];
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.f;
+    if (is_constrained(bc, c, g[0], g[2], M)) {
+      s = du[c * M3 + node];
+    } else {
+#pragma unroll
+      for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y)
+#pragma unroll
+          for (int x = 0; x < 2; ++x)
+            if (has[2][z] && has[1][y] && has[0][x]) {
+              const long long e = el[0][x] + (long long)N * (el[1][y] + (long long)N * el[2][z]);
+              const int q = lo[0][x] + n * (lo[1][y] + n * lo[2][z]);
+              s += vloc[(c * n3 + q) * E + e];
+            }
+    }
+    v[c * M3 + node] = s;
+  }
 }
 
 // ------------------------------------------------------------------ point cache
@@ -544,18 +610,20 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       a.cachedf_out[9 * a.nq + cbase + t] = split(lnJ);
     }
     if (a.cache32_out) {
+      // the FP32 applies run over all elements in natural order (element-local results)
+      const long long en = elem_natural(a, e0 + t / n3), q = t % n3;
       if (P <= kRegMaxP && a.reg32) {
         // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
-        // elements of a colour are contiguous
-        const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
+        // elements are contiguous
+        const long long E = a.nq / n3;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + slot] = float(Fi[k]);
-        a.cache32_out[(9 * n3 + q) * E + slot] = float(lnJ);
+        for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + en] = float(Fi[k]);
+        a.cache32_out[(9 * n3 + q) * E + en] = float(lnJ);
       } else {
-        // layout [10][E n^3] (same as FP64) for the shared-memory kernel
+        // layout [10][E n^3] for the shared-memory kernel
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a.cache32_out[k * a.nq + cbase + t] = float(Fi[k]);
-        a.cache32_out[9 * a.nq + cbase + t] = float(lnJ);
+        for (int k = 0; k < 9; ++k) a.cache32_out[k * a.nq + en * n3 + q] = float(Fi[k]);
+        a.cache32_out[9 * a.nq + en * n3 + q] = float(lnJ);
       }
     }
   }
@@ -833,6 +901,30 @@ nhmf_status run_colours(nhmf_ctx* c, KernelT kernel, OpArgs a, int NE, int threa
   return cuda_check(c, cudaGetLastError(), what);
 }
 
+// The element-local FP32 apply: `kernel` once over the class of all elements (NE per block),
+// writing c->vloc, then k_gather_local<P> onto v with the Dirichlet rows (bc of `a`).
+template <int P, typename KernelT>
+nhmf_status run_local(nhmf_ctx* c, KernelT kernel, OpArgs a, int NE, int threads, size_t smem, const float* du,
+                      float* v, cudaStream_t s) {
+  if (cudaError_t e = prepare(kernel, smem); e != cudaSuccess) return cuda_check(c, e, "apply");
+  if (!c->vloc) return fail(c, NHMF_ERR_STATE, "apply: no element-local buffer (set_linearization first)");
+  nhmf_ctx::Rec rec{NHMF_KIND_APPLY, 2, nullptr, nullptr};
+  if (c->profiling) {
+    cudaEventCreate(&rec.a);
+    cudaEventCreate(&rec.b);
+    cudaEventRecord(rec.a, s);
+  }
+  a.col = c->g.all;
+  a.vloc = c->vloc;
+  kernel<<<(unsigned)((c->g.E + NE - 1) / NE), threads, smem, s>>>(a);
+  k_gather_local<P><<<(unsigned)((c->g.M3 + 255) / 256), 256, 0, s>>>(c->vloc, du, v, c->g.N, c->g.M, a.bc);
+  if (c->profiling) {
+    cudaEventRecord(rec.b, s);
+    c->prof.push_back(rec);
+  }
+  return cuda_check(c, cudaGetLastError(), "apply");
+}
+
 template <typename T>
 nhmf_status fix_rows(nhmf_ctx* c, const T* src, T* out, int mode, T value, cudaStream_t s) {
   if (c->prm.bc == NHMF_BC_NONE) return NHMF_OK;
@@ -856,21 +948,28 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
   a.cachesp_in = c->cachesp;
   const size_t slots = kTabSlots + (STRAT == NHMF_ON_THE_FLY ? 15 : 12) * (size_t)NI;  // spatial: as cached
   const size_t smem = slots * sizeof(T);
-  if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
-    return cuda_check(c, e, "apply memset");
-  nhmf_status st;
   // the energy model is a compile-time parameter of the on-the-fly point code (a runtime
   // branch would charge the split model's registers to every model)
   constexpr int SPLIT = STRAT == NHMF_ON_THE_FLY ? NHMF_MODEL_SPLIT : NHMF_MODEL_COMPRESSIBLE;
   const bool split = STRAT == NHMF_ON_THE_FLY && c->prm.model == NHMF_MODEL_SPLIT;
-  bool reg = false;
-  if constexpr (sizeof(T) == 4 && P <= kRegMaxP) reg = c->reg32;
-  if (reg) {
-    if constexpr (sizeof(T) == 4 && P <= kRegMaxP) {
-      auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
-      st = run_colours(c, k, a, kRegThreads, kRegThreads, 0, s, "apply", NHMF_KIND_APPLY);
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: one launch over all elements with element-local results, then the node gather
+    // (which also writes the Dirichlet rows): no memset, no colour classes
+    const float* du32 = static_cast<const float*>(du);
+    float* v32 = static_cast<float*>(v);
+    if constexpr (P <= kRegMaxP) {
+      if (c->reg32) {
+        auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
+        return run_local<P>(c, k, a, kRegThreads, kRegThreads, 0, du32, v32, s);
+      }
     }
-  } else {
+    auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;
+    return run_local<P>(c, k, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, du32, v32, s);
+  }
+  if (cudaError_t e = cudaMemsetAsync(v, 0, sizeof(S) * 3 * c->g.M3, s); e != cudaSuccess)
+    return cuda_check(c, e, "apply memset");
+  nhmf_status st;
+  {
     auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;
     st = run_colours(c, k, a, NE, LaunchCfg<P, T, STRAT>::THREADS, smem, s, "apply", NHMF_KIND_APPLY);
   }

@@ -87,6 +87,7 @@ struct OpArgs {
   const double* cachesp_in;
   const double* factor;  // per-element material factor (natural element order) or null
   unsigned* status;
+  float* vloc;           // element-local FP32 results [3][n^3][E] (element-local apply) or null
 };
 
 __device__ __forceinline__ bool is_constrained(int bc, int c, int gi, int gk, int M) {
@@ -104,9 +105,17 @@ __device__ __forceinline__ void item_node(const OpArgs& a, long long e_in_colour
   const int ix = int(e_in_colour % c.nx);
   const int iy = int((e_in_colour / c.nx) % c.ny);
   const int iz = int(e_in_colour / ((long long)c.nx * c.ny));
-  gi = P * (c.cx + 2 * ix) + q % n;
-  gj = P * (c.cy + 2 * iy) + (q / n) % n;
-  gk = P * (c.cz + 2 * iz) + q / (n * n);
+  gi = P * (c.cx + c.stride * ix) + q % n;
+  gj = P * (c.cy + c.stride * iy) + (q / n) % n;
+  gk = P * (c.cz + c.stride * iz) + q / (n * n);
+}
+
+// Natural index ex + N (ey + N ez) of element e_in_colour of the launch's colour class.
+__device__ __forceinline__ long long elem_natural(const OpArgs& a, long long e_in_colour) {
+  const Colour& c = a.col;
+  const long long ix = e_in_colour % c.nx, iy = (e_in_colour / c.nx) % c.ny, iz = e_in_colour / ((long long)c.nx * c.ny);
+  const long long ex = c.cx + c.stride * ix, ey = c.cy + c.stride * iy, ez = c.cz + c.stride * iz;
+  return ex + (long long)a.N * (ey + (long long)a.N * ez);
 }
 
 // Material factor of element e_in_colour of the launch's colour class (1 if homogeneous).
@@ -114,7 +123,7 @@ __device__ __forceinline__ double elem_factor(const OpArgs& a, long long e_in_co
   if (!a.factor) return 1.0;
   const Colour& c = a.col;
   const long long ix = e_in_colour % c.nx, iy = (e_in_colour / c.nx) % c.ny, iz = e_in_colour / ((long long)c.nx * c.ny);
-  const long long ex = c.cx + 2 * ix, ey = c.cy + 2 * iy, ez = c.cz + 2 * iz;
+  const long long ex = c.cx + c.stride * ix, ey = c.cy + c.stride * iy, ez = c.cz + c.stride * iz;
   return a.factor[ex + (long long)a.N * (ey + (long long)a.N * ez)];
 }
 
