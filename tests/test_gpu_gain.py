@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 def test_learned_preconditioner_gain_is_measured():
     import torch
-    from tests.test_gpu_unet import flat_params, he_params
+    from tests.unet_cases import flat_params, he_params
     nhmf = lib_or_fail()
     n_el, p, S, comp = 16, 2, 20, 0.1
     n = 3 * (p * n_el + 1) ** 3
@@ -46,3 +46,40 @@ def test_learned_preconditioner_gain_is_measured():
         assert rel_l2(finals[name], finals["plain"]) <= 1e-6, name
         results[name]["time_vs_plain"] = results[name]["seconds"] / results["plain"]["seconds"]
     print(json.dumps({"train_loss": [l0, l1], "solvers": results}))
+
+
+def test_learned_multigrid_correction_gain_is_measured():
+    """The network as a correction on top of the FP32 multigrid V-cycle V,
+    z = V(r) + N(r - A V(r)), trained on the pairs (r_j - A V(r_j), x* - x_j - V(r_j)) that the
+    mixed multigrid solves of load steps 1-5 record; steps 6-12 then run with and without the
+    correction from the same state.  Both reach the 1e-8 Newton tolerance and the same
+    equilibrium; iterations and times are printed (the measured ratio, which may be below 1)."""
+    import torch
+    nhmf = lib_or_fail()
+    n_el, p, S, comp = 16, 2, 20, 0.1
+    n = 3 * (p * n_el + 1) ** 3
+    prob = nhmf.Problem(n_el, p, 1.0, 1.5, 2)
+    nhmf.nhmf_unet_create(prob.ctx, 200)
+    from tests.unet_cases import flat_params, he_params
+    nhmf.nhmf_unet_set_params(prob.ctx, flat_params(he_params()))
+    u = cuda(np.zeros(n))
+    prob.solve(u, load_steps=S, compression=comp, last_step=5, solver=nhmf.NHMF_SOLVER_MIXED_GMG, record_pairs=1,
+               cg_pair_every=4, linear_rtol=1e-8)
+    npairs = nhmf.nhmf_unet_num_pairs(prob.ctx)
+    assert npairs >= 10
+    l0, l1 = nhmf.nhmf_unet_train(prob.ctx, 20, 1e-3)
+    assert l1 < l0
+    results, finals = {}, {}
+    for name, solver in [("mixed_gmg", nhmf.NHMF_SOLVER_MIXED_GMG), ("mixed_gmg_learned", nhmf.NHMF_SOLVER_MIXED_GMG_LEARNED)]:
+        uu = u.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = prob.solve(uu, load_steps=S, compression=comp, first_step=6, last_step=12, linear_rtol=1e-8, solver=solver)
+        torch.cuda.synchronize()
+        results[name] = {"seconds": time.perf_counter() - t0, "outer_iters": st["total_linear_iters"],
+                         "vcycles": st["total_linear_iters"], "fallbacks": sum(st["fallbacks"])}
+        assert all(r <= 1e-8 for r in st["rel_residual"]), name
+        finals[name] = host(uu)
+    assert rel_l2(finals["mixed_gmg_learned"], finals["mixed_gmg"]) <= 1e-6
+    results["mixed_gmg_learned"]["time_vs_mixed_gmg"] = results["mixed_gmg_learned"]["seconds"] / results["mixed_gmg"]["seconds"]
+    print(json.dumps({"pairs": npairs, "train_loss": [l0, l1], "solvers": results}))

@@ -18,7 +18,6 @@ Two kinds of parity:
   over the voxels of a level, reach 4.4e-2 on the stride-2 layers of the 5^3 and 9^3
   coarsest grids (few terms, no averaging) and 1.9e-2 once that grid is 17^3 (65^3).  Bars:
   5e-3 on the output, 1e-4 on the loss, 5e-2 on each gradient tensor, 2.5e-2 from 65^3 up."""
-"""
 import numpy as np
 import pytest
 
