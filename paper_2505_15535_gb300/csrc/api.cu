@@ -155,12 +155,13 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
   const size_t cache_elems = 10 * (size_t)c->g.nq;
   // element-local results of the FP32 apply (allocated here, before any solver captures an
   // FP32 apply in a CUDA graph)
+  const size_t tiled_nq = (size_t)tiled_elems(c->g.E) * c->g.n * c->g.n * c->g.n;
   if (!c->vloc)
-    if ((st = cuda_check(c, cudaMalloc(&c->vloc, 3 * (size_t)c->g.nq * sizeof(float)), "vloc alloc")) != NHMF_OK) return st;
+    if ((st = cuda_check(c, cudaMalloc(&c->vloc, 3 * tiled_nq * sizeof(float)), "vloc alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP64) && !c->cache64)
     if ((st = cuda_check(c, cudaMalloc(&c->cache64, cache_elems * sizeof(double)), "cache64 alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_FP32) && !c->cache32)
-    if ((st = cuda_check(c, cudaMalloc(&c->cache32, cache_elems * sizeof(float)), "cache32 alloc")) != NHMF_OK) return st;
+    if ((st = cuda_check(c, cudaMalloc(&c->cache32, 10 * tiled_nq * sizeof(float)), "cache32 alloc")) != NHMF_OK) return st;
   if ((mask & NHMF_CACHE_SPATIAL) && !c->cachesp)
     if ((st = cuda_check(c, cudaMalloc(&c->cachesp, 36 * (size_t)c->g.nq * sizeof(double)), "cachesp alloc")) != NHMF_OK)
       return st;

@@ -24,6 +24,13 @@ constexpr int kMaxN = 5;  // p + 1 for p <= 4
 constexpr int kRegMaxP = NHMF_REG_MAXP;
 constexpr long long kRegMinColour = NHMF_REG_MIN_COLOUR;
 
+// Element tiles of the FP32 apply's arrays: per-element data of 32 consecutive elements (in
+// natural order) are stored value-row by value-row, [E / kTile][values][kTile], so that a
+// warp of one-thread-per-element code reads and writes whole 128-byte rows and every warp's
+// data is one contiguous block (DRAM pages and TLB entries stay few).
+constexpr int kTile = 32;
+inline long long tiled_elems(long long E) { return (E + kTile - 1) / kTile * kTile; }
+
 // 1D tables of the Q_p element on [0, 1] (Section 2.2, 2.4), FP64.
 //   B[q][i]  = l_i(x_q): GLL Lagrange basis at the Gauss points
 //   Dc[q][r] = derivative of the Lagrange basis on the Gauss points, at Gauss point q
@@ -91,8 +98,8 @@ struct nhmf_ctx {
   double* ubar = nullptr;     // linearisation point, FP64
   float* ubar32 = nullptr;    // its FP32 copy (FP32 on-the-fly apply)
   double* cache64 = nullptr;  // [10][nq]
-  float* cache32 = nullptr;   // [10][nq], elements in natural order
-  float* vloc = nullptr;      // [3][(p+1)^3][E] element-local results of the FP32 apply
+  float* cache32 = nullptr;   // FP32 point cache, elements in natural order (see kTile)
+  float* vloc = nullptr;      // element-local results of the FP32 apply, [E/32][3][(p+1)^3][32]
   float2* cachedf = nullptr;  // [10][nq] (hi, lo) double-float pairs
   double* cachesp = nullptr;  // [36][nq] J c (21), tau (6), F^-1 (9): Algorithm 2
   double* factor = nullptr;   // [E] per-element material factors (natural order), or null

@@ -96,15 +96,19 @@ __device__ __forceinline__ void scatter_add(const OpArgs& a, const T* src, long 
 }
 
 // Element-local results of the block's elements (launched on the class of all elements, so the
-// slot is the natural element index) into vloc[c][q][E]: consecutive threads write
-// consecutive elements of one (c, q) row.
+// slot is the natural element index) into the element tiles of vloc, [E/32][3][n^3][32]:
+// consecutive threads write consecutive elements of one (c, q) row.
 template <int P, int NE>
 __device__ __forceinline__ void store_local(const OpArgs& a, const float* src, long long e0, int nvalid) {
   constexpr int n3 = (P + 1) * (P + 1) * (P + 1), NI = NE * n3;
-  const long long E = a.nq / n3, slot = a.col.slot0 + e0;
+  const long long slot = a.col.slot0 + e0;
+  const unsigned long long keep_pol = l2_evict_last();
   for (int t = threadIdx.x; t < 3 * n3 * NE; t += blockDim.x) {
     const int e = t % NE, cq = t / NE;
-    if (e < nvalid) a.vloc[cq * E + slot + e] = src[(cq / n3) * NI + e * n3 + cq % n3];
+    const long long el = slot + e;
+    if (e < nvalid)
+      st_policy(a.vloc + ((el / kTile) * 3 * n3 + cq) * kTile + el % kTile, src[(cq / n3) * NI + e * n3 + cq % n3],
+                keep_pol);
   }
 }
 
@@ -263,10 +267,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
           for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
           lnJ = T(cache[9 * a.nq + cbase + t]);
         } else {
-          const long long E = a.nq / n3, slot = a.col.slot0 + e0 + t / n3, q = t % n3;
+          const long long slot = a.col.slot0 + e0 + t / n3, q = t % n3;
+          const auto* tile = cache + (slot / kTile) * (10 * n3 * kTile) + slot % kTile;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = T(cache[(k * n3 + q) * E + slot]);
-          lnJ = T(cache[(9 * n3 + q) * E + slot]);
+          for (int k = 0; k < 9; ++k) Fi[k] = T(tile[(k * n3 + q) * kTile]);
+          lnJ = T(tile[(9 * n3 + q) * kTile]);
         }
       } else {
 #pragma unroll
@@ -312,14 +317,18 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
 // mu and h ride on the transposed tables and the material factor on du.  The on-the-fly kernel
 // runs its B and B^T passes in even-odd form at odd n; the cached kernel keeps the matrix form.
 // Launched once over the class of all elements; each thread writes its element's results to
-// vloc[c][q][E] (consecutive threads, consecutive addresses) for k_gather_local.
+// its column of the element tile of vloc (a warp writes whole 128-byte rows) for
+// k_gather_local, and reads the point cache from the same tiling.
 #ifndef NHMF_REG_THREADS
 #define NHMF_REG_THREADS 128
+#endif
+#ifndef NHMF_REG_MINB
+#define NHMF_REG_MINB 1
 #endif
 constexpr int kRegThreads = NHMF_REG_THREADS;  // threads (= elements) per block
 
 template <int P, int STRAT, int MODEL>
-__global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
+__global__ void __launch_bounds__(kRegThreads, NHMF_REG_MINB) k_apply_reg(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n;
   const long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (ec >= a.col.count) return;
@@ -328,9 +337,13 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
   const int gi0 = P * (col.cx + col.stride * ix), gj0 = P * (col.cy + col.stride * iy),
             gk0 = P * (col.cz + col.stride * iz);
   const long long M = a.M;
-  const long long slot = col.slot0 + ec, E = a.nq / n3;
+  const long long slot = col.slot0 + ec;
   const float* __restrict__ du = static_cast<const float*>(a.du);
-  float* __restrict__ vloc = a.vloc;
+  // this element's column of its tile in the point cache and in vloc
+  float* __restrict__ vloc = a.vloc + (slot / kTile) * (3 * n3 * kTile) + slot % kTile;
+  const float* __restrict__ cache =
+      static_cast<const float*>(a.cache) + (slot / kTile) * (10 * n3 * kTile) + slot % kTile;
+  const unsigned long long stream_pol = l2_evict_first();  // the point cache is read once
   auto node = [&](int i, int j, int k) { return (gi0 + i) + M * ((gj0 + j) + M * (long long)(gk0 + k)); };
   auto idx = [](int i, int j, int k) { return i + n * (j + n * k); };
 
@@ -428,10 +441,9 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
 #pragma unroll
     for (int q = 0; q < n3; ++q) acc[c][q] = 0.f;
   const float r2 = float(a.r2mu), inv_mu = float(1.0 / a.mu);
-  const float* __restrict__ cache = static_cast<const float*>(a.cache);
   bool bad = false;
 #pragma unroll
-  for (int qz = 0; qz < n; ++qz)
+  for (int qz = 0; qz < n; ++qz) {
 #pragma unroll
     for (int qy = 0; qy < n; ++qy)
 #pragma unroll
@@ -447,8 +459,8 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
           for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0 ? 1.f : 0.f) + H[k];
         } else {
 #pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = __ldg(cache + (k * n3 + q) * E + slot);
-          lnJ = __ldg(cache + (9 * n3 + q) * E + slot);
+          for (int k = 0; k < 9; ++k) Fi[k] = ld_policy(cache + (k * n3 + q) * kTile, stream_pol);
+          lnJ = ld_policy(cache + (9 * n3 + q) * kTile, stream_pol);
         }
         float dH[9], g[9];
         grad_at(a.Dcf, qv, qx, qy, qz, dH);
@@ -467,6 +479,7 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
             acc[c][idx(qx, qy, m)] = fmaf(a.DcWf[qz * n + m], g[3 * c + 2], acc[c][idx(qx, qy, m)]);
           }
       }
+  }
   if (bad) atomicOr(a.status, kStatusNonPosJ);
   // transposed weighted interpolation back to the nodes: out[i] = sum_q B[q][i] w_q acc[q]
 #pragma unroll
@@ -475,14 +488,15 @@ __global__ void __launch_bounds__(kRegThreads) k_apply_reg(const OpArgs a) {
     pass(acc[c], 1, a.eof[2], a.BWf, true);
     pass(acc[c], 2, a.eof[2], a.BWf, true);
   }
+  const unsigned long long keep_pol = l2_evict_last();  // read back by the gather that follows
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int q = 0; q < n3; ++q) vloc[(c * n3 + q) * E + slot] = acc[c][q];
+    for (int q = 0; q < n3; ++q) st_policy(vloc + (c * n3 + q) * kTile, acc[c][q], keep_pol);
 }
 
 // ------------------------------------------------------------------ element-local gather
-// v[c][node] = sum of vloc[c][q][e] over the elements e whose closure holds the node (1, 2, 4
+// v[c][node] = sum of vloc(e; c, q) over the elements e whose closure holds the node (1, 2, 4
 // or 8 of them; q the node's local index in e), always in increasing (ez, ey, ex) order, so
 // the result is bitwise deterministic without atomics.  Dirichlet rows (unless raw):
 // v = du there.  One thread per node.
@@ -493,39 +507,46 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
   const long long M3 = (long long)M * M * M, node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (node >= M3) return;
   const int g[3] = {int(node % M), int((node / M) % M), int(node / ((long long)M * M))};
-  const long long E = (long long)N * N * N;
+  const unsigned long long done_pol = l2_evict_first();  // each element-local value is read once
   // per direction: the element below the node (local index P), if any, then the element at or
-  // above it (local index g % P)
+  // above it (local index g % P); absent elements get a clamped (valid) index and are masked
+  // after the load, so that all 24 loads are independent and in flight together
   int el[3][2], lo[3][2];
   bool has[3][2];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const bool shared = g[d] % P == 0;
     has[d][0] = shared && g[d] > 0;
-    el[d][0] = g[d] / P - 1;
+    el[d][0] = max(g[d] / P - 1, 0);
     lo[d][0] = P;
     has[d][1] = !shared || g[d] < M - 1;
-    el[d][1] = g[d] / P;
+    el[d][1] = min(g[d] / P, N - 1);
     lo[d][1] = g[d] % P;
   }
+  float val[3][8];
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const long long e = el[0][x] + (long long)N * (el[1][y] + (long long)N * el[2][z]);
+        const int q = lo[0][x] + n * (lo[1][y] + n * lo[2][z]);
+        const float* src = vloc + ((e / kTile) * 3 * n3 + q) * kTile + e % kTile;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) val[c][4 * z + 2 * y + x] = ld_policy(src + c * n3 * kTile, done_pol);
+      }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float s = 0.f;
-    if (is_constrained(bc, c, g[0], g[2], M)) {
-      s = du[c * M3 + node];
-    } else {
 #pragma unroll
-      for (int z = 0; z < 2; ++z)
+    for (int z = 0; z < 2; ++z)
 #pragma unroll
-        for (int y = 0; y < 2; ++y)
+      for (int y = 0; y < 2; ++y)
 #pragma unroll
-          for (int x = 0; x < 2; ++x)
-            if (has[2][z] && has[1][y] && has[0][x]) {
-              const long long e = el[0][x] + (long long)N * (el[1][y] + (long long)N * el[2][z]);
-              const int q = lo[0][x] + n * (lo[1][y] + n * lo[2][z]);
-              s += vloc[(c * n3 + q) * E + e];
-            }
-    }
+        for (int x = 0; x < 2; ++x)
+          if (has[2][z] && has[1][y] && has[0][x]) s += val[c][4 * z + 2 * y + x];
+    if (is_constrained(bc, c, g[0], g[2], M)) s = du[c * M3 + node];
     v[c * M3 + node] = s;
   }
 }
@@ -613,12 +634,11 @@ __global__ void __launch_bounds__(Cfg<P, double>::THREADS) k_cache(const OpArgs 
       // the FP32 applies run over all elements in natural order (element-local results)
       const long long en = elem_natural(a, e0 + t / n3), q = t % n3;
       if (P <= kRegMaxP && a.reg32) {
-        // layout [10][n^3][E] for the register kernel (one thread per element): consecutive
-        // elements are contiguous
-        const long long E = a.nq / n3;
+        // element tiles [E/32][10][n^3][32] for the register kernel (one thread per element)
+        float* tile = a.cache32_out + (en / kTile) * (10 * n3 * kTile) + en % kTile;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a.cache32_out[(k * n3 + q) * E + en] = float(Fi[k]);
-        a.cache32_out[(9 * n3 + q) * E + en] = float(lnJ);
+        for (int k = 0; k < 9; ++k) tile[(k * n3 + q) * kTile] = float(Fi[k]);
+        tile[(9 * n3 + q) * kTile] = float(lnJ);
       } else {
         // layout [10][E n^3] for the shared-memory kernel
 #pragma unroll

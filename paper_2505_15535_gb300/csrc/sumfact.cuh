@@ -90,6 +90,39 @@ struct OpArgs {
   float* vloc;           // element-local FP32 results [3][n^3][E] (element-local apply) or null
 };
 
+// ------------------------------------------------------------------ memory helpers (PTX)
+// L2 eviction-priority policies (createpolicy) and loads/stores that carry them: the FP32
+// apply streams its point cache with evict_first and writes its element-local results with
+// evict_last, so that the results are still in L2 when the node gather reads them.
+#ifndef NHMF_L2HINT
+#define NHMF_L2HINT 1
+#endif
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float ld_policy(const float* a, unsigned long long pol) {
+#if NHMF_L2HINT
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ void st_policy(float* a, float v, unsigned long long pol) {
+#if NHMF_L2HINT
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+#else
+  *a = v;
+#endif
+}
 __device__ __forceinline__ bool is_constrained(int bc, int c, int gi, int gk, int M) {
   if (bc == NHMF_BC_CLAMP_X0) return gi == 0;
   if (bc == NHMF_BC_COMPRESSION) return gk == 0 || (c == 2 && gk == M - 1);
