@@ -531,7 +531,13 @@ def run_newton(args):
     last = min(S, args.last_step) if args.last_step else S
     prob = nhmf.Problem(w.n_el, w.degree, w.mu, w.lam, w.bc)
     solvers = [s.strip() for s in args.solvers.split(",") if s.strip()]
-    learned = any(s in ("learned", "mixed_learned") for s in solvers)
+    LEARNED = ("learned", "mixed_learned", "mixed_gmg_learned")
+    learned = any(s in LEARNED for s in solvers)
+    # the learned correction of the multigrid solver trains on pairs recorded by mixed_gmg
+    # solves; the other learned solvers on pairs recorded by the plain solver
+    base_solver = "mixed_gmg" if "mixed_gmg_learned" in solvers else "plain"
+    if learned and base_solver not in solvers:
+        raise SystemExit(f"--solvers must include {base_solver} (it records the training pairs)")
     if learned:
         nhmf.nhmf_unet_create(prob.ctx, args.pairs)
         nhmf.nhmf_unet_set_params(prob.ctx, he_init_flat())
@@ -539,7 +545,8 @@ def run_newton(args):
                 newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter)
     ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
            "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED,
-           "gmg": nhmf.NHMF_SOLVER_GMG, "mixed_gmg": nhmf.NHMF_SOLVER_MIXED_GMG}
+           "gmg": nhmf.NHMF_SOLVER_GMG, "mixed_gmg": nhmf.NHMF_SOLVER_MIXED_GMG,
+           "mixed_gmg_learned": nhmf.NHMF_SOLVER_MIXED_GMG_LEARNED}
     du_err = torch.from_numpy(inp.draw_vector(77, w.n_dofs)).to(dev)
 
     def fp32_error(uu):
@@ -562,14 +569,17 @@ def run_newton(args):
         u = torch.zeros(w.n_dofs, dtype=torch.float64, device=dev)
         per = []
         first = 1
-        if name in ("learned", "mixed_learned"):
-            # start from the plain solver's state after the training steps
+        if name in LEARNED:
+            # start from the recording solver's state after the training steps
             first = args.train_steps + 1
-            u = states["plain"][args.train_steps - 1].clone()
+            u = states[base_solver][args.train_steps - 1].clone()
         for step in range(first, last + 1):
             kw = dict(base, first_step=step, last_step=step, solver=ids[name])
-            if name == "plain" and learned and step <= args.train_steps:
-                kw.update(record_pairs=1, cg_pair_every=8, synthetic_pairs=args.synthetic)
+            if name == base_solver and learned and step <= args.train_steps:
+                if base_solver == "plain":
+                    kw.update(record_pairs=1, cg_pair_every=8, synthetic_pairs=args.synthetic)
+                else:
+                    kw.update(record_pairs=1, cg_pair_every=args.gmg_pair_iters)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = prob.solve(u, **kw)
@@ -579,7 +589,7 @@ def run_newton(args):
             rec = {"step": step, "seconds": dt, "newton": st["newton_iters"][0], "outer": st["linear_iters"][0],
                    "inner": st["inner_iters"][0], "fallbacks": st["fallbacks"][0], "rel_residual": st["rel_residual"][0]}
             per.append(rec)
-            if name == "plain" and learned and step == args.train_steps:
+            if name == base_solver and learned and step == args.train_steps:
                 t0 = time.perf_counter()
                 l0, l1 = nhmf.nhmf_unet_train(prob.ctx, args.epochs, 1e-3)
                 torch.cuda.synchronize()
@@ -588,28 +598,31 @@ def run_newton(args):
         out["solvers"][name] = {"steps": per, "seconds": sum(r["seconds"] for r in per),
                                 "outer": sum(r["outer"] for r in per), "inner": sum(r["inner"] for r in per),
                                 "newton": sum(r["newton"] for r in per), "fallbacks": sum(r["fallbacks"] for r in per)}
-    # per-step agreement with plain and oracle checks on sampled rows
-    if "plain" in states:
-        plain = states["plain"]
+    # per-step agreement with the reference solver's states (plain if it ran, else the first)
+    ref_solver = "plain" if "plain" in states else (solvers[0] if solvers else None)
+    if ref_solver in states:
+        refs = states[ref_solver]
         for name, lst in states.items():
-            off = args.train_steps if name in ("learned", "mixed_learned") else 0
+            off = args.train_steps if name in LEARNED else 0
             for k, uu in enumerate(lst):
                 rec = out["solvers"][name]["steps"][k]
-                ref = plain[k + off]
-                rec["rel_diff_vs_plain"] = float(torch.linalg.norm(uu - ref) / torch.linalg.norm(ref))
+                ref = refs[k + off]
+                rec[f"rel_diff_vs_{ref_solver}"] = float(torch.linalg.norm(uu - ref) / torch.linalg.norm(ref))
     # FP32 apply error vs the FP64 apply at each converged state of the first solver
     first_solver = solvers[0] if solvers else None
     if first_solver in states:
         for k, uu in enumerate(states[first_solver]):
             out["solvers"][first_solver]["steps"][k]["fp32_apply_rel_err_vs_fp64"] = fp32_error(uu)
     sp = out["solvers"]
-    if "plain" in sp:
+    for ref_name in ("plain", "mixed_gmg"):
+        if ref_name not in sp:
+            continue
         for name in sp:
-            if name in ("plain",):
+            if name == ref_name:
                 continue
-            off = args.train_steps if name in ("learned", "mixed_learned") else 0
-            t_plain = sum(r["seconds"] for r in sp["plain"]["steps"][off:])
-            sp[name]["speedup_vs_plain_same_steps"] = t_plain / sp[name]["seconds"] if sp[name]["seconds"] else None
+            off = args.train_steps if name in LEARNED else 0
+            t_ref = sum(r["seconds"] for r in sp[ref_name]["steps"][off:])
+            sp[name][f"speedup_vs_{ref_name}_same_steps"] = t_ref / sp[name]["seconds"] if sp[name]["seconds"] else None
     print(json.dumps(out), flush=True)
     prob.close()
     return 0
@@ -707,6 +720,8 @@ def main():
     ap.add_argument("--synthetic", type=int, default=8)
     ap.add_argument("--pairs", type=int, default=150)
     ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--gmg-pair-iters", type=int, default=4,
+                    help="newton mode: pairs per linear solve recorded by mixed_gmg for mixed_gmg_learned")
     ap.add_argument("--linear-rtol", type=float, default=1e-8)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--inner-max-iter", type=int, default=1000)

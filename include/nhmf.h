@@ -103,8 +103,8 @@ const char* nhmf_last_error(const nhmf_ctx* ctx);
  * F^-1 (9, row-major); layout [36][E*(p+1)^3]); 10*E*(p+1)^3 values
  * each, layout [10][E*(p+1)^3] with elements in colour-major order, except the FP32 cache,
  * whose elements are in natural order ex + N (ey + N ez) (the FP32 apply runs over all
- * elements at once), and which for p <= 2 on meshes of N >= 64 is [10][(p+1)^3][E], for the
- * one-thread-per-element kernel.  Also allocates the FP32 apply's element-local result buffer
+ * elements at once), and which for p <= 2 on meshes of N >= 64 is tiled by 32 elements,
+ * [E/32][10][(p+1)^3][32], for the one-thread-per-element kernel.  Also allocates the FP32 apply's element-local result buffer
  * (3*E*(p+1)^3 floats) on first call.  Synchronises and returns NHMF_ERR_NONPOS_J if
  * det F <= 0 anywhere. */
 nhmf_status nhmf_set_linearization(nhmf_ctx* ctx, const double* u, int cache_mask, void* stream);
@@ -182,9 +182,17 @@ nhmf_status nhmf_check_status(nhmf_ctx* ctx, void* stream);
  *                          interpolation and its transpose, Jacobi-CG on the coarsest level
  *                          (to 1e-6 in an FP64 V-cycle, 1e-4 in an FP32 one);
  *   NHMF_SOLVER_MIXED_GMG  the same V-cycle in FP32 (FP32 applies, smoothers, transfers)
- *                          inside FP64 flexible CG. */
+ *                          inside FP64 flexible CG;
+ *   NHMF_SOLVER_MIXED_GMG_LEARNED the FP32 V-cycle V plus the trained U-Net N on the residual
+ *                          the V-cycle leaves, z = V(r) + omega c with c = N(t), t = r - A V(r),
+ *                          and the A-optimal step omega = (c.t) / (c.A c) (A by FP32 applies),
+ *                          inside FP64 flexible CG; the network is trained on pairs
+ *                          recorded by MIXED_GMG solves (record_pairs); falls back to
+ *                          Jacobi-CG from the current iterate on stagnation as the learned
+ *                          solvers do. */
 enum { NHMF_SOLVER_JACOBI_CG = 0, NHMF_SOLVER_MIXED_FCG = 1, NHMF_SOLVER_LEARNED_FCG = 2,
-       NHMF_SOLVER_MIXED_LEARNED = 3, NHMF_SOLVER_GMG = 4, NHMF_SOLVER_MIXED_GMG = 5 };
+       NHMF_SOLVER_MIXED_LEARNED = 3, NHMF_SOLVER_GMG = 4, NHMF_SOLVER_MIXED_GMG = 5,
+       NHMF_SOLVER_MIXED_GMG_LEARNED = 6 };
 #define NHMF_MAX_STEPS 64
 
 typedef struct {
@@ -202,10 +210,13 @@ typedef struct {
   double inner_rtol;    /* mixed: FP32 inner CG relative tolerance, default 1e-3 */
   int inner_max_iter;   /* mixed: FP32 inner CG iteration cap, default 1000 */
   int check_every;      /* iterations between host convergence reads, default 10 */
-  int record_pairs;     /* JACOBI_CG with a U-Net: store training pairs (Newton (b, du) and CG
-                           (r_j, x* - x_j)) in the network's pair store, default 0 */
-  int cg_pair_every;    /* CG pairs at iterations j = k, 4k, 16k (k = this), default 8 */
-  int learned_stall_window;     /* LEARNED_FCG: fall back to Jacobi-CG when the residual */
+  int record_pairs;     /* with a U-Net, store training pairs in the network's pair store
+                           (default 0): JACOBI_CG, Newton (b, du) and CG (r_j, x* - x_j);
+                           MIXED_GMG, the pairs of MIXED_GMG_LEARNED's correction,
+                           (r_j - A V(r_j), x* - x_j - V(r_j)), at the first k FCG iterations
+                           of each linear solve (k = cg_pair_every) */
+  int cg_pair_every;    /* JACOBI_CG: pairs at iterations j = k, 4k, 16k (k = this), default 8 */
+  int learned_stall_window;     /* learned solvers: fall back to Jacobi-CG when the residual */
   double learned_stall_factor;  /* drops by less than this factor over this many iterations
                                    (defaults 10 and 0.9), or after linear_max_iter/4 iterations */
   int synthetic_pairs;  /* with record_pairs: per Newton iterate, also store this many pairs

@@ -118,6 +118,13 @@ __global__ void k_ratio(const double* num, const double* den, double sign, doubl
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = sign * (*num / *den);
 }
 
+__global__ void k_ratio_or_zero(const double* num, const double* den, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double r = *num / *den;
+    *out = (*den > 0.0 && isfinite(r)) ? r : 0.0;
+  }
+}
+
 template <typename TI, typename TO>
 __global__ void k_scale_convert(long long n, const TI* x, const double* scale, bool invert, TO* y) {
   double s = scale ? *scale : 1.0;
@@ -194,6 +201,9 @@ void axpby(long long n, double a, const double* pa, const double* x, double b, c
 }
 void ratio(const double* num, const double* den, double sign, double* out, cudaStream_t s) {
   k_ratio<<<1, 32, 0, s>>>(num, den, sign, out);
+}
+void ratio_or_zero(const double* num, const double* den, double* out, cudaStream_t s) {
+  k_ratio_or_zero<<<1, 32, 0, s>>>(num, den, out);
 }
 void to_fp32_scaled(long long n, const double* x, const double* scale, bool invert, float* y, cudaStream_t s) {
   k_scale_convert<double, float><<<kEwBlocks, kEwThreads, 0, s>>>(n, x, scale, invert, y);

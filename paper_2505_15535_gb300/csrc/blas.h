@@ -21,6 +21,8 @@ template <typename T>
 void jacobi(long long n, const T* r, const T* dinv, T* z, double* rz, double* rr, double* partials, cudaStream_t s);
 void axpby(long long n, double a, const double* pa, const double* x, double b, const double* pb, double* y, cudaStream_t s);
 void ratio(const double* num, const double* den, double sign, double* out, cudaStream_t s);
+// out = num / den if den > 0 and the quotient is finite, else 0 (a guarded step length)
+void ratio_or_zero(const double* num, const double* den, double* out, cudaStream_t s);
 void to_fp32_scaled(long long n, const double* x, const double* scale, bool invert, float* y, cudaStream_t s);
 void to_fp64_scaled(long long n, const float* x, const double* scale, double* y, cudaStream_t s);
 // x *= dinv (element-wise)

@@ -40,7 +40,8 @@ __global__ void k_bc(int bc, int M, long long M3, double top_uz, double* u, doub
   }
 }
 
-enum Slot { RZ0 = 0, RZ1 = 1, PQ = 2, RR = 3, BN = 4, ALPHA = 5, BETA = 6, ZQ = 7, PR = 8, PQPREV = 9,
+enum Slot { CT = 24, CAC = 25, OMEGA = 26, CNORM = 27,  // the learned correction's step length
+            RZ0 = 0, RZ1 = 1, PQ = 2, RR = 3, BN = 4, ALPHA = 5, BETA = 6, ZQ = 7, PR = 8, PQPREV = 9,
             RNORM = 10, TMP = 11, IN_RZ0 = 16, IN_RZ1 = 17, IN_PQ = 18, IN_RR = 19, IN_BN = 20 };
 
 struct Ctx {
@@ -477,8 +478,36 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     auto precond = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
     return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
   }
-  if (o.solver == NHMF_SOLVER_GMG || o.solver == NHMF_SOLVER_MIXED_GMG) {
-    const bool f32 = o.solver == NHMF_SOLVER_MIXED_GMG;
+  // fall back to Jacobi-CG on the remaining residual w.r of a stalled flexible solve:
+  // A d = r, sol += d
+  auto fallback_cg = [&]() -> nhmf_status {
+    *fallbacks += 1;
+    double bnh, rnh;
+    nhmf_status st = norm(x, b, TMP, &bnh);
+    if (st != NHMF_OK) return st;
+    if ((st = norm(x, w.r, TMP, &rnh)) != NHMF_OK) return st;
+    cudaMemcpyAsync(w.b2, w.r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+    long long it2 = 0;
+    double rel2 = 0.0;
+    const double rtol2 = rnh > 0.0 ? std::min(1.0, o.linear_rtol * bnh / rnh) : 1.0;
+    st = pcg<double>(x, o.strategy, w.b2, w.x2, w.dinv, w.r, w.z, w.p, w.q, rtol2, o.linear_max_iter,
+                     o.check_every, RZ0, &it2, &rel2);
+    if (st != NHMF_OK) return st;
+    axpby(x.n, 1.0, nullptr, w.x2, 1.0, nullptr, sol, x.s);
+    *outer += it2;
+    *relres = rel2 * rnh / bnh;
+    return cuda_check(x.c, cudaGetLastError(), "fallback");
+  };
+  if (o.solver == NHMF_SOLVER_GMG || o.solver == NHMF_SOLVER_MIXED_GMG || o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED) {
+    const bool f32 = o.solver != NHMF_SOLVER_GMG;
+    const bool learned = o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED;
+    UNet* un = x.c->unet;
+    if (learned && !un) return fail(x.c, NHMF_ERR_STATE, "learned correction: no network in this context");
+    // training pairs of the learned correction, recorded by MIXED_GMG solves (see below)
+    const bool record = o.solver == NHMF_SOLVER_MIXED_GMG && o.record_pairs && un;
+    const long long rec_iters = o.cg_pair_every > 0 ? o.cg_pair_every : 8;
+    std::vector<int> slots;
+    long long jprec = 0;
     nhmf_status st = gmg_prepare(x.c, o.strategy, f32, x.s, false, w.diag);
     if (st == NHMF_ERR_NONPOS_J) st = gmg_prepare(x.c, o.strategy, f32, x.s, true, w.diag);  // folded coarse state
     if (st != NHMF_OK) return st;
@@ -503,6 +532,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     }
     GmgLevel& top = x.c->gmg->L.back();
     const int ltop = (int)x.c->gmg->L.size() - 1;
+    const int strat32 = o.strategy == NHMF_SPATIAL ? NHMF_ON_THE_FLY : o.strategy;
     auto precond = [&](const double* r, double* z) -> nhmf_status {
       if (!f32) return vcycle<double>(x.c, ltop, o, r, z, x.s, inner);
       norm2(x.n, r, w.sc + TMP, w.partials, x.s);
@@ -510,9 +540,47 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
       nhmf_status s2 = vcycle<float>(x.c, ltop, o, top.b32, top.x32, x.s, inner);
       if (s2 != NHMF_OK) return s2;
       to_fp64_scaled(x.n, top.x32, w.sc + TMP, z, x.s);
+      const bool rec_now = record && un->npairs < un->cap && jprec < rec_iters;
+      ++jprec;
+      if (learned || rec_now) {
+        // residual the V-cycle leaves, t = r - A z, from an FP32 apply to its FP32 output
+        if ((s2 = launch_apply(x.c, NHMF_FP32, strat32, top.x32, top.r32, x.s)) != NHMF_OK) return s2;
+        to_fp64_scaled(x.n, top.r32, w.sc + TMP, w.t, x.s);
+        axpby(x.n, 1.0, nullptr, r, -1.0, nullptr, w.t, x.s);
+        if (rec_now) {
+          // pair (t, x* - (x_j + z)): the error left after the V-cycle, A (x* - x_j - z) = t
+          cudaMemcpyAsync(w.x2, sol, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
+          axpby(x.n, 1.0, nullptr, z, 1.0, nullptr, w.x2, x.s);
+          const int slot = unet_snapshot_begin(x.c, w.t, w.x2, x.s);
+          if (slot >= 0) slots.push_back(slot);
+        }
+        if (learned) {
+          // c = N(t) has the direction of the remaining error but no meaningful scale (the
+          // training pairs are normalised): z += omega c with the A-optimal step
+          // omega = (c . t) / (c . A c), A c from an FP32 apply
+          unet_precondition(x.c, w.t, w.x2, x.s);
+          norm2(x.n, w.x2, w.sc + CNORM, w.partials, x.s);
+          to_fp32_scaled(x.n, w.x2, w.sc + CNORM, true, top.b32, x.s);
+          if ((s2 = launch_apply(x.c, NHMF_FP32, strat32, top.b32, top.r32, x.s)) != NHMF_OK) return s2;
+          to_fp64_scaled(x.n, top.r32, w.sc + CNORM, w.b2, x.s);
+          dot(x.n, w.x2, w.t, w.sc + CT, w.partials, x.s);
+          dot(x.n, w.x2, w.b2, w.sc + CAC, w.partials, x.s);
+          ratio_or_zero(w.sc + CT, w.sc + CAC, w.sc + OMEGA, x.s);
+          axpby(x.n, 1.0, w.sc + OMEGA, w.x2, 1.0, nullptr, z, x.s);
+        }
+      }
       return cuda_check(x.c, cudaGetLastError(), "mixed gmg");
     };
+    if (learned) {
+      st = fcg(x, o.strategy, b, sol, o.linear_rtol, std::max(1, o.linear_max_iter / 4), precond, outer, relres,
+               o.learned_stall_window, o.learned_stall_factor);
+      return st == NHMF_ERR_NOT_CONVERGED ? fallback_cg() : st;
+    }
     st = fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+    if (st == NHMF_OK && !slots.empty()) {
+      for (int slot : slots) unet_snapshot_finish(x.c, slot, sol, x.s);
+      return cuda_check(x.c, cudaGetLastError(), "pair recording");
+    }
     if (st != NHMF_ERR_BREAKDOWN) return st;
     // a breakdown left: solve with Jacobi-CG from scratch (the reference solver of the method)
     *fallbacks += 1;
@@ -535,22 +603,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
             : mpcg2(x, o.strategy, b, sol, o.linear_rtol, cap, inner_cg, network, outer, relres,
                     o.learned_stall_window, o.learned_stall_factor);
     if (st != NHMF_ERR_NOT_CONVERGED) return st;
-    // fall back to Jacobi-CG on the remaining residual: A d = r, sol += d
-    *fallbacks += 1;
-    double bnh, rnh;
-    if ((st = norm(x, b, TMP, &bnh)) != NHMF_OK) return st;
-    if ((st = norm(x, w.r, TMP, &rnh)) != NHMF_OK) return st;
-    cudaMemcpyAsync(w.b2, w.r, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
-    long long it2 = 0;
-    double rel2 = 0.0;
-    const double rtol2 = rnh > 0.0 ? std::min(1.0, o.linear_rtol * bnh / rnh) : 1.0;
-    st = pcg<double>(x, o.strategy, w.b2, w.x2, w.dinv, w.r, w.z, w.p, w.q, rtol2, o.linear_max_iter,
-                     o.check_every, RZ0, &it2, &rel2);
-    if (st != NHMF_OK) return st;
-    axpby(x.n, 1.0, nullptr, w.x2, 1.0, nullptr, sol, x.s);
-    *outer += it2;
-    *relres = rel2 * rnh / bnh;
-    return cuda_check(x.c, cudaGetLastError(), "fallback");
+    return fallback_cg();
   }
   return fail(x.c, NHMF_ERR_ARG, "unknown solver");
 }
@@ -559,13 +612,13 @@ int cache_mask(const nhmf_solve_opts& o) {
   if (o.strategy == NHMF_SPATIAL) return NHMF_CACHE_SPATIAL;
   if (o.strategy != NHMF_CACHED) return 0;
   return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED ||
-          o.solver == NHMF_SOLVER_MIXED_GMG)
+          o.solver == NHMF_SOLVER_MIXED_GMG || o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED)
              ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
              : NHMF_CACHE_FP64;
 }
 
 nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
-  if (!o || o->solver < 0 || o->solver > 5 ||
+  if (!o || o->solver < 0 || o->solver > NHMF_SOLVER_MIXED_GMG_LEARNED ||
       (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED && o->strategy != NHMF_SPATIAL) ||
       o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
       o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)

@@ -35,7 +35,7 @@ class nhmf_params(ctypes.Structure):
 
 
 NHMF_SOLVER_JACOBI_CG, NHMF_SOLVER_MIXED_FCG, NHMF_SOLVER_LEARNED_FCG, NHMF_SOLVER_MIXED_LEARNED = 0, 1, 2, 3
-NHMF_SOLVER_GMG, NHMF_SOLVER_MIXED_GMG = 4, 5
+NHMF_SOLVER_GMG, NHMF_SOLVER_MIXED_GMG, NHMF_SOLVER_MIXED_GMG_LEARNED = 4, 5, 6
 NHMF_MAX_STEPS = 64
 
 
