@@ -325,6 +325,13 @@ enum { NHMF_KIND_APPLY = 0, NHMF_KIND_CACHE = 1, NHMF_KIND_RESIDUAL = 2, NHMF_KI
 nhmf_status nhmf_profile_enable(nhmf_ctx* ctx, int enable);
 nhmf_status nhmf_profile_read(nhmf_ctx* ctx, int kind, double* elapsed_ms, long long* launches);
 
+/* Measured FMA throughput of the current device in TFLOP/s (FMA = 2 FLOP) for precision
+ * NHMF_FP64 or NHMF_FP32: the ALU roofline denominator of the apply kernels (not an operation
+ * of the paper).  Independent FMA chains in every thread of 8 blocks of 256 threads per SM,
+ * best of three timed launches after one warm-up (CUDA events).  Allocates and frees a few
+ * bytes; synchronises the device. */
+nhmf_status nhmf_measure_fma_peak(int precision, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,7 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_double), _P]),
     "nhmf_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]),
+    "nhmf_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -209,6 +210,15 @@ def nhmf_profile_read(ctx, kind):
     n = ctypes.c_longlong()
     _check(ctx, lib().nhmf_profile_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def nhmf_measure_fma_peak(precision):
+    """Measured FMA throughput of the current device in TFLOP/s (NHMF_FP64 or NHMF_FP32)."""
+    out = ctypes.c_double()
+    st = lib().nhmf_measure_fma_peak(precision, ctypes.byref(out))
+    if st != NHMF_OK:
+        raise NhmfError(st, "measure_fma_peak")
+    return out.value
 
 
 def nhmf_solve_opts_default(**overrides):

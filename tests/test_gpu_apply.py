@@ -235,3 +235,32 @@ def test_call_order_and_argument_errors(nhmf):
         nhmf.nhmf_create(0, 2, 1.0, 1.5, 0)
     with pytest.raises(nhmf.NhmfError):
         nhmf.nhmf_create(4, 5, 1.0, 1.5, 0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_fp32_register_kernel_at_64_all_rows(nhmf, p):
+    """N = 64: the FP32 applies run the one-thread-per-element kernel over 32-element tiles and
+    the node gather; every row against the oracle (Q1), or the rows on and around the tile
+    faces, the corners and the Dirichlet planes (Q2), both strategies, all three presets."""
+    n_el = 64
+    for bc in (0, 1, 2):
+        w, u, du = case(n_el, p, bc, seed=7)
+        m = Mesh(n_el, p)
+        op = Operator(m, w.mu, w.lam, bc)
+        if p == 1:
+            rows = np.arange(w.n_dofs)
+            ref = op.apply(u, du)
+        else:
+            M = w.n_nodes_1d
+            pick = [0, 1, 2, 3, 4, 63, 64, 65, 127, 128, M - 1]     # node planes at tile faces and edges
+            nodes = [i + M * (j + M * k) for i in pick for j in pick[:6] + [M - 1] for k in (0, 3, 4, 5, M - 1)]
+            rows = np.array(sorted({c * M ** 3 + nd for nd in nodes for c in range(3)}))
+            ref = op.apply_rows(u, du, rows)
+        prob = nhmf.Problem.from_workload(w)
+        prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP32)
+        for strat in (nhmf.NHMF_ON_THE_FLY, nhmf.NHMF_CACHED):
+            v32 = cuda(np.zeros(u.size, dtype=np.float32))
+            prob.apply(cuda(du.astype(np.float32)), v32, nhmf.NHMF_FP32, strat)
+            got = host(v32)[rows]
+            assert rel_l2(got, ref) <= FP32_TOL, (p, bc, strat, rel_l2(got, ref))
+        prob.close()
