@@ -263,9 +263,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
           const float2 z = cdf[9 * a.nq + cbase + t];
           lnJ = T(z.x, z.y);
         } else if (sizeof(typename Store<T>::type) == 8 || P > kRegMaxP || !a.reg32) {
+          // the cache is read once per apply: evict it first, keep du and v in L2
+          const unsigned long long pol = l2_evict_first();
 #pragma unroll
-          for (int k = 0; k < 9; ++k) Fi[k] = T(cache[k * a.nq + cbase + t]);
-          lnJ = T(cache[9 * a.nq + cbase + t]);
+          for (int k = 0; k < 9; ++k) Fi[k] = T(ld_policy(cache + k * a.nq + cbase + t, pol));
+          lnJ = T(ld_policy(cache + 9 * a.nq + cbase + t, pol));
         } else {
           const long long slot = a.col.slot0 + e0 + t / n3, q = t % n3;
           const auto* tile = cache + (slot / kTile) * (10 * n3 * kTile) + slot % kTile;
@@ -435,6 +437,23 @@ __global__ void __launch_bounds__(kRegThreads, NHMF_REG_MINB) k_apply_reg(const 
           for (int i = 0; i < n; ++i) ub[c][idx(i, j, k)] = a.u32[c * a.M3 + node(i, j, k)];
     to_points(ub);
   }
+  // Compressible model on the fly: the values of ubar at the points go to shared memory
+  // ([3 n^3][T], one column per thread), and the kinematics (F^-1, J - 1, ln J) of each
+  // qz-slice are computed in a rolled loop into a slice buffer ([10][n^2][T]) that the unrolled
+  // point code then reads: the kinematics code exists once instead of n^3 times, which keeps
+  // the unrolled kernel within the instruction cache, and ubar holds no registers there.
+  constexpr bool KIN = STRAT == NHMF_ON_THE_FLY && MODEL == NHMF_MODEL_COMPRESSIBLE;
+  constexpr int n2 = n * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* ubs = reinterpret_cast<float*>(smem_raw);
+  float* kin = ubs + 3 * n3 * blockDim.x;
+  const int T = blockDim.x;
+  if constexpr (KIN) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < n3; ++q) ubs[(c * n3 + q) * T + threadIdx.x] = ub[c][q];
+  }
   float acc[3][n3];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -444,13 +463,45 @@ __global__ void __launch_bounds__(kRegThreads, NHMF_REG_MINB) k_apply_reg(const 
   bool bad = false;
 #pragma unroll
   for (int qz = 0; qz < n; ++qz) {
+    if constexpr (KIN) {
+#pragma unroll 1
+      for (int pt = 0; pt < n2; ++pt) {
+        const int qx = pt % n, qy = pt / n;
+        const float* u0 = ubs + threadIdx.x;
+        float H[9], Fi[9], lnJ;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            gx = fmaf(a.Dchf[qx * n + m], u0[(c * n3 + idx(m, qy, qz)) * T], gx);
+            gy = fmaf(a.Dchf[qy * n + m], u0[(c * n3 + idx(qx, m, qz)) * T], gy);
+            gz = fmaf(a.Dchf[qz * n + m], u0[(c * n3 + idx(qx, qy, m)) * T], gz);
+          }
+          H[3 * c + 0] = gx;
+          H[3 * c + 1] = gy;
+          H[3 * c + 2] = gz;
+        }
+        const float Jm1 = kinematics(H, Fi, lnJ);
+        bad |= !(Jm1 > -1.f);
+        float* k0 = kin + pt * T + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) k0[k * n2 * T] = Fi[k];
+        k0[9 * n2 * T] = lnJ;
+      }
+    }
 #pragma unroll
     for (int qy = 0; qy < n; ++qy)
 #pragma unroll
       for (int qx = 0; qx < n; ++qx) {
         const int q = idx(qx, qy, qz);
         float Fi[9], lnJ, Jm1 = 0.f, F[9];
-        if constexpr (STRAT == NHMF_ON_THE_FLY) {
+        if constexpr (KIN) {
+          const float* k0 = kin + (qx + n * qy) * T + threadIdx.x;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Fi[k] = k0[k * n2 * T];
+          lnJ = k0[9 * n2 * T];
+        } else if constexpr (STRAT == NHMF_ON_THE_FLY) {
           float H[9];
           grad_at(a.Dchf, ub, qx, qy, qz, H);  // physical gradient: Dch = Dc / h
           Jm1 = kinematics(H, Fi, lnJ);
@@ -504,9 +555,14 @@ template <int P>
 __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ vloc, const float* __restrict__ du,
                                                      float* __restrict__ v, int N, int M, int bc) {
   constexpr int n = P + 1, n3 = n * n * n;
-  const long long M3 = (long long)M * M * M, node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (node >= M3) return;
-  const int g[3] = {int(node % M), int((node / M) % M), int(node / ((long long)M * M))};
+  static_assert(kTile == 32, "tile index by shift and mask");
+  // grid: x covers the M^2 nodes of one z-plane, y the plane (32-bit index arithmetic; the
+  // launcher keeps the element count below 2^31)
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= M * M) return;
+  const int gj = ij / M;
+  const int g[3] = {ij - gj * M, gj, (int)blockIdx.y};
+  const long long node = ij + (long long)M * M * blockIdx.y, M3 = (long long)M * M * M;
   const unsigned long long done_pol = l2_evict_first();  // each element-local value is read once
   // per direction: the element below the node (local index P), if any, then the element at or
   // above it (local index g % P); absent elements get a clamped (valid) index and are masked
@@ -515,13 +571,14 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
   bool has[3][2];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const bool shared = g[d] % P == 0;
+    const int gp = g[d] / P, gr = g[d] - gp * P;
+    const bool shared = gr == 0;
     has[d][0] = shared && g[d] > 0;
-    el[d][0] = max(g[d] / P - 1, 0);
+    el[d][0] = max(gp - 1, 0);
     lo[d][0] = P;
     has[d][1] = !shared || g[d] < M - 1;
-    el[d][1] = min(g[d] / P, N - 1);
-    lo[d][1] = g[d] % P;
+    el[d][1] = min(gp, N - 1);
+    lo[d][1] = gr;
   }
   float val[3][8];
 #pragma unroll
@@ -530,9 +587,9 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
     for (int y = 0; y < 2; ++y)
 #pragma unroll
       for (int x = 0; x < 2; ++x) {
-        const long long e = el[0][x] + (long long)N * (el[1][y] + (long long)N * el[2][z]);
+        const unsigned e = (unsigned)el[0][x] + (unsigned)N * ((unsigned)el[1][y] + (unsigned)N * (unsigned)el[2][z]);
         const int q = lo[0][x] + n * (lo[1][y] + n * lo[2][z]);
-        const float* src = vloc + ((e / kTile) * 3 * n3 + q) * kTile + e % kTile;
+        const float* src = vloc + (size_t)(e >> 5) * (3 * n3 * kTile) + q * kTile + (e & 31u);
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c][4 * z + 2 * y + x] = ld_policy(src + c * n3 * kTile, done_pol);
       }
@@ -928,6 +985,8 @@ nhmf_status run_local(nhmf_ctx* c, KernelT kernel, OpArgs a, int NE, int threads
                       float* v, cudaStream_t s) {
   if (cudaError_t e = prepare(kernel, smem); e != cudaSuccess) return cuda_check(c, e, "apply");
   if (!c->vloc) return fail(c, NHMF_ERR_STATE, "apply: no element-local buffer (set_linearization first)");
+  if (c->g.E > 0x7fffffffLL || (long long)c->g.M * c->g.M > 0x7fffffffLL)
+    return fail(c, NHMF_ERR_ARG, "apply: the FP32 element-local path needs fewer than 2^31 elements");
   nhmf_ctx::Rec rec{NHMF_KIND_APPLY, 2, nullptr, nullptr};
   if (c->profiling) {
     cudaEventCreate(&rec.a);
@@ -937,7 +996,8 @@ nhmf_status run_local(nhmf_ctx* c, KernelT kernel, OpArgs a, int NE, int threads
   a.col = c->g.all;
   a.vloc = c->vloc;
   kernel<<<(unsigned)((c->g.E + NE - 1) / NE), threads, smem, s>>>(a);
-  k_gather_local<P><<<(unsigned)((c->g.M3 + 255) / 256), 256, 0, s>>>(c->vloc, du, v, c->g.N, c->g.M, a.bc);
+  const dim3 gather_grid((unsigned)(((long long)c->g.M * c->g.M + 255) / 256), (unsigned)c->g.M);
+  k_gather_local<P><<<gather_grid, 256, 0, s>>>(c->vloc, du, v, c->g.N, c->g.M, a.bc);
   if (c->profiling) {
     cudaEventRecord(rec.b, s);
     c->prof.push_back(rec);
@@ -979,8 +1039,13 @@ nhmf_status apply_p(nhmf_ctx* c, const void* du, void* v, bool raw, cudaStream_t
     float* v32 = static_cast<float*>(v);
     if constexpr (P <= kRegMaxP) {
       if (c->reg32) {
-        auto* k = split ? k_apply_reg<P, STRAT, SPLIT> : k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>;
-        return run_local<P>(c, k, a, kRegThreads, kRegThreads, 0, du32, v32, s);
+        // the compressible on-the-fly kernel's point values and slice kinematics (see k_apply_reg)
+        constexpr size_t n3 = (P + 1) * (P + 1) * (P + 1), n2 = (P + 1) * (P + 1);
+        const size_t kin_smem = (3 * n3 + 10 * n2) * kRegThreads * sizeof(float);
+        if (split)
+          return run_local<P>(c, k_apply_reg<P, STRAT, SPLIT>, a, kRegThreads, kRegThreads, 0, du32, v32, s);
+        return run_local<P>(c, k_apply_reg<P, STRAT, NHMF_MODEL_COMPRESSIBLE>, a, kRegThreads, kRegThreads,
+                            STRAT == NHMF_ON_THE_FLY ? kin_smem : 0, du32, v32, s);
       }
     }
     auto* k = split ? k_apply<P, T, STRAT, SPLIT> : k_apply<P, T, STRAT, NHMF_MODEL_COMPRESSIBLE>;

@@ -91,9 +91,10 @@ struct OpArgs {
 };
 
 // ------------------------------------------------------------------ memory helpers (PTX)
-// L2 eviction-priority policies (createpolicy) and loads/stores that carry them: the FP32
-// apply streams its point cache with evict_first and writes its element-local results with
-// evict_last, so that the results are still in L2 when the node gather reads them.
+// L2 eviction-priority policies (createpolicy) and loads/stores that carry them: the applies
+// stream their point caches with evict_first, so that the vectors they reuse stay in L2 (the
+// FP64 colour launches re-read du and v eight times), and the FP32 apply writes its
+// element-local results with evict_last, so that they are still in L2 when the gather reads them.
 #ifndef NHMF_L2HINT
 #define NHMF_L2HINT 1
 #endif
@@ -111,6 +112,15 @@ __device__ __forceinline__ float ld_policy(const float* a, unsigned long long po
 #if NHMF_L2HINT
   float v;
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ double ld_policy(const double* a, unsigned long long pol) {
+#if NHMF_L2HINT
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
   return v;
 #else
   return __ldg(a);
