@@ -437,17 +437,20 @@ def run_gpu(args):
         wn = inp.WORKLOADS["q2_64_compress"]
         pn = nhmf.Problem.from_workload(wn)
         newton = {"workload": f"q2_64_compress: {describe(wn)}; load steps 1-2 of {wn.load_steps}"}
-        for sname, sid in (("plain_fp64_jacobi_cg", nhmf.NHMF_SOLVER_JACOBI_CG),
-                           ("mixed_fp32_gmg", nhmf.NHMF_SOLVER_MIXED_GMG)):
+        for sname, sid, outer in (("plain_fp64_jacobi_cg", nhmf.NHMF_SOLVER_JACOBI_CG, nhmf.NHMF_FP64),
+                                  ("mixed_fp32_gmg", nhmf.NHMF_SOLVER_MIXED_GMG, nhmf.NHMF_FP64),
+                                  ("mixed_fp32_gmg_df64_outer", nhmf.NHMF_SOLVER_MIXED_GMG, nhmf.NHMF_DF64)):
             un = torch.zeros(wn.n_dofs, dtype=torch.float64, device=dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = pn.solve(un, solver=sid, load_steps=wn.load_steps, compression=wn.compression, last_step=2,
-                          linear_rtol=1e-8)
+                          linear_rtol=1e-8, outer_apply=outer)
             torch.cuda.synchronize()
             newton[sname] = {"seconds": time.perf_counter() - t0, "newton_iters": sum(st["newton_iters"]),
                              "outer_iters": st["total_linear_iters"], "rel_residual": max(st["rel_residual"])}
         newton["speedup"] = newton["plain_fp64_jacobi_cg"]["seconds"] / newton["mixed_fp32_gmg"]["seconds"]
+        newton["speedup_df64_outer"] = (newton["plain_fp64_jacobi_cg"]["seconds"] /
+                                        newton["mixed_fp32_gmg_df64_outer"]["seconds"])
         pn.close()
 
     # ---- CPU oracle (rank 0, N = 1): whole-workload applies on all host cores, ~cpu_seconds
@@ -559,6 +562,7 @@ def run_newton(args):
         nhmf.nhmf_unet_set_params(prob.ctx, he_init_flat())
     base = dict(compression=w.compression, load_steps=S, linear_rtol=args.linear_rtol,
                 newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter)
+    outer = {"fp64": nhmf.NHMF_FP64, "df64": nhmf.NHMF_DF64}[args.outer]
     ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
            "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED,
            "gmg": nhmf.NHMF_SOLVER_GMG, "mixed_gmg": nhmf.NHMF_SOLVER_MIXED_GMG,
@@ -579,7 +583,8 @@ def run_newton(args):
         return out
 
     out = {"metric": NEWTON_METRIC, "mode": "newton", "workload": f"{w.name}: " + describe(w) +
-           f"; {S} load steps of {w.compression / S:g}", "steps_run": last, "solvers": {}}
+           f"; {S} load steps of {w.compression / S:g}", "steps_run": last, "solvers": {},
+           "outer_apply": args.outer + " (flexible solvers; plain Jacobi-CG always FP64)"}
     states = {}
     for name in solvers:
         u = torch.zeros(w.n_dofs, dtype=torch.float64, device=dev)
@@ -590,7 +595,8 @@ def run_newton(args):
             first = args.train_steps + 1
             u = states[base_solver][args.train_steps - 1].clone()
         for step in range(first, last + 1):
-            kw = dict(base, first_step=step, last_step=step, solver=ids[name])
+            kw = dict(base, first_step=step, last_step=step, solver=ids[name],
+                      outer_apply=nhmf.NHMF_FP64 if name == "plain" else outer)
             if name == base_solver and learned and step <= args.train_steps:
                 if base_solver == "plain":
                     kw.update(record_pairs=1, cg_pair_every=8, synthetic_pairs=args.synthetic)
@@ -736,6 +742,8 @@ def main():
     ap.add_argument("--synthetic", type=int, default=8)
     ap.add_argument("--pairs", type=int, default=150)
     ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--outer", choices=["fp64", "df64"], default="fp64",
+                    help="newton mode: arithmetic of the flexible solvers' outer applies")
     ap.add_argument("--gmg-pair-iters", type=int, default=4,
                     help="newton mode: pairs per linear solve recorded by mixed_gmg for mixed_gmg_learned")
     ap.add_argument("--linear-rtol", type=float, default=1e-8)

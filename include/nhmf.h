@@ -225,6 +225,12 @@ typedef struct {
   unsigned long long seed;      /* counter-based generator seed of those fields, default 1 */
   int smoother_degree;          /* GMG: Chebyshev steps per pre-/post-smoothing, default 3 */
   double smoother_range;        /* GMG: lmax / lmin of the Chebyshev interval, default 15 */
+  int outer_apply;              /* arithmetic of the FP64 outer applies of the flexible solvers
+                                   (every solver but JACOBI_CG): NHMF_FP64 (default) or NHMF_DF64,
+                                   the FP64-accurate double-float apply on the FP32 pipe (cached
+                                   strategy only; its point cache is built at each Newton
+                                   linearisation).  Residuals, right-hand sides and the reported
+                                   true residual stay native FP64. */
 } nhmf_solve_opts;
 
 typedef struct {

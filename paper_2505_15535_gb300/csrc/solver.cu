@@ -49,6 +49,7 @@ struct Ctx {
   cudaStream_t s;
   long long n;
   SolverWork& w;
+  int outer = NHMF_FP64;  // arithmetic of the flexible solvers' outer applies (FP64 or DF64)
 };
 
 }  // namespace
@@ -245,7 +246,7 @@ nhmf_status fcg(Ctx& x, int strat, const double* b, double* sol, double rtol, in
       ratio(sc + ZQ, sc + PQPREV, -1.0, sc + BETA, x.s);
       axpby(x.n, 1.0, nullptr, w.z, 1.0, sc + BETA, w.p, x.s);
     }
-    if ((st = launch_apply(c, NHMF_FP64, strat, w.p, q, x.s)) != NHMF_OK) return st;
+    if ((st = launch_apply(c, x.outer, strat, w.p, q, x.s)) != NHMF_OK) return st;
     dot(x.n, w.p, q, sc + PQ, w.partials, x.s);
     dot(x.n, w.p, w.r, sc + PR, w.partials, x.s);
     ratio(sc + PR, sc + PQ, 1.0, sc + ALPHA, x.s);
@@ -332,8 +333,8 @@ nhmf_status mpcg2(Ctx& x, int strat, const double* b, double* sol, double rtol, 
   for (; k < maxit;) {
     if ((st = m1(w.r, z1)) != NHMF_OK) return st;
     if ((st = m2(w.r, z2)) != NHMF_OK) return st;
-    if ((st = launch_apply(c, NHMF_FP64, strat, z1, a1, x.s)) != NHMF_OK) return st;
-    if ((st = launch_apply(c, NHMF_FP64, strat, z2, a2, x.s)) != NHMF_OK) return st;
+    if ((st = launch_apply(c, x.outer, strat, z1, a1, x.s)) != NHMF_OK) return st;
+    if ((st = launch_apply(c, x.outer, strat, z2, a2, x.s)) != NHMF_OK) return st;
     if (have_prev) {
       // beta = G_prev^-1 [q1.z1 q1.z2; q2.z1 q2.z2]
       double C[4] = {0, 0, 0, 0};
@@ -454,6 +455,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
                    long long* inner, double* relres, int* fallbacks) {
   SolverWork& w = x.w;
   *inner = 0;
+  x.outer = o.outer_apply == NHMF_DF64 ? NHMF_DF64 : NHMF_FP64;  // the flexible solvers' outer applies
   if (o.solver == NHMF_SOLVER_JACOBI_CG) {
     UNet* u = x.c->unet;
     if (!(o.record_pairs && u && u->npairs < u->cap))
@@ -611,17 +613,20 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
 int cache_mask(const nhmf_solve_opts& o) {
   if (o.strategy == NHMF_SPATIAL) return NHMF_CACHE_SPATIAL;
   if (o.strategy != NHMF_CACHED) return 0;
-  return (o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED ||
-          o.solver == NHMF_SOLVER_MIXED_GMG || o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED)
-             ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
-             : NHMF_CACHE_FP64;
+  const int df = o.outer_apply == NHMF_DF64 && o.solver != NHMF_SOLVER_JACOBI_CG ? NHMF_CACHE_DF64 : 0;
+  return ((o.solver == NHMF_SOLVER_MIXED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED ||
+           o.solver == NHMF_SOLVER_MIXED_GMG || o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED)
+              ? (NHMF_CACHE_FP64 | NHMF_CACHE_FP32)
+              : NHMF_CACHE_FP64) | df;
 }
 
 nhmf_status check_opts(nhmf_ctx* c, const nhmf_solve_opts* o) {
   if (!o || o->solver < 0 || o->solver > NHMF_SOLVER_MIXED_GMG_LEARNED ||
       (o->strategy != NHMF_ON_THE_FLY && o->strategy != NHMF_CACHED && o->strategy != NHMF_SPATIAL) ||
       o->load_steps < 1 || o->newton_max_iter < 1 || o->linear_max_iter < 1 || o->check_every < 1 ||
-      o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0)
+      o->inner_max_iter < 1 || !(o->linear_rtol > 0) || !(o->newton_rtol > 0) || o->max_backtracks < 0 ||
+      (o->outer_apply != NHMF_FP64 && o->outer_apply != NHMF_DF64) ||
+      (o->outer_apply == NHMF_DF64 && o->strategy != NHMF_CACHED))
     return fail(c, NHMF_ERR_ARG, "solve: bad options");
   return NHMF_OK;
 }
@@ -674,6 +679,7 @@ void nhmf_solve_opts_default(nhmf_solve_opts* o) {
   o->seed = 1;
   o->smoother_degree = 3;
   o->smoother_range = 15.0;
+  o->outer_apply = NHMF_FP64;
 }
 
 nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const double* b, double* xsol, long long* iters,
@@ -685,7 +691,8 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "linear_solve: no linearisation point set");
   if (o->strategy == NHMF_SPATIAL && !c->cachesp)
     return fail(c, NHMF_ERR_STATE, "linear_solve: the spatial strategy needs the NHMF_CACHE_SPATIAL cache");
-  if (o->strategy == NHMF_CACHED && (!c->cache64 || ((cache_mask(*o) & NHMF_CACHE_FP32) && !c->cache32)))
+  if (o->strategy == NHMF_CACHED && (!c->cache64 || ((cache_mask(*o) & NHMF_CACHE_FP32) && !c->cache32) ||
+                                     ((cache_mask(*o) & NHMF_CACHE_DF64) && !c->cachedf)))
     return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
   if ((st = ensure_work(c)) != NHMF_OK) return st;
   Ctx x{c, c->work->stream, 3 * c->g.M3, *c->work};

@@ -49,7 +49,8 @@ class nhmf_solve_opts(ctypes.Structure):
                 ("record_pairs", ctypes.c_int), ("cg_pair_every", ctypes.c_int),
                 ("learned_stall_window", ctypes.c_int), ("learned_stall_factor", ctypes.c_double),
                 ("synthetic_pairs", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-                ("smoother_degree", ctypes.c_int), ("smoother_range", ctypes.c_double)]
+                ("smoother_degree", ctypes.c_int), ("smoother_range", ctypes.c_double),
+                ("outer_apply", ctypes.c_int)]
 
 
 class nhmf_solve_stats(ctypes.Structure):

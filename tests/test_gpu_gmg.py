@@ -52,3 +52,34 @@ def test_gmg_newton_matches_oracle(nhmf):
         st = prob.solve(u, solver=solver, load_steps=S, compression=comp, linear_rtol=1e-10)
         assert all(r <= 1e-8 for r in st["rel_residual"])
         assert rel_l2(host(u), u_ref) <= 1e-7
+
+
+def test_double_float_outer_applies(nhmf):
+    """outer_apply = NHMF_DF64: the flexible solvers' outer Krylov applies in FP64-accurate
+    double-float arithmetic.  The linear solve meets the same true FP64 residual (checked with
+    the oracle), and Newton with mixed multigrid matches the oracle's Newton like the FP64 outer
+    applies do."""
+    w = inp.Workload("d", 8, 2, 1.0, 1.5, 2, "scaled", 0.01, "normal", 1.0, 6301, 6302)
+    u = inp.draw_u(w)
+    b = inp.draw_vector(81, w.n_dofs)
+    b[inp.dirichlet_mask(8, 2, 2).reshape(-1)] = 0.0
+    prob = nhmf.Problem.from_workload(w)
+    prob.set_linearization(cuda(u), nhmf.NHMF_CACHE_FP64 | nhmf.NHMF_CACHE_FP32 | nhmf.NHMF_CACHE_DF64)
+    op = Operator(Mesh(8, 2), 1.0, 1.5, 2)
+    for solver in (nhmf.NHMF_SOLVER_MIXED_FCG, nhmf.NHMF_SOLVER_MIXED_GMG):
+        x = cuda(np.zeros_like(u))
+        it, _, rel = prob.linear_solve(cuda(b), x, solver=solver, linear_rtol=1e-10, outer_apply=nhmf.NHMF_DF64)
+        assert rel <= 1e-10, (solver, rel)
+        assert np.linalg.norm(b - op.apply(u, host(x))) / np.linalg.norm(b) <= 2e-10
+    n_el, p, S, comp = 4, 2, 2, 0.08
+    op = Operator(Mesh(n_el, p), 1.0, 1.5, bc=2)
+    u_ref, _ = newton_load_steps(op, steps=S, compression=comp)
+    prob = nhmf.Problem(n_el, p, 1.0, 1.5, 2)
+    uu = cuda(np.zeros(op.mesh.n_dofs))
+    st = prob.solve(uu, solver=nhmf.NHMF_SOLVER_MIXED_GMG, load_steps=S, compression=comp, linear_rtol=1e-10,
+                    outer_apply=nhmf.NHMF_DF64)
+    assert all(r <= 1e-8 for r in st["rel_residual"])
+    assert rel_l2(host(uu), u_ref) <= 1e-7
+    with pytest.raises(nhmf.NhmfError):
+        prob.solve(uu, solver=nhmf.NHMF_SOLVER_MIXED_GMG, strategy=nhmf.NHMF_ON_THE_FLY, load_steps=S,
+                   compression=comp, outer_apply=nhmf.NHMF_DF64)
