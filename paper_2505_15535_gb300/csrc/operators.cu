@@ -1,11 +1,15 @@
 // Matrix-free operators of compressible neo-Hookean elasticity on the GPU:
-//   k_apply     tangent application, on the fly (Algorithm 1) or from the point cache
-//   k_cache     point cache {F^-1, ln J} at the linearisation point (partial assembly, Section 3.2)
-//   k_residual  residual R(u) (Eq. F)
-//   k_diagonal  operator diagonal (Section 2.3)
-// Each block processes NE elements of one colour class; elements of a class share no node,
-// so the read-modify-write scatter of a launch is race-free and deterministic.  The eight
-// classes run as eight launches in a fixed order.
+//   k_apply         tangent application, on the fly (Algorithm 1) or from the point cache
+//   k_apply_reg     FP32 tangent application, one element per thread in registers (p <= 2)
+//   k_gather_local  FP32: sums the element-local results of the apply at the nodes
+//   k_cache         point cache {F^-1, ln J} at the linearisation point (partial assembly, Section 3.2)
+//   k_residual      residual R(u) (Eq. F)
+//   k_diagonal      operator diagonal (Section 2.3)
+// FP64 and double-float: each block processes NE elements of one colour class; elements of a
+// class share no node, so the read-modify-write scatter of a launch is race-free and
+// deterministic, and the eight classes run as eight launches in a fixed order.  FP32: one
+// launch over all elements writes element-local results, and the gather adds each node's
+// contributions in a fixed order (also deterministic, no atomics).
 #include <algorithm>
 #include <type_traits>
 
@@ -454,6 +458,7 @@ __global__ void __launch_bounds__(kRegThreads, NHMF_REG_MINB) k_apply_reg(const 
 #pragma unroll
       for (int q = 0; q < n3; ++q) ubs[(c * n3 + q) * T + threadIdx.x] = ub[c][q];
   }
+
   float acc[3][n3];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
