@@ -37,8 +37,16 @@ template <> struct Cfg<1, float> { static constexpr int NE = 32, THREADS = 256; 
 #define NHMF_Q2F_THREADS 224
 #endif
 template <> struct Cfg<2, float> { static constexpr int NE = NHMF_Q2F_NE, THREADS = NHMF_Q2F_THREADS; };
-template <> struct Cfg<3, float> { static constexpr int NE = 8, THREADS = 256; };
-template <> struct Cfg<4, float> { static constexpr int NE = 8, THREADS = 256; };
+#ifndef NHMF_Q3F_NE
+#define NHMF_Q3F_NE 8
+#define NHMF_Q3F_THREADS 256
+#endif
+#ifndef NHMF_Q4F_NE
+#define NHMF_Q4F_NE 8
+#define NHMF_Q4F_THREADS 256
+#endif
+template <> struct Cfg<3, float> { static constexpr int NE = NHMF_Q3F_NE, THREADS = NHMF_Q3F_THREADS; };
+template <> struct Cfg<4, float> { static constexpr int NE = NHMF_Q4F_NE, THREADS = NHMF_Q4F_THREADS; };
 struct df64;
 template <int P> struct Cfg<P, df64> : Cfg<P, double> {};
 template <> struct Cfg<4, df64> { static constexpr int NE = 4, THREADS = 256; };
