@@ -42,8 +42,8 @@ template <> struct Cfg<2, float> { static constexpr int NE = NHMF_Q2F_NE, THREAD
 #define NHMF_Q3F_THREADS 256
 #endif
 #ifndef NHMF_Q4F_NE
-#define NHMF_Q4F_NE 8
-#define NHMF_Q4F_THREADS 256
+#define NHMF_Q4F_NE 4
+#define NHMF_Q4F_THREADS 160
 #endif
 template <> struct Cfg<3, float> { static constexpr int NE = NHMF_Q3F_NE, THREADS = NHMF_Q3F_THREADS; };
 template <> struct Cfg<4, float> { static constexpr int NE = NHMF_Q4F_NE, THREADS = NHMF_Q4F_THREADS; };

@@ -382,11 +382,11 @@ enum { L_IN = 0, L_E0, L_D1, L_E1, L_D2, L_M2, L_U1, L_T1, L_U0, L_T0, L_OUT };
 // (p - p0) + R + 1 + dx + dy R of the padded positions p0 - 1 .. p0 + 128 + 2R (L = 130 + 2R
 // rows, zero outside the grid).  A staged plane is kept as two arrays of 16-byte halves
 // (channels 0-7, then 8-15, L rows apart), so that 8 consecutive rows form one canonical
-// K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of up to kTcZ tiles along z
-// (fewer on small grids) with a ring of four plane slots: while the 27 MMAs of tile z (M = 128 positions, N = 16
-// output channels, K = 16 input channels, BF16 -> FP32, one per tap) run, its threads stage
-// plane z + 2 for the next tile; the MMAs are committed to an mbarrier and the four warps read
-// their 32 accumulator rows back from tensor memory.
+// K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of up to kTcZ tiles
+// along z (fewer on small grids) with a ring of four plane slots and two accumulators: while
+// the 27 MMAs of tile z (M = 128 positions, N = 16 output channels, K = 16 input channels,
+// BF16 -> FP32, one per tap) run, its four warps read tile z - 1's 32 accumulator rows each
+// back from tensor memory and stage plane z + 2 for the next tile with cp.async.
 constexpr int kTcThreads = 128;
 constexpr int kTcCols = 32;                   // TMEM columns allocated per block (N = 16 used)
 constexpr int kTcZ = 8;                       // at most this many tiles per block column along z
@@ -515,7 +515,7 @@ __device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long lon
   }
 }
 
-size_t conv_tc_smem(int m) { return 27 * 512 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 16; }
+size_t conv_tc_smem(int m) { return 27 * 512 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32; }
 
 // Stage positions base .. base + L - 1 of plane zz in a padded row order of length R with the
 // grid at x in [xo, xo + m), y in [yo, yo + m) (zeros elsewhere) into `slot` (two halves L rows apart).
@@ -537,59 +537,109 @@ __device__ __forceinline__ void tc_stage(const __nv_bfloat16* __restrict__ in, i
   }
 }
 
+// Asynchronous form of tc_stage: 16-byte cp.async copies (zero-filled outside the grid), one
+// commit group per call; the caller waits with cp_async_wait_all before the MMAs read the slot.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(__cvta_generic_to_global(src)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__ in, int m, int R, int L, int base,
+                                               int xo, int yo, int zz, unsigned char* slot) {
+  const uint32_t s = smem_u32(slot);
+  const uint4* g = reinterpret_cast<const uint4*>(in);
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    const int pp = base + j;
+    const uint4* src = g;  // a valid address for the zero-filled copies, which read nothing
+    uint32_t bytes = 0;
+    if (pp >= 0 && zz >= 0 && zz < m) {
+      const int y = pp / R - yo, x = pp % R - xo;
+      if (y >= 0 && y < m && x >= 0 && x < m) {
+        src = g + 2 * (x + (long long)m * (y + (long long)m * zz));
+        bytes = 16;
+      }
+    }
+    cp_async16(s + (uint32_t)j * 16u, src, bytes);
+    cp_async16(s + (uint32_t)(L + j) * 16u, src + 1, bytes);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Two accumulators (TMEM columns 0-15 and 16-31) and two mbarriers.  Per tile z of a column:
+// thread 0 issues its 27 MMAs into accumulator t & 1 (t counts the block's tiles); all threads
+// wait for tile z - 1's MMAs, which frees the slot of plane z - 2 for plane z + 2, start that
+// copy, write tile z - 1's outputs, then wait for the copy and synchronise before tile z + 1's
+// MMAs are issued.
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
   unsigned char* sB = sm;                                  // [27][512 B] weights, canonical
   unsigned char* sA = sm + 27 * 512;                       // [4 slots][2 halves][L][16 B]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 8 * L * 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  const uint32_t s_bar = smem_u32(bar);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 8 * L * 16);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const uint32_t s_bar0 = smem_u32(bar);
   const int warp = threadIdx.x >> 5;
   auto slot = [&](int plane) { return sA + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
-  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kTcCols);
+  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar0, kTcCols);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_bar0 + 8u), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc, nvox = (long long)m * m * m;
-  uint32_t phase = 0;
+  uint32_t phases = 0;  // bit b: the phase of mbarrier b to wait for next
+  unsigned t = 0;       // tiles issued by this block
   bool timed_out = false;
+  // waits for the MMAs of the tile with counter tt, then writes its outputs (plane zz)
+  auto finish = [&](unsigned tt, int p0, int zz) -> bool {
+    const unsigned b = tt & 1u;
+    const bool done = tc_wait(s_bar0 + 8u * b, (phases >> b) & 1u);
+    phases ^= 1u << b;
+    if (__syncthreads_or(!done) != 0) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[16];
+    tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + 16u * b, r);
+    const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
+    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * zz), nvox, r);
+    return true;
+  };
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
     // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
-    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
-    for (int z = zb; z < ze; ++z) {
+    for (int z = zb; z < ze; ++z, ++t) {
       if (threadIdx.x == 0) {
-        const uint32_t b0 = smem_u32(sB);
+        const uint32_t b0 = smem_u32(sB), acc = tmem + 16u * (t & 1u);
         for (int tap = 0; tap < 27; ++tap) {
           const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
           const int j0 = R + 1 + dx + dy * R;  // rows j0 .. j0 + 127 < L of plane z + dz
-          tc_mma(tmem, tc_desc(smem_u32(slot(z + dz)) + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
+          tc_mma(acc, tc_desc(smem_u32(slot(z + dz)) + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
                  tc_desc(b0 + (uint32_t)tap * 512u, 256u, 128u), tap > 0);
         }
-        tc_commit(s_bar);
+        tc_commit(s_bar0 + 8u * (t & 1u));
       }
-      // plane z + 2 (for the next tile) goes to the slot of plane z - 2, which no MMA in flight reads
-      if (z + 1 < ze) {
-        tc_stage(a.in, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (z > zb && !finish(t - 1, p0, z - 1)) {
+        timed_out = true;
+        break;
       }
-      const bool done = tc_wait(s_bar, phase);
-      phase ^= 1u;
-      timed_out = __syncthreads_or(!done) != 0;
-      if (timed_out) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t r[16];
-      tc_ld16(tmem + ((32u * (uint32_t)warp) << 16), r);
-      const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
-      if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * z), nvox, r);
-      tc_sync();  // the next tile's MMAs overwrite the accumulator and read the plane staged above
+      // tile z - 1 is complete: plane z + 2 goes to the slot of plane z - 2
+      if (z + 1 < ze) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
+      cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_sync();  // tile z + 1's MMAs read the plane staged above and overwrite tile z - 1's accumulator
     }
+    if (!timed_out && !finish(t - 1, p0, ze - 1)) timed_out = true;
+    tc_sync();
   }
+  cp_async_wait_all();
   tc_teardown(tmem, kTcCols, timed_out, status);
 }
-
 // ------------------------------------------------------------------ transposed stride-2 conv on tcgen05
 // out[o] = sum over taps d with o - d even of W_d in[(o - d) / 2], per direction.  Writing
 // o = 2c + q (q = 0, 1), class q = 0 takes tap d = 0 (source c) and q = 1 takes d = -1 (source
@@ -627,7 +677,8 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(mi, zb + zc);
     // staged row j of a plane is coarse position p0 + j = y R + x
-    for (int pl = zb; pl <= zb + 1; ++pl) tc_stage(a.in, mi, R, L, p0, 0, 0, pl, slot(pl));
+    for (int pl = zb; pl <= zb + 1; ++pl) tc_stage_async(a.in, mi, R, L, p0, 0, 0, pl, slot(pl));
+    cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
     for (int cz = zb; cz < ze; ++cz) {
@@ -650,10 +701,8 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
         }
         tc_commit(s_bar);
       }
-      if (cz + 1 < ze) {  // plane cz + 2 goes to the slot of plane cz - 1
-        tc_stage(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2));
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
+      // plane cz + 2 goes to the slot of plane cz - 1; the copy runs during the MMAs and the epilogue
+      if (cz + 1 < ze) tc_stage_async(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2));
       const bool done = tc_wait(s_bar, phase);
       phase ^= 1u;
       timed_out = __syncthreads_or(!done) != 0;
@@ -668,9 +717,12 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
         if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1))
           tc_emit(a, (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz)), nvox, r);
       }
+      cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_sync();
     }
   }
+  cp_async_wait_all();
   tc_teardown(tmem, kUpCols, timed_out, status);
 }
 
@@ -689,42 +741,57 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint3
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
 }
 
-size_t wgrad_s1_smem(int m) { return 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16; }
+size_t wgrad_s1_smem(int m) { return 2 * 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16; }
+
+// P rows of a tile, asynchronously: position p0 + j = y R + x + 1 of plane z (zero on the pad
+// columns and past the plane) to row j of both 16-byte channel halves (128 rows apart).
+__device__ __forceinline__ void wg_stage_rows_async(const __nv_bfloat16* __restrict__ P, int m, int R, int p0, int z,
+                                                    unsigned char* sP) {
+  const uint32_t s = smem_u32(sP);
+  const uint4* g = reinterpret_cast<const uint4*>(P);
+  for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+    const int p = p0 + j, y = p / R, x = p % R - 1;
+    const uint4* src = g;
+    uint32_t bytes = 0;
+    if (p < m * R && x >= 0 && x < m) {
+      src = g + 2 * (x + (long long)m * (y + (long long)m * z));
+      bytes = 16;
+    }
+    cp_async16(s + (uint32_t)j * 16u, src, bytes);
+    cp_async16(s + (uint32_t)(128 + j) * 16u, src + 1, bytes);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __restrict__ P,
                                                          const __nv_bfloat16* __restrict__ Q, int m, int zc,
                                                          float* partial) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int R = m + 2, L = 130 + 2 * R;
-  unsigned char* sP = sm;                       // [2 halves][128][16 B]
-  unsigned char* sQ = sm + 2 * 128 * 16;        // [4 slots][2 halves][L][16 B]
+  unsigned char* sP0 = sm;                      // [2 buffers][2 halves][128][16 B]
+  unsigned char* sQ = sm + 2 * 2 * 128 * 16;    // [4 slots][2 halves][L][16 B]
   auto slot = [&](int plane) { return sQ + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc;
   float acc[3][2][4] = {};
+  unsigned tt = 0;  // tiles done by this block; the P rows of tile tt are in buffer tt & 1
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
   for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
-    tc_stage(Q, m, R, L, p0 - 1, 1, 1, zb - 1, slot(zb - 1));
-    tc_stage(Q, m, R, L, p0 - 1, 1, 1, zb, slot(zb));
-    for (int z = zb; z < ze; ++z) {
-      tc_stage(Q, m, R, L, p0 - 1, 1, 1, z + 1, slot(z + 1));
-      // P rows: position p0 + j = y R + x + 1 of plane z (zero on the pad columns and past the plane)
-      for (int j = threadIdx.x; j < 128; j += blockDim.x) {
-        const int p = p0 + j, y = p / R, x = p % R - 1;
-        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-        if (p < m * R && x >= 0 && x < m) {
-          const uint4* src = reinterpret_cast<const uint4*>(P) + 2 * (x + (long long)m * (y + (long long)m * z));
-          lo = __ldg(src);
-          hi = __ldg(src + 1);
-        }
-        *reinterpret_cast<uint4*>(sP + j * 16) = lo;
-        *reinterpret_cast<uint4*>(sP + (128 + j) * 16) = hi;
+    // planes z - 1 .. z + 1 of Q and the P rows of plane z are in shared memory when tile z
+    // starts; plane z + 2 and the rows of plane z + 1 are copied while tile z computes
+    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    wg_stage_rows_async(P, m, R, p0, zb, sP0 + (tt & 1u) * 4096);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int z = zb; z < ze; ++z, ++tt) {
+      if (z + 1 < ze) {
+        tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
+        wg_stage_rows_async(P, m, R, p0, z + 1, sP0 + ((tt + 1) & 1u) * 4096);
       }
-      __syncthreads();
-      const uint32_t sp = smem_u32(sP);
+      const uint32_t sp = smem_u32(sP0 + (tt & 1u) * 4096);
       for (int c = 0; c < 8; ++c) {
         // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
         uint32_t a0, a1, a2, a3;
@@ -742,6 +809,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
       }
+      cp_async_wait_all();
       __syncthreads();
     }
   }
