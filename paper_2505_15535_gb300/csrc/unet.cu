@@ -383,15 +383,12 @@ enum { L_IN = 0, L_E0, L_D1, L_E1, L_D2, L_M2, L_U1, L_T1, L_U0, L_T0, L_OUT };
 // rows, zero outside the grid).  A staged plane is kept as two arrays of 16-byte halves
 // (channels 0-7, then 8-15, L rows apart), so that 8 consecutive rows form one canonical
 // K-major core matrix (8 rows x 16 B, no swizzle).  A block walks a column of up to kTcZ tiles
-// along z (fewer on small grids) with a ring of four plane slots and two accumulators: while
-// the 27 MMAs of tile z (M = 128 positions, N = 16 output channels, K = 16 input channels,
-// BF16 -> FP32, one per tap) run, its four warps read tile z - 1's 32 accumulator rows each
-// back from tensor memory and stage plane z + 2 for the next tile with cp.async.
+// along z (fewer on small grids); MMAs are M = 128 positions x N output columns x K = 16 input
+// channels, BF16 -> FP32 in tensor memory, issued by one thread, and each warp reads its 32
+// accumulator rows back.
 constexpr int kTcThreads = 128;
-constexpr int kTcCols = 32;                   // TMEM columns allocated per block (N = 16 used)
 constexpr int kTcZ = 8;                       // at most this many tiles per block column along z
 constexpr int kTcUnits = 600;                 // shorter columns below this many column units
-constexpr int kTcBlocksPerSM = 3;
 constexpr unsigned kTcSpinLimit = 1u << 22;   // bounded wait for the MMAs of one tile
 // instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10), both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24
@@ -406,12 +403,18 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// D[tmem] (+)= A B for one 128 x 16 x 16 tile; issued by one thread.
-__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, bool accumulate) {
+// instruction descriptor of an M = 128 MMA with N output columns (a multiple of 16, <= 256)
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// D[tmem] (+)= A B for one 128 x N x 16 tile (N = 16 unless idesc says otherwise); issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, bool accumulate,
+                                       uint32_t idesc = kTcIdesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"((uint32_t)accumulate) : "memory");
+      "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)accumulate) : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -445,6 +448,22 @@ __device__ __forceinline__ void tc_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// `cols` TMEM columns and `nbar` consecutive mbarriers (8 bytes apart) for the block.
+__device__ __forceinline__ uint32_t tc_alloc_init(uint32_t* tslot, uint32_t bar, int nbar, uint32_t cols) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nbar; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar + 8u * (uint32_t)i), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_sync();
+  return *tslot;
+}
+
 // Block setup: weights [27][16 co][16 ci] to the canonical per-tap layout (co, ci) at
 // (co % 8) 16 + (co / 8) 128 + (ci % 8) 2 + (ci / 8) 256, `cols` TMEM columns, the mbarrier.
 __device__ __forceinline__ uint32_t tc_setup(const __nv_bfloat16* w, unsigned char* sB, uint32_t* tslot,
@@ -454,17 +473,7 @@ __device__ __forceinline__ uint32_t tc_setup(const __nv_bfloat16* w, unsigned ch
     const int tap = i >> 5, co = (i >> 1) & 15, hf = i & 1;
     *reinterpret_cast<uint4*>(sB + tap * 512 + (co & 7) * 16 + (co >> 3) * 128 + hf * 256) = wg[i];
   }
-  if (threadIdx.x < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(cols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_sync();
-  return *tslot;
+  return tc_alloc_init(tslot, bar, 1, cols);
 }
 
 __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t cols, bool timed_out, unsigned* status) {
@@ -515,36 +524,17 @@ __device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long lon
   }
 }
 
-size_t conv_tc_smem(int m) { return 27 * 512 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32; }
-
-// Stage positions base .. base + L - 1 of plane zz in a padded row order of length R with the
-// grid at x in [xo, xo + m), y in [yo, yo + m) (zeros elsewhere) into `slot` (two halves L rows apart).
-__device__ __forceinline__ void tc_stage(const __nv_bfloat16* __restrict__ in, int m, int R, int L, int base,
-                                         int xo, int yo, int zz, unsigned char* slot) {
-  for (int j = threadIdx.x; j < L; j += blockDim.x) {
-    const int pp = base + j;
-    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-    if (pp >= 0 && zz >= 0 && zz < m) {
-      const int y = pp / R - yo, x = pp % R - xo;
-      if (y >= 0 && y < m && x >= 0 && x < m) {
-        const uint4* src = reinterpret_cast<const uint4*>(in) + 2 * (x + (long long)m * (y + (long long)m * zz));
-        lo = __ldg(src);
-        hi = __ldg(src + 1);
-      }
-    }
-    *reinterpret_cast<uint4*>(slot + j * 16) = lo;
-    *reinterpret_cast<uint4*>(slot + (L + j) * 16) = hi;
-  }
-}
-
-// Asynchronous form of tc_stage: 16-byte cp.async copies (zero-filled outside the grid), one
-// commit group per call; the caller waits with cp_async_wait_all before the MMAs read the slot.
+// 16-byte global -> shared copy on the cp.async path; `bytes` = 0 zero-fills the destination.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(__cvta_generic_to_global(src)),
                "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Stage positions base .. base + L - 1 of plane zz in a padded row order of length R with the
+// grid at x in [xo, xo + m), y in [yo, yo + m) (zeros elsewhere) into `slot` (two 16-byte
+// channel halves, L rows apart) with cp.async, as one commit group; the caller waits for the
+// group (cp.async.wait_group / wait_all) and, before MMAs read the slot, fences the async proxy.
 __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__ in, int m, int R, int L, int base,
                                                int xo, int yo, int zz, unsigned char* slot) {
   const uint32_t s = smem_u32(slot);
@@ -566,80 +556,127 @@ __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Two accumulators (TMEM columns 0-15 and 16-31) and two mbarriers.  Per tile z of a column:
-// thread 0 issues its 27 MMAs into accumulator t & 1 (t counts the block's tiles); all threads
-// wait for tile z - 1's MMAs, which frees the slot of plane z - 2 for plane z + 2, start that
-// copy, write tile z - 1's outputs, then wait for the copy and synchronise before tile z + 1's
-// MMAs are issued.
+// Plane-streaming form.  A block keeps the accumulators of all (up to kTcZ) output tiles of its
+// column in tensor memory (16 columns each) and passes each input plane zi of the column's
+// window (zb - 1 .. ze, inside the grid) through the tensor cores once: for each in-plane tap
+// (dx, dy) one MMA of N = 16, 32 or 48 multiplies the plane's shifted 128-row window by the
+// weights of dz = +1, 0, -1 stacked along N, and so adds plane zi's contribution to outputs
+// zi - 1, zi, zi + 1 at once (those inside the column).  Each A tile is read 9 times per plane
+// instead of 27 times per output tile.  The weights of each (dx, dy) form a 48-row strip, row
+// 16 b + co holding dz = 1 - b, so that the rows of any run of consecutive outputs are one
+// window of the strip.  Every output receives its 27 taps in the order of the per-tap form
+// (dz, then dy, then dx) on a zeroed accumulator.  Planes are staged with cp.async in a ring of
+// three slots, two planes ahead; output zi - 2 is read back while plane zi's MMAs run.
+constexpr int kTcSCols = 16 * kTcZ;               // TMEM columns: one 16-column accumulator per output tile
+constexpr size_t kTcSSmemMin = 48 * 1024;         // at most 4 blocks (4 x 128 TMEM columns) per SM
+constexpr int kTcSBlocksPerSM = 4;
+
+__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(0u) : "memory");
+}
+
+// Weights [27][16 co][16 ci] as 9 strips of 48 rows: strip s = tap % 9 (dx, dy), row r =
+// 16 (2 - tap / 9) + co, canonical K-major at (r % 8) 16 + (r / 8) 128 + (ci / 8) 768.
+__device__ __forceinline__ void tc_weights_strips(const __nv_bfloat16* w, unsigned char* sB) {
+  const uint4* wg = reinterpret_cast<const uint4*>(w);
+  for (int i = threadIdx.x; i < 27 * 16 * 2; i += blockDim.x) {
+    const int tap = i >> 5, co = (i >> 1) & 15, hf = i & 1, r = 16 * (2 - tap / 9) + co;
+    *reinterpret_cast<uint4*>(sB + (tap % 9) * 1536 + (r & 7) * 16 + (r >> 3) * 128 + hf * 768) = wg[i];
+  }
+}
+
+size_t conv_tc_smem(int m) {
+  const size_t need = 9 * 1536 + 3 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32;
+  return std::max(need, kTcSSmemMin);
+}
+
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
-  unsigned char* sB = sm;                                  // [27][512 B] weights, canonical
-  unsigned char* sA = sm + 27 * 512;                       // [4 slots][2 halves][L][16 B]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 8 * L * 16);  // [2]
+  unsigned char* sB = sm;                                  // [9 strips][1536 B] weights
+  unsigned char* sA = sm + 9 * 1536;                       // [3 slots][2 halves][L][16 B]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 6 * L * 16);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const uint32_t s_bar0 = smem_u32(bar);
   const int warp = threadIdx.x >> 5;
-  auto slot = [&](int plane) { return sA + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
-  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar0, kTcCols);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_bar0 + 8u), "r"(1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
+  auto slot = [&](int plane) { return sA + (plane % 3) * 2 * L * 16; };  // plane >= 0
+  tc_weights_strips(a.w, sB);
+  const uint32_t tmem = tc_alloc_init(tslot, s_bar0, 2, kTcSCols);
+  const uint32_t lanes = tmem + ((32u * (uint32_t)warp) << 16);  // this warp's 32 TMEM lanes
 
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc, nvox = (long long)m * m * m;
   uint32_t phases = 0;  // bit b: the phase of mbarrier b to wait for next
-  unsigned t = 0;       // tiles issued by this block
+  unsigned k = 0;       // planes issued by this block; plane k commits to mbarrier k & 1
   bool timed_out = false;
-  // waits for the MMAs of the tile with counter tt, then writes its outputs (plane zz)
-  auto finish = [&](unsigned tt, int p0, int zz) -> bool {
-    const unsigned b = tt & 1u;
+  auto wait_plane = [&](unsigned kk) -> bool {
+    const unsigned b = kk & 1u;
     const bool done = tc_wait(s_bar0 + 8u * b, (phases >> b) & 1u);
     phases ^= 1u << b;
     if (__syncthreads_or(!done) != 0) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    uint32_t r[16];
-    tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + 16u * b, r);
-    const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
-    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * zz), nvox, r);
     return true;
+  };
+  // writes output plane o (accumulator o - zb) of the tile at p0
+  auto finish = [&](int p0, int zb, int o) {
+    uint32_t r[16];
+    tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
+    const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
+    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * o), nvox, r);
   };
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
+    const int first = max(zb - 1, 0), last = min(ze, m - 1);  // input planes of the column
+    for (int c = 0; c < ze - zb; ++c) tc_st16_zero(lanes + 16u * (uint32_t)c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
-    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    for (int pl = first; pl <= min(first + 1, last); ++pl) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
     cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
-    for (int z = zb; z < ze; ++z, ++t) {
+    for (int zi = first; zi <= last; ++zi, ++k) {
       if (threadIdx.x == 0) {
-        const uint32_t b0 = smem_u32(sB), acc = tmem + 16u * (t & 1u);
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
-          const int j0 = R + 1 + dx + dy * R;  // rows j0 .. j0 + 127 < L of plane z + dz
-          tc_mma(acc, tc_desc(smem_u32(slot(z + dz)) + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
-                 tc_desc(b0 + (uint32_t)tap * 512u, 256u, 128u), tap > 0);
+        const int olo = max(zi - 1, zb), ohi = min(zi + 1, ze - 1), blo = 1 - zi + olo;
+        const uint32_t idesc = tc_idesc(16 * (ohi - olo + 1)), acc = tmem + 16u * (uint32_t)(olo - zb);
+        const uint32_t sa = smem_u32(slot(zi)), sb = smem_u32(sB) + 256u * (uint32_t)blo;
+        for (int s = 0; s < 9; ++s) {
+          const int dx = s % 3 - 1, dy = s / 3 - 1;
+          const int j0 = R + 1 + dx + dy * R;  // rows j0 .. j0 + 127 < L of plane zi
+          tc_mma(acc, tc_desc(sa + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
+                 tc_desc(sb + 1536u * (uint32_t)s, 768u, 128u), true, idesc);
         }
-        tc_commit(s_bar0 + 8u * (t & 1u));
+        tc_commit(s_bar0 + 8u * (k & 1u));
       }
-      if (z > zb && !finish(t - 1, p0, z - 1)) {
+      // plane zi - 1's MMAs done: output zi - 2 is complete and slot (zi - 1) % 3 takes plane zi + 2
+      if (zi > first && !wait_plane(k - 1)) {
         timed_out = true;
         break;
       }
-      // tile z - 1 is complete: plane z + 2 goes to the slot of plane z - 2
-      if (z + 1 < ze) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
-      cp_async_wait_all();
+      const bool ahead = zi + 2 <= last;
+      if (ahead) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, zi + 2, slot(zi + 2));
+      if (zi > first && zi - 2 >= zb) finish(p0, zb, zi - 2);
+      if (ahead)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane zi + 1 has landed
+      else
+        cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_sync();  // tile z + 1's MMAs read the plane staged above and overwrite tile z - 1's accumulator
+      tc_sync();
     }
-    if (!timed_out && !finish(t - 1, p0, ze - 1)) timed_out = true;
+    if (!timed_out) {
+      if (!wait_plane(k - 1)) {
+        timed_out = true;
+      } else {
+        for (int o = max(zb, last - 1); o < ze; ++o) finish(p0, zb, o);
+      }
+    }
     tc_sync();
   }
   cp_async_wait_all();
-  tc_teardown(tmem, kTcCols, timed_out, status);
+  tc_teardown(tmem, kTcSCols, timed_out, status);
 }
+
 // ------------------------------------------------------------------ transposed stride-2 conv on tcgen05
 // out[o] = sum over taps d with o - d even of W_d in[(o - d) / 2], per direction.  Writing
 // o = 2c + q (q = 0, 1), class q = 0 takes tap d = 0 (source c) and q = 1 takes d = -1 (source
@@ -855,7 +892,7 @@ void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   const long long m = a.m_out, per_plane = (m * (m + 2) + 127) / 128;
   const int zc = tc_column(per_plane, (int)m);
   const long long nunits = per_plane * ((m + zc - 1) / zc);
-  k_conv_tc<<<(int)std::min<long long>(nunits, kTcBlocksPerSM * 152), kTcThreads, smem, s>>>(a, zc, status);
+  k_conv_tc<<<(int)std::min<long long>(nunits, kTcSBlocksPerSM * 152), kTcThreads, smem, s>>>(a, zc, status);
 }
 
 // out = act(conv_G(in; w) + bias + add) * mask
