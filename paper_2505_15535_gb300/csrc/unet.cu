@@ -484,16 +484,20 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t cols, bool t
 }
 
 // Epilogue of one output voxel v from its 16 FP32 accumulators: + bias + add, ReLU, mask, store.
-__device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long long nvox, const uint32_t (&r)[16]) {
+__device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long long nvox, const uint32_t (&r)[16],
+                                        const float* bias) {
   float o[16];
 #pragma unroll
-  for (int ch = 0; ch < 16; ++ch) o[ch] = __uint_as_float(r[ch]) + (a.bias ? a.bias[ch] : 0.f);
+  for (int ch = 0; ch < 16; ++ch) o[ch] = __uint_as_float(r[ch]) + (bias ? bias[ch] : 0.f);
   if (a.add) {
+    const uint4* ap = reinterpret_cast<const uint4*>(a.add + v * kC);
+    const uint4 q0 = ap[0], q1 = ap[1];
+    const uint32_t q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int ch = 0; ch < 16; ch += 2) {
-      const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(a.add + v * kC + ch);
-      o[ch] += __low2float(ad);
-      o[ch + 1] += __high2float(ad);
+    for (int h = 0; h < 8; ++h) {
+      const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
+      o[2 * h] += __low2float(ad);
+      o[2 * h + 1] += __high2float(ad);
     }
   }
   if (a.relu) {
@@ -501,11 +505,14 @@ __device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long lon
     for (int ch = 0; ch < 16; ++ch) o[ch] = fmaxf(o[ch], 0.f);
   }
   if (a.mask) {
+    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + v * kC);
+    const uint4 q0 = mp[0], q1 = mp[1];
+    const uint32_t q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int ch = 0; ch < 16; ch += 2) {
-      const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kC + ch);
-      if (!(__low2float(mk) > 0.f)) o[ch] = 0.f;
-      if (!(__high2float(mk) > 0.f)) o[ch + 1] = 0.f;
+    for (int h = 0; h < 8; ++h) {
+      const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
+      if (!(__low2float(mk) > 0.f)) o[2 * h] = 0.f;
+      if (!(__high2float(mk) > 0.f)) o[2 * h + 1] = 0.f;
     }
   }
   if (a.out_planar) {
@@ -539,19 +546,24 @@ __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__
                                                int xo, int yo, int zz, unsigned char* slot) {
   const uint32_t s = smem_u32(slot);
   const uint4* g = reinterpret_cast<const uint4*>(in);
+  const bool plane_in = zz >= 0 && zz < m;
+  // padded row and column of position base + j (base >= -R), stepped without division
+  int yr = (base + (int)threadIdx.x + R) / R - 1, xr = (base + (int)threadIdx.x + R) % R;
   for (int j = threadIdx.x; j < L; j += blockDim.x) {
-    const int pp = base + j;
+    const int y = yr - yo, x = xr - xo;
     const uint4* src = g;  // a valid address for the zero-filled copies, which read nothing
     uint32_t bytes = 0;
-    if (pp >= 0 && zz >= 0 && zz < m) {
-      const int y = pp / R - yo, x = pp % R - xo;
-      if (y >= 0 && y < m && x >= 0 && x < m) {
-        src = g + 2 * (x + (long long)m * (y + (long long)m * zz));
-        bytes = 16;
-      }
+    if (plane_in && y >= 0 && y < m && x >= 0 && x < m) {
+      src = g + 2 * (x + (long long)m * (y + (long long)m * zz));
+      bytes = 16;
     }
     cp_async16(s + (uint32_t)j * 16u, src, bytes);
     cp_async16(s + (uint32_t)(L + j) * 16u, src + 1, bytes);
+    xr += blockDim.x;
+    while (xr >= R) {
+      xr -= R;
+      ++yr;
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -587,23 +599,40 @@ __device__ __forceinline__ void tc_weights_strips(const __nv_bfloat16* w, unsign
   }
 }
 
+#ifndef NHMF_CONV_SLOTS
+#define NHMF_CONV_SLOTS 3
+#endif
+constexpr int kTcSlots = NHMF_CONV_SLOTS;  // plane slots: planes are staged kTcSlots - 1 ahead
+
 size_t conv_tc_smem(int m) {
-  const size_t need = 9 * 1536 + 3 * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32;
+  const size_t need = 9 * 1536 + kTcSlots * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32 + 64;
   return std::max(need, kTcSSmemMin);
 }
 
+__device__ __forceinline__ void cp_async_wait_upto(int n) {  // n most recent groups may stay pending
+  if (n <= 0)
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (n == 1)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc, unsigned* status) {
+  static_assert(kTcSlots >= 3 && kTcSlots <= 4, "three or four plane slots");
   extern __shared__ __align__(128) unsigned char sm[];
   const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
   unsigned char* sB = sm;                                  // [9 strips][1536 B] weights
-  unsigned char* sA = sm + 9 * 1536;                       // [3 slots][2 halves][L][16 B]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 6 * L * 16);  // [2]
+  unsigned char* sA = sm + 9 * 1536;                       // [kTcSlots][2 halves][L][16 B]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + kTcSlots * 2 * L * 16);  // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  float* sbias = reinterpret_cast<float*>(bar + 4);        // [16]
   const uint32_t s_bar0 = smem_u32(bar);
   const int warp = threadIdx.x >> 5;
-  auto slot = [&](int plane) { return sA + (plane % 3) * 2 * L * 16; };  // plane >= 0
+  auto slot = [&](int plane) { return sA + (plane % kTcSlots) * 2 * L * 16; };  // plane >= 0
   tc_weights_strips(a.w, sB);
-  const uint32_t tmem = tc_alloc_init(tslot, s_bar0, 2, kTcSCols);
+  if (threadIdx.x < 16) sbias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.f;
+  const uint32_t tmem = tc_alloc_init(tslot, s_bar0, 2, kTcSCols);  // synchronises the block
   const uint32_t lanes = tmem + ((32u * (uint32_t)warp) << 16);  // this warp's 32 TMEM lanes
 
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
@@ -611,9 +640,11 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc
   uint32_t phases = 0;  // bit b: the phase of mbarrier b to wait for next
   unsigned k = 0;       // planes issued by this block; plane k commits to mbarrier k & 1
   bool timed_out = false;
+  // thread 0 polls the mbarrier; the block learns the outcome at the barrier
   auto wait_plane = [&](unsigned kk) -> bool {
     const unsigned b = kk & 1u;
-    const bool done = tc_wait(s_bar0 + 8u * b, (phases >> b) & 1u);
+    bool done = true;
+    if (threadIdx.x == 0) done = tc_wait(s_bar0 + 8u * b, (phases >> b) & 1u);
     phases ^= 1u << b;
     if (__syncthreads_or(!done) != 0) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -624,7 +655,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc
     uint32_t r[16];
     tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
     const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
-    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * o), nvox, r);
+    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * o), nvox, r, sbias);
   };
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
@@ -632,8 +663,9 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc
     for (int c = 0; c < ze - zb; ++c) tc_st16_zero(lanes + 16u * (uint32_t)c);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
-    for (int pl = first; pl <= min(first + 1, last); ++pl) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
-    cp_async_wait_all();
+    for (int pl = first; pl <= min(first + kTcSlots - 2, last); ++pl)
+      tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    cp_async_wait_upto(min(kTcSlots - 3, last - first - 1));  // planes first, first + 1 have landed
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
     for (int zi = first; zi <= last; ++zi, ++k) {
@@ -649,18 +681,17 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc
         }
         tc_commit(s_bar0 + 8u * (k & 1u));
       }
-      // plane zi - 1's MMAs done: output zi - 2 is complete and slot (zi - 1) % 3 takes plane zi + 2
+      // plane zi - 1's MMAs done: output zi - 2 is complete and the slot of plane zi - 1 takes
+      // plane zi + kTcSlots - 1
       if (zi > first && !wait_plane(k - 1)) {
         timed_out = true;
         break;
       }
-      const bool ahead = zi + 2 <= last;
-      if (ahead) tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, zi + 2, slot(zi + 2));
+      if (zi + kTcSlots - 1 <= last)
+        tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, zi + kTcSlots - 1, slot(zi + kTcSlots - 1));
       if (zi > first && zi - 2 >= zb) finish(p0, zb, zi - 2);
-      if (ahead)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane zi + 1 has landed
-      else
-        cp_async_wait_all();
+      // plane zi + 1 has landed; the planes staged after it may still be in flight
+      cp_async_wait_upto(min(kTcSlots - 2, last - zi - 1));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_sync();
     }
@@ -752,7 +783,7 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
         uint32_t r[16];
         tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + (uint32_t)(16 * cl), r);
         if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1))
-          tc_emit(a, (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz)), nvox, r);
+          tc_emit(a, (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz)), nvox, r, a.bias);
       }
       cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
