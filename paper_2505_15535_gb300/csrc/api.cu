@@ -138,6 +138,7 @@ nhmf_status nhmf_check_status(nhmf_ctx* c, void* stream) {
   if (h & kStatusNonFinite) return fail(c, NHMF_ERR_NONFINITE, "non-finite value");
   if (h & kStatusBreakdown) return fail(c, NHMF_ERR_BREAKDOWN, "Krylov breakdown: p^T A p <= 0");
   if (h & kStatusTcTimeout) return fail(c, NHMF_ERR_CUDA, "tensor-core completion wait timed out");
+  if (h & kStatusTmaSetup) return fail(c, NHMF_ERR_CUDA, "tensor-map encoding for a convolution failed");
   return NHMF_OK;
 }
 

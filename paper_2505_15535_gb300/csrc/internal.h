@@ -119,7 +119,7 @@ struct nhmf_ctx {
 
 namespace nhmf {
 
-enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u, kStatusTcTimeout = 8u };
+enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u, kStatusTcTimeout = 8u, kStatusTmaSetup = 16u };
 void free_work(nhmf_ctx* c);
 nhmf_status ensure_work(nhmf_ctx* c);
 

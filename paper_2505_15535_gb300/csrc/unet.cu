@@ -8,12 +8,13 @@
 // with 3x3x3 zero-padded cross-correlations: conv (stride 1), down (stride 2) and up (the
 // transposed stride-2 convolution).  Activations are channels-last [voxel][16] BF16 (32 B
 // per voxel, one DRAM sector); inputs and outputs with 3 channels are padded to 16 with
-// zero weights.  Every convolution - forward, backward-data and the weight gradient - is an
-// implicit GEMM on the tensor cores with mma.sync m16n8k16 BF16 -> FP32:
-//   forward/backward-data: rows = 16 output voxels, K = 16 input channels per tap, N = 16
-//   output channels (two n8 tiles), 27 taps accumulated in registers;
-//   weight gradient: rows = 16 channels of the per-voxel operand, K = 16 voxels, N = 16
-//   channels of the gathered operand; partial sums per block, reduced in a fixed order.
+// zero weights.  Every convolution is an implicit GEMM on the tensor cores, BF16 -> FP32:
+//   stride-1 forward/backward-data (k_conv_tc) and the transposed stride-2 convolution
+//   (k_up_tc): tcgen05 MMAs with accumulators in tensor memory, M = 128 positions, K = 16
+//   input channels, N = output channels (stacked over dz in the stride-1 form);
+//   stride-2 down-convolution (k_conv) and weight gradients (k_wgrad, k_wgrad_s1): mma.sync
+//   m16n8k16; weight gradients as partial sums per block, reduced in a fixed order.
+#include <cuda.h>  // CUtensorMap and the encoder's types; the encoder itself comes from the driver at run time
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -483,21 +484,34 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t cols, bool t
   if (timed_out && threadIdx.x == 0) atomicOr(status, kStatusTcTimeout);
 }
 
+// Skip-connection and mask rows of voxel v (32 bytes each), or zeros where absent.
+__device__ __forceinline__ void tc_load_addmask(const ConvArgs& a, long long v, uint4 (&ad)[2], uint4 (&mk)[2]) {
+  ad[0] = ad[1] = mk[0] = mk[1] = make_uint4(0u, 0u, 0u, 0u);
+  if (a.add) {
+    const uint4* ap = reinterpret_cast<const uint4*>(a.add + v * kC);
+    ad[0] = ap[0];
+    ad[1] = ap[1];
+  }
+  if (a.mask) {
+    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + v * kC);
+    mk[0] = mp[0];
+    mk[1] = mp[1];
+  }
+}
+
 // Epilogue of one output voxel v from its 16 FP32 accumulators: + bias + add, ReLU, mask, store.
 __device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long long nvox, const uint32_t (&r)[16],
-                                        const float* bias) {
+                                        const float* bias, const uint4 (&ad)[2], const uint4 (&mk)[2]) {
   float o[16];
 #pragma unroll
   for (int ch = 0; ch < 16; ++ch) o[ch] = __uint_as_float(r[ch]) + (bias ? bias[ch] : 0.f);
   if (a.add) {
-    const uint4* ap = reinterpret_cast<const uint4*>(a.add + v * kC);
-    const uint4 q0 = ap[0], q1 = ap[1];
-    const uint32_t q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const uint32_t q[8] = {ad[0].x, ad[0].y, ad[0].z, ad[0].w, ad[1].x, ad[1].y, ad[1].z, ad[1].w};
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
-      const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
-      o[2 * h] += __low2float(ad);
-      o[2 * h + 1] += __high2float(ad);
+      const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
+      o[2 * h] += __low2float(x2);
+      o[2 * h + 1] += __high2float(x2);
     }
   }
   if (a.relu) {
@@ -505,14 +519,12 @@ __device__ __forceinline__ void tc_emit(const ConvArgs& a, long long v, long lon
     for (int ch = 0; ch < 16; ++ch) o[ch] = fmaxf(o[ch], 0.f);
   }
   if (a.mask) {
-    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + v * kC);
-    const uint4 q0 = mp[0], q1 = mp[1];
-    const uint32_t q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const uint32_t q[8] = {mk[0].x, mk[0].y, mk[0].z, mk[0].w, mk[1].x, mk[1].y, mk[1].z, mk[1].w};
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
-      const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
-      if (!(__low2float(mk) > 0.f)) o[2 * h] = 0.f;
-      if (!(__high2float(mk) > 0.f)) o[2 * h + 1] = 0.f;
+      const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
+      if (!(__low2float(x2) > 0.f)) o[2 * h] = 0.f;
+      if (!(__high2float(x2) > 0.f)) o[2 * h + 1] = 0.f;
     }
   }
   if (a.out_planar) {
@@ -542,14 +554,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // grid at x in [xo, xo + m), y in [yo, yo + m) (zeros elsewhere) into `slot` (two 16-byte
 // channel halves, L rows apart) with cp.async, as one commit group; the caller waits for the
 // group (cp.async.wait_group / wait_all) and, before MMAs read the slot, fences the async proxy.
+// Threads tid = 0 .. nthr - 1 of the block take rows tid, tid + nthr, ...
 __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__ in, int m, int R, int L, int base,
-                                               int xo, int yo, int zz, unsigned char* slot) {
+                                               int xo, int yo, int zz, unsigned char* slot, int tid, int nthr) {
   const uint32_t s = smem_u32(slot);
   const uint4* g = reinterpret_cast<const uint4*>(in);
   const bool plane_in = zz >= 0 && zz < m;
   // padded row and column of position base + j (base >= -R), stepped without division
-  int yr = (base + (int)threadIdx.x + R) / R - 1, xr = (base + (int)threadIdx.x + R) % R;
-  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+  int yr = (base + tid + R) / R - 1, xr = (base + tid + R) % R;
+  for (int j = tid; j < L; j += nthr) {
     const int y = yr - yo, x = xr - xo;
     const uint4* src = g;  // a valid address for the zero-filled copies, which read nothing
     uint32_t bytes = 0;
@@ -559,7 +572,7 @@ __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__
     }
     cp_async16(s + (uint32_t)j * 16u, src, bytes);
     cp_async16(s + (uint32_t)(L + j) * 16u, src + 1, bytes);
-    xr += blockDim.x;
+    xr += nthr;
     while (xr >= R) {
       xr -= R;
       ++yr;
@@ -577,11 +590,25 @@ __device__ __forceinline__ void tc_stage_async(const __nv_bfloat16* __restrict__
 // instead of 27 times per output tile.  The weights of each (dx, dy) form a 48-row strip, row
 // 16 b + co holding dz = 1 - b, so that the rows of any run of consecutive outputs are one
 // window of the strip.  Every output receives its 27 taps in the order of the per-tap form
-// (dz, then dy, then dx) on a zeroed accumulator.  Planes are staged with cp.async in a ring of
-// three slots, two planes ahead; output zi - 2 is read back while plane zi's MMAs run.
+// (dz, then dy, then dx) on a zeroed accumulator.
+//
+// Planes arrive by TMA (cp.async.bulk.tensor, 5-D map [z][y][x][2 halves][8 channels]): per
+// 16-byte channel half one box of NY whole padded rows, x from x0 - 1 to x0 + W and zero
+// outside the grid, so that staged row r of a half is padded position Yb R + r (Yb = the padded
+// row of the tile's first halo position p0 - 1).  The grid runs as x-strips of W <=
+// kConvStripMax columns (R = W + 2; a strip's halo columns hold the neighbouring strip's data),
+// which keeps the boxes within the 256-element limit and the slots small (four blocks per SM).
+// One thread of warp 4 waits for plane zi's box, issues its 9 MMAs and, once plane zi - 1's
+// MMAs are done, refills that slot with plane zi + 2 (three slots); warps 0-3 zero a column's
+// accumulators and read output zi - 2 back while plane zi's MMAs run.
 constexpr int kTcSCols = 16 * kTcZ;               // TMEM columns: one 16-column accumulator per output tile
 constexpr size_t kTcSSmemMin = 48 * 1024;         // at most 4 blocks (4 x 128 TMEM columns) per SM
-constexpr int kTcSBlocksPerSM = 4;
+constexpr int kTcSlots = 3;
+#ifndef NHMF_CONV_STRIP
+#define NHMF_CONV_STRIP 64
+#endif
+constexpr int kConvStripMax = NHMF_CONV_STRIP;    // widest x-strip
+constexpr int kTcSThreads = 160;                  // warps 0-3: accumulators; warp 4: TMA and MMA issue
 
 __device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
   asm volatile(
@@ -599,112 +626,169 @@ __device__ __forceinline__ void tc_weights_strips(const __nv_bfloat16* w, unsign
   }
 }
 
-#ifndef NHMF_CONV_SLOTS
-#define NHMF_CONV_SLOTS 3
-#endif
-constexpr int kTcSlots = NHMF_CONV_SLOTS;  // plane slots: planes are staged kTcSlots - 1 ahead
+// x-strips of a stride-1 conv on an m^3 grid: count and width.
+int conv_strip_width(int m, int* nstrips) {
+  *nstrips = (m + kConvStripMax - 1) / kConvStripMax;
+  return (m + *nstrips - 1) / *nstrips;
+}
+
+// Padded rows per box: a tile's taps read rows up to 128 + 3 R - 1 past the box start.
+__host__ __device__ inline int tma_ny(int R) { return (128 + 3 * R) / R + 1; }
+// Bytes of one staged channel half (NY R rows of 16 bytes), rounded up to 128.
+__host__ __device__ inline uint32_t tma_h(int R) { return (uint32_t)((tma_ny(R) * R * 16 + 127) / 128 * 128); }
 
 size_t conv_tc_smem(int m) {
-  const size_t need = 9 * 1536 + kTcSlots * 2 * (size_t)(130 + 2 * (m + 2)) * 16 + 32 + 64;
+  int ns = 0;
+  const int W = conv_strip_width(m, &ns);
+  const size_t need = 9 * 1536 + kTcSlots * 2 * (size_t)tma_h(W + 2) + 8 * 5 + 8 + 64;
   return std::max(need, kTcSSmemMin);
 }
 
-__device__ __forceinline__ void cp_async_wait_upto(int n) {  // n most recent groups may stay pending
-  if (n <= 0)
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  else if (n == 1)
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-  else
-    asm volatile("cp.async.wait_group 2;" ::: "memory");
+// OR of `v` over warps 0-3 (named barrier 1, 128 threads).
+__device__ __forceinline__ bool bar_or_128(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r) : "r"((uint32_t)v) : "memory");
+  return r != 0;
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const ConvArgs a, int zc, unsigned* status) {
-  static_assert(kTcSlots >= 3 && kTcSlots <= 4, "three or four plane slots");
+
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kTcSThreads) k_conv_tc(const ConvArgs a, const __grid_constant__ CUtensorMap map,
+                                                         int zc, int W, int nstrips, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const int m = a.m_out, R = m + 2, L = 130 + 2 * R;
-  unsigned char* sB = sm;                                  // [9 strips][1536 B] weights
-  unsigned char* sA = sm + 9 * 1536;                       // [kTcSlots][2 halves][L][16 B]
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + kTcSlots * 2 * L * 16);  // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  float* sbias = reinterpret_cast<float*>(bar + 4);        // [16]
-  const uint32_t s_bar0 = smem_u32(bar);
+  const int m = a.m_out, R = W + 2, NY = tma_ny(R);
+  const uint32_t H = tma_h(R);
+  unsigned char* sB = sm;
+  unsigned char* sA = sm + 9 * 1536;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + kTcSlots * 2 * H);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + kTcSlots);
+  float* sbias = reinterpret_cast<float*>(bar + 3 + kTcSlots);
+  const uint32_t s_done = smem_u32(bar), s_full = s_done + 16u;
   const int warp = threadIdx.x >> 5;
-  auto slot = [&](int plane) { return sA + (plane % kTcSlots) * 2 * L * 16; };  // plane >= 0
+  const bool epi = warp < 4, issuer = threadIdx.x == 128;
   tc_weights_strips(a.w, sB);
   if (threadIdx.x < 16) sbias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.f;
-  const uint32_t tmem = tc_alloc_init(tslot, s_bar0, 2, kTcSCols);  // synchronises the block
-  const uint32_t lanes = tmem + ((32u * (uint32_t)warp) << 16);  // this warp's 32 TMEM lanes
-
+  const uint32_t tmem = tc_alloc_init(tslot, s_done, 2 + kTcSlots, kTcSCols);
+  const uint32_t lanes = tmem + ((32u * (uint32_t)(warp & 3)) << 16);
+  const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
-  const long long nunits = (long long)per_plane * nzc, nvox = (long long)m * m * m;
-  uint32_t phases = 0;  // bit b: the phase of mbarrier b to wait for next
-  unsigned k = 0;       // planes issued by this block; plane k commits to mbarrier k & 1
+  const long long nunits = (long long)per_plane * nstrips * nzc, nvox = (long long)m * m * m;
+  const uint32_t box_bytes = 2u * (uint32_t)(NY * R * 16);
+  unsigned k = 0, kc = 0;
+  uint32_t fpar = 0, fpend = 0;
   bool timed_out = false;
-  // thread 0 polls the mbarrier; the block learns the outcome at the barrier
+  auto plane_done = [&](unsigned kk) { return tc_wait(s_done + 8u * (kk & 1u), (kk >> 1) & 1u); };
   auto wait_plane = [&](unsigned kk) -> bool {
-    const unsigned b = kk & 1u;
     bool done = true;
-    if (threadIdx.x == 0) done = tc_wait(s_bar0 + 8u * b, (phases >> b) & 1u);
-    phases ^= 1u << b;
-    if (__syncthreads_or(!done) != 0) return false;
+    if (threadIdx.x == 0) done = plane_done(kk);
+    if (bar_or_128(!done)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     return true;
   };
-  // writes output plane o (accumulator o - zb) of the tile at p0
-  auto finish = [&](int p0, int zb, int o) {
-    uint32_t r[16];
-    tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
-    const int p = p0 + threadIdx.x, y = p / R, x = p % R - 1;  // row threadIdx.x is position p
-    if (p < m * R && x >= 0 && x < m) tc_emit(a, x + (long long)m * (y + (long long)m * o), nvox, r, sbias);
+  auto sync_or = [&](bool fail) -> bool {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool any = __syncthreads_or(fail) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return any;
   };
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
-    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
-    const int first = max(zb - 1, 0), last = min(ze, m - 1);  // input planes of the column
-    for (int c = 0; c < ze - zb; ++c) tc_st16_zero(lanes + 16u * (uint32_t)c);
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    // staged row j of a plane is padded position p0 - 1 + j = (y + 1) R + (x + 1)
-    for (int pl = first; pl <= min(first + kTcSlots - 2, last); ++pl)
-      tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
-    cp_async_wait_upto(min(kTcSlots - 3, last - first - 1));  // planes first, first + 1 have landed
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_sync();
+    const int p0 = int(unit % per_plane) * 128;
+    const long long rest = unit / per_plane;
+    const int x0 = int(rest % nstrips) * W, zb = int(rest / nstrips) * zc, ze = min(m, zb + zc);
+    const int first = max(zb - 1, 0), last = min(ze, m - 1);
+    const int Yb = (p0 - 1 + R) / R - 1;
+    const int p = p0 + (int)threadIdx.x, y = p / R, xl = p % R - 1;
+    const bool own = epi && p < m * R && xl >= 0 && xl < W && x0 + xl < m;
+    const long long v0 = (x0 + xl) + (long long)m * y;
+    auto stage = [&](int z) {
+      const int sl = z % kTcSlots;
+      const uint32_t fb = s_full + 8u * (uint32_t)sl, dst = sA0 + (uint32_t)sl * 2u * H;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(box_bytes) : "memory");
+      tma_load5(dst, &map, 0, 0, x0 - 1, Yb - 1, z, fb);
+      tma_load5(dst + H, &map, 0, 1, x0 - 1, Yb - 1, z, fb);
+      fpend |= 1u << sl;
+    };
+    if (epi) {
+      for (int c = 0; c < ze - zb; ++c) tc_st16_zero(lanes + 16u * (uint32_t)c);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    if (issuer) {
+      stage(first);
+      if (first + 1 <= last) stage(first + 1);
+    }
+    sync_or(false);
     for (int zi = first; zi <= last; ++zi, ++k) {
-      if (threadIdx.x == 0) {
-        const int olo = max(zi - 1, zb), ohi = min(zi + 1, ze - 1), blo = 1 - zi + olo;
-        const uint32_t idesc = tc_idesc(16 * (ohi - olo + 1)), acc = tmem + 16u * (uint32_t)(olo - zb);
-        const uint32_t sa = smem_u32(slot(zi)), sb = smem_u32(sB) + 256u * (uint32_t)blo;
-        for (int s = 0; s < 9; ++s) {
-          const int dx = s % 3 - 1, dy = s / 3 - 1;
-          const int j0 = R + 1 + dx + dy * R;  // rows j0 .. j0 + 127 < L of plane zi
-          tc_mma(acc, tc_desc(sa + (uint32_t)j0 * 16u, (uint32_t)(L * 16), 128u),
-                 tc_desc(sb + 1536u * (uint32_t)s, 768u, 128u), true, idesc);
+      bool fail = false;
+      if (issuer) {
+        const int sl = zi % kTcSlots;
+        fail = !tc_wait(s_full + 8u * (uint32_t)sl, (fpar >> sl) & 1u);
+        fpar ^= 1u << sl;
+        fpend &= ~(1u << sl);
+        if (!fail) {
+          const int olo = max(zi - 1, zb), ohi = min(zi + 1, ze - 1), blo = 1 - zi + olo;
+          const uint32_t idesc = tc_idesc(16 * (ohi - olo + 1)), acc = tmem + 16u * (uint32_t)(olo - zb);
+          const uint64_t da = tc_desc(sA0 + (uint32_t)sl * 2u * H + (uint32_t)(p0 + R - Yb * R) * 16u, H, 128u);
+          const uint64_t db = tc_desc(sB0 + 256u * (uint32_t)blo, 768u, 128u);
+#pragma unroll
+          for (int s = 0; s < 9; ++s) {
+            const int dx = s % 3 - 1, dy = s / 3 - 1;
+            tc_mma(acc, da + (uint64_t)(long long)(dx + dy * R), db + (uint64_t)(96 * s), true, idesc);
+          }
+          tc_commit(s_done + 8u * (k & 1u));
+          kc = k + 1;
+          if (zi + 2 <= last) {
+            if (zi > first) fail = !plane_done(k - 1);
+            if (!fail) stage(zi + 2);
+          }
         }
-        tc_commit(s_bar0 + 8u * (k & 1u));
       }
-      // plane zi - 1's MMAs done: output zi - 2 is complete and the slot of plane zi - 1 takes
-      // plane zi + kTcSlots - 1
-      if (zi > first && !wait_plane(k - 1)) {
-        timed_out = true;
-        break;
+      if (epi && zi > first) {
+        const int o = zi - 2;
+        const bool emit = o >= zb && own;
+        uint4 ad[2], mk[2];
+        if (emit) tc_load_addmask(a, v0 + (long long)m * m * o, ad, mk);
+        fail = !wait_plane(k - 1);
+        if (!fail && o >= zb) {
+          uint32_t r[16];
+          tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
+          if (emit) tc_emit(a, v0 + (long long)m * m * o, nvox, r, sbias, ad, mk);
+        }
       }
-      if (zi + kTcSlots - 1 <= last)
-        tc_stage_async(a.in, m, R, L, p0 - 1, 1, 1, zi + kTcSlots - 1, slot(zi + kTcSlots - 1));
-      if (zi > first && zi - 2 >= zb) finish(p0, zb, zi - 2);
-      // plane zi + 1 has landed; the planes staged after it may still be in flight
-      cp_async_wait_upto(min(kTcSlots - 2, last - zi - 1));
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_sync();
+      if (sync_or(fail)) { timed_out = true; break; }
     }
     if (!timed_out) {
-      if (!wait_plane(k - 1)) {
-        timed_out = true;
-      } else {
-        for (int o = max(zb, last - 1); o < ze; ++o) finish(p0, zb, o);
+      bool fail = false;
+      if (epi) {
+        fail = !wait_plane(k - 1);
+        for (int o = max(zb, last - 1); o < ze && !fail; ++o) {
+          uint32_t r[16];
+          tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
+          if (own) {
+            uint4 ad[2], mk[2];
+            tc_load_addmask(a, v0 + (long long)m * m * o, ad, mk);
+            tc_emit(a, v0 + (long long)m * m * o, nvox, r, sbias, ad, mk);
+          }
+        }
       }
+      if (sync_or(fail)) timed_out = true;
     }
-    tc_sync();
   }
-  cp_async_wait_all();
+  if (issuer && timed_out) {
+    for (int sl = 0; sl < kTcSlots; ++sl)
+      if (fpend & (1u << sl)) tc_wait(s_full + 8u * (uint32_t)sl, (fpar >> sl) & 1u);
+    if (kc > 0) plane_done(kc - 1);
+  }
   tc_teardown(tmem, kTcSCols, timed_out, status);
 }
 
@@ -745,7 +829,7 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
   for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(mi, zb + zc);
     // staged row j of a plane is coarse position p0 + j = y R + x
-    for (int pl = zb; pl <= zb + 1; ++pl) tc_stage_async(a.in, mi, R, L, p0, 0, 0, pl, slot(pl));
+    for (int pl = zb; pl <= zb + 1; ++pl) tc_stage_async(a.in, mi, R, L, p0, 0, 0, pl, slot(pl), threadIdx.x, blockDim.x);
     cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
@@ -770,7 +854,7 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
         tc_commit(s_bar);
       }
       // plane cz + 2 goes to the slot of plane cz - 1; the copy runs during the MMAs and the epilogue
-      if (cz + 1 < ze) tc_stage_async(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2));
+      if (cz + 1 < ze) tc_stage_async(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2), threadIdx.x, blockDim.x);
       const bool done = tc_wait(s_bar, phase);
       phase ^= 1u;
       timed_out = __syncthreads_or(!done) != 0;
@@ -782,8 +866,12 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
         const int qx = cl & 1, qy = (cl >> 1) & 1, qz = cl >> 2;
         uint32_t r[16];
         tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + (uint32_t)(16 * cl), r);
-        if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1))
-          tc_emit(a, (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz)), nvox, r, a.bias);
+        if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1)) {
+          const long long v = (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz));
+          uint4 ad[2], mk[2];
+          tc_load_addmask(a, v, ad, mk);
+          tc_emit(a, v, nvox, r, a.bias, ad, mk);
+        }
       }
       cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -850,13 +938,13 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
     const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
     // planes z - 1 .. z + 1 of Q and the P rows of plane z are in shared memory when tile z
     // starts; plane z + 2 and the rows of plane z + 1 are copied while tile z computes
-    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, pl, slot(pl));
+    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, pl, slot(pl), threadIdx.x, blockDim.x);
     wg_stage_rows_async(P, m, R, p0, zb, sP0 + (tt & 1u) * 4096);
     cp_async_wait_all();
     __syncthreads();
     for (int z = zb; z < ze; ++z, ++tt) {
       if (z + 1 < ze) {
-        tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2));
+        tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2), threadIdx.x, blockDim.x);
         wg_stage_rows_async(P, m, R, p0, z + 1, sP0 + ((tt + 1) & 1u) * 4096);
       }
       const uint32_t sp = smem_u32(sP0 + (tt & 1u) * 4096);
@@ -917,13 +1005,58 @@ void up_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   k_up_tc<<<(int)std::min<long long>(nunits, 4 * 152), kTcThreads, smem, s>>>(a, zc, status);
 }
 
+typedef CUresult (*TensorMapEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                         CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// The driver's tiled tensor-map encoder, looked up once (null if the driver lacks it).
+TensorMapEncodeTiled tensor_map_encoder() {
+  static const TensorMapEncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (TensorMapEncodeTiled) nullptr;
+    return reinterpret_cast<TensorMapEncodeTiled>(p);
+  }();
+  return fn;
+}
+__global__ void k_flag(unsigned* status, unsigned bit) { atomicOr(status, bit); }
+
+// A stride-1 convolution: the tensor map of the input (boxes of NY padded rows of one channel
+// half), then the streaming kernel on 4 blocks per SM (or fewer if shared memory limits it).
 void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
-  const size_t smem = conv_tc_smem(a.m_out);
+  const int m = a.m_out;
+  int nstrips = 0;
+  const int W = conv_strip_width(m, &nstrips), R = W + 2;
+  CUtensorMap map;
+  const TensorMapEncodeTiled enc = tensor_map_encoder();
+  const cuuint64_t dims[5] = {8, 2, (cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)m};
+  const cuuint64_t strides[4] = {16, 32, 32ull * (cuuint64_t)m, 32ull * (cuuint64_t)m * (cuuint64_t)m};
+  const cuuint32_t box[5] = {8, 1, (cuuint32_t)R, (cuuint32_t)tma_ny(R), 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (!enc || enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(a.in), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    k_flag<<<1, 1, 0, s>>>(status, kStatusTmaSetup);
+    return;
+  }
+  const size_t smem = conv_tc_smem(m);
   cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long long m = a.m_out, per_plane = (m * (m + 2) + 127) / 128;
-  const int zc = tc_column(per_plane, (int)m);
-  const long long nunits = per_plane * ((m + zc - 1) / zc);
-  k_conv_tc<<<(int)std::min<long long>(nunits, kTcSBlocksPerSM * 152), kTcThreads, smem, s>>>(a, zc, status);
+  cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const long long per_plane = ((long long)m * R + 127) / 128;
+  const int zc = tc_column(per_plane * nstrips, m);
+  const long long nunits = per_plane * nstrips * ((m + zc - 1) / zc);
+  static int nsm = 0, smem_sm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm = std::max(nsm, 1);
+  }
+  const int per_sm = std::max(1, std::min(4, smem_sm / (int)(smem + 1024)));
+  k_conv_tc<<<(int)std::min<long long>(nunits, (long long)per_sm * nsm), kTcSThreads, smem, s>>>(a, map, zc, W, nstrips,
+                                                                                                  status);
 }
 
 // out = act(conv_G(in; w) + bias + add) * mask
@@ -1315,6 +1448,7 @@ nhmf_status nhmf_unet_loss_grad(nhmf_ctx* c, const float* x, const float* e, dou
   if (st == NHMF_OK && grads_host)
     st = cuda_check(c, cudaMemcpyAsync(grads_host, u.grads, u.nparams * sizeof(float), cudaMemcpyDeviceToHost, s), "grad read");
   if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "loss_grad sync");
+  if (st == NHMF_OK) st = nhmf_check_status(c, stream);  // tensor-core waits and tensor maps
   *loss = nd[1] > 0.0 ? nd[0] / nd[1] : 0.0;
   return st;
 }
@@ -1355,6 +1489,7 @@ nhmf_status nhmf_unet_train(nhmf_ctx* c, int epochs, double lr, double* loss_fir
     double acc = 0.0;
     nhmf_status st = cuda_check(c, cudaMemcpyAsync(&acc, u.sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s), "train loss");
     if (st == NHMF_OK) st = cuda_check(c, cudaStreamSynchronize(s), "train sync");
+    if (st == NHMF_OK) st = nhmf_check_status(c, stream);  // tensor-core waits and tensor maps
     if (st != NHMF_OK) return st;
     if (!std::isfinite(acc)) return fail(c, NHMF_ERR_NONFINITE, "unet_train: non-finite loss");
     if (ep == 0) *loss_first = acc / u.npairs;
