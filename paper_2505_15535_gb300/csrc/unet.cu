@@ -203,12 +203,23 @@ __global__ void __launch_bounds__(288) k_wgrad(const __nv_bfloat16* P, int mp, c
 
 // Sum the partials in block order and write the layer's weight gradient in the flat layout:
 // conv/down W[o][c][tap] (a = o, b = c); up U[c][o][tap] (a = c, b = o).
-__global__ void k_wgrad_reduce(const float* partial, int nblocks, float* grad_w, int kind, int cin, int cout) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 27 * 256) return;
-  const int tap = idx / 256, aa = (idx / 16) % 16, bb = idx % 16;
+// Sum of the per-block weight-gradient partials [nblocks][27 * 256], in a fixed order: a block
+// takes 32 consecutive entries, its 8 warps sum every eighth partial block (coalesced rows),
+// and one warp adds the 8 sums.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* partial, int nblocks, float* grad_w, int kind,
+                                                      int cin, int cout) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 32 + tx;  // gridDim.x = 27 * 256 / 32
   float s = 0.f;
-  for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * 27 * 256 + idx];
+  for (int b = ty; b < nblocks; b += 8) s += partial[(long long)b * 27 * 256 + idx];
+  __shared__ float sh[8][33];
+  sh[ty][tx] = s;
+  __syncthreads();
+  if (ty != 0) return;
+  s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += sh[j][tx];
+  const int tap = idx / 256, aa = (idx / 16) % 16, bb = idx % 16;
   if (kind == UP) {
     if (aa < cin && bb < cout) grad_w[((long long)aa * cout + bb) * 27 + tap] = s;
   } else {
@@ -217,27 +228,58 @@ __global__ void k_wgrad_reduce(const float* partial, int nblocks, float* grad_w,
 }
 
 // Bias gradient: per-block channel sums of P, then a fixed-order reduction.
+// Per-block channel sums of P [voxel][16] (the bias gradient's partials): a thread adds whole
+// 32-byte voxel rows, then the block adds its threads' sums in a fixed order.
 __global__ void __launch_bounds__(256) k_bgrad_partial(const __nv_bfloat16* P, long long nvox, float* partial) {
-  const int ch = threadIdx.x & 15, lanegrp = threadIdx.x >> 4;  // 16 voxel lanes x 16 channels
-  float s = 0.f;
-  for (long long v = (long long)blockIdx.x * 16 + lanegrp; v < nvox; v += (long long)gridDim.x * 16)
-    s += __bfloat162float(P[v * kC + ch]);
-  __shared__ float sh[256];
-  sh[threadIdx.x] = s;
+  float s[16];
+#pragma unroll
+  for (int ch = 0; ch < 16; ++ch) s[ch] = 0.f;
+  for (long long v = (long long)blockIdx.x * 256 + threadIdx.x; v < nvox; v += (long long)gridDim.x * 256) {
+    const uint4* src = reinterpret_cast<const uint4*>(P + v * kC);
+    const uint4 q0 = src[0], q1 = src[1];
+    const uint32_t q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162*>(&q[h]);
+      s[2 * h] += __low2float(x2);
+      s[2 * h + 1] += __high2float(x2);
+    }
+  }
+  __shared__ float sh[16][257];
+#pragma unroll
+  for (int ch = 0; ch < 16; ++ch) sh[ch][threadIdx.x] = s[ch];
+  __syncthreads();
+  __shared__ float sh2[16][17];
+  {
+    const int ch = threadIdx.x & 15, g = threadIdx.x >> 4;  // 16 groups of 16 threads
+    float r = 0.f;
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r += sh[ch][g * 16 + l];
+    sh2[g][ch] = r;
+  }
   __syncthreads();
   if (threadIdx.x < 16) {
     float r = 0.f;
-    for (int l = 0; l < 16; ++l) r += sh[l * 16 + threadIdx.x];
+#pragma unroll
+    for (int g = 0; g < 16; ++g) r += sh2[g][threadIdx.x];
     partial[blockIdx.x * 16 + threadIdx.x] = r;
   }
 }
 
-__global__ void k_bgrad_reduce(const float* partial, int nblocks, float* grad_b, int cout) {
-  const int ch = threadIdx.x;
-  if (ch >= cout) return;
-  float s = 0.f;
-  for (int b = 0; b < nblocks; ++b) s += partial[b * 16 + ch];
-  grad_b[ch] = s;
+// grad_b[ch] = sum over the partial blocks, in a fixed order (one block of 256 threads).
+__global__ void __launch_bounds__(256) k_bgrad_reduce(const float* partial, int nblocks, float* grad_b, int cout) {
+  const int ch = threadIdx.x & 15, g = threadIdx.x >> 4;
+  float r = 0.f;
+  for (int b = g; b < nblocks; b += 16) r += partial[b * 16 + ch];
+  __shared__ float sh[16][17];
+  sh[g][ch] = r;
+  __syncthreads();
+  if (threadIdx.x < 16 && threadIdx.x < cout) {
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) t += sh[j][threadIdx.x];
+    grad_b[threadIdx.x] = t;
+  }
 }
 
 // Forward and backward-data BF16 weights of one layer from the FP32 master weights.
@@ -273,7 +315,8 @@ __global__ void k_adam(long long n, float* p, const float* g, float* m, float* v
 }
 
 __device__ __forceinline__ bool constrained_dof(int bc, int c, long long v, int M) {
-  const int i = int(v % M), k = int(v / ((long long)M * M));
+  const int vv = (int)v;  // grids of at most 785^3 nodes
+  const int i = vv % M, k = vv / (M * M);
   if (bc == NHMF_BC_CLAMP_X0) return i == 0;
   if (bc == NHMF_BC_COMPRESSION) return k == 0 || (c == 2 && k == M - 1);
   return false;
@@ -299,12 +342,17 @@ __global__ void k_input(const TS* src, long long n, const double* den, double mu
 __global__ void __launch_bounds__(kRedThreads) k_loss_partials(const float* y, const float* e, long long n, int bc,
                                                                int M, double* partials) {
   double num = 0.0, den = 0.0;
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < 3 * n; i += (long long)kRedBlocks * kRedThreads) {
-    const int c = int(i / n);
-    if (constrained_dof(bc, c, i % n, M)) continue;
-    const double d = double(y[i]) - double(e[i]);
-    num += d * d;
-    den += double(e[i]) * double(e[i]);
+  const int nn = (int)n, MM = M * M;  // grids of at most 785^3 nodes
+  for (int v = blockIdx.x * kRedThreads + threadIdx.x; v < nn; v += kRedBlocks * kRedThreads) {
+    const int i = v % M, k = v / MM;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const bool fixed = bc == NHMF_BC_CLAMP_X0 ? i == 0 : bc == NHMF_BC_COMPRESSION && (k == 0 || (c == 2 && k == M - 1));
+      if (fixed) continue;
+      const double ev = double(e[(long long)c * n + v]), d = double(y[(long long)c * n + v]) - ev;
+      num += d * d;
+      den += ev * ev;
+    }
   }
   __shared__ double sh[2][kRedThreads / 32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -327,16 +375,30 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_partials(const float* y, c
   }
 }
 
-__global__ void k_loss_final(const double* partials, double* num, double* den, double* loss_acc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Sums of the kRedBlocks loss partials in a fixed order (one block of kRedThreads threads).
+__global__ void __launch_bounds__(kRedThreads) k_loss_final(const double* partials, double* num, double* den,
+                                                            double* loss_acc) {
   double a = 0.0, b = 0.0;
-  for (int i = 0; i < kRedBlocks; ++i) {
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) {
     a += partials[i];
     b += partials[kRedBlocks + i];
   }
-  *num = a;
-  *den = b;
-  if (loss_acc) *loss_acc += b > 0.0 ? a / b : 0.0;
+  __shared__ double sh[2][kRedThreads];
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int st = kRedThreads / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *num = sh[0][0];
+    *den = sh[1][0];
+    if (loss_acc) *loss_acc += sh[1][0] > 0.0 ? sh[0][0] / sh[1][0] : 0.0;
+  }
 }
 
 // dy16[v][c] = 2 f (y - e) / den for c < 3, 0 otherwise.
@@ -1088,14 +1150,14 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
     k_wgrad<DOWN2><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
   }
   const UNetLayer& L = u.L[layer];
-  k_wgrad_reduce<<<(27 * 256 + 255) / 256, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
+  k_wgrad_reduce<<<27 * 256 / 32, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
 }
 
 void bgrad(UNet& u, int layer, const __nv_bfloat16* P, long long nvox, cudaStream_t s) {
   const int blocks = 256;
   float* part = u.partial + (long long)kWgBlocks * 27 * 256;
   k_bgrad_partial<<<blocks, 256, 0, s>>>(P, nvox, part);
-  k_bgrad_reduce<<<1, 32, 0, s>>>(part, blocks, u.grads + u.L[layer].boff, u.L[layer].cout);
+  k_bgrad_reduce<<<1, 256, 0, s>>>(part, blocks, u.grads + u.L[layer].boff, u.L[layer].cout);
 }
 
 }  // namespace
@@ -1252,7 +1314,7 @@ void unet_loss_and_grad(nhmf_ctx* c, const float* target, bool accumulate, cudaS
   UNet& u = *c->unet;
   double* partials = c->work->partials;
   k_loss_partials<<<kRedBlocks, kRedThreads, 0, s>>>(u.y, target, u.N0, c->prm.bc, u.M0, partials);
-  k_loss_final<<<1, 32, 0, s>>>(partials, u.sc + 1, u.sc + 2, accumulate ? u.sc + 3 : nullptr);
+  k_loss_final<<<1, kRedThreads, 0, s>>>(partials, u.sc + 1, u.sc + 2, accumulate ? u.sc + 3 : nullptr);
   k_loss_grad<<<kConvBlocks, 256, 0, s>>>(u.y, target, u.N0, c->prm.bc, u.M0, u.sc + 2, u.g0a);
 }
 
