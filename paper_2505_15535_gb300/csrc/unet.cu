@@ -12,7 +12,7 @@
 //   stride-1 forward/backward-data (k_conv_tc) and the transposed stride-2 convolution
 //   (k_up_tc): tcgen05 MMAs with accumulators in tensor memory, M = 128 positions, K = 16
 //   input channels, N = output channels (stacked over dz in the stride-1 form);
-//   stride-2 down-convolution (k_conv) and weight gradients (k_wgrad, k_wgrad_s1): mma.sync
+//   stride-2 down-convolution (k_conv) and weight gradients (k_wgrad_s1, k_wgrad_s2): mma.sync
 //   m16n8k16; weight gradients as partial sums per block, reduced in a fixed order.
 #include <cuda.h>  // CUtensorMap and the encoder's types; the encoder itself comes from the driver at run time
 #include <cuda_bf16.h>
@@ -149,63 +149,10 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
   }
 }
 
-// Weight gradient G[tap][a][b] = sum_v P[v][a] Q[src(v, tap)][b] over the P grid, for the
-// gathers S1 and DOWN2; 9 warps, warp w owns taps 3w..3w+2; per-block partials.
-template <int G>
-__global__ void __launch_bounds__(288) k_wgrad(const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
-                                               float* partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const long long m = mp, nvox = m * m * m, nks = (nvox + 15) / 16;
-  float acc[3][2][4] = {};
-  for (long long ks = blockIdx.x; ks < nks; ks += gridDim.x) {
-    const long long kb = ks * 16;
-    const long long vv[4] = {kb + 2 * t, kb + 2 * t + 1, kb + 8 + 2 * t, kb + 9 + 2 * t};
-    int ci[4], cj[4], ck[4];
-    bool ok[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ok[q] = vv[q] < nvox;
-      ci[q] = int(vv[q] % m);
-      cj[q] = int((vv[q] / m) % m);
-      ck[q] = int(vv[q] / (m * m));
-    }
-    const __nv_bfloat16 z = __float2bfloat16(0.f);
-    auto p = [&](int q, int ch) { return ok[q] ? P[vv[q] * kC + ch] : z; };
-    const uint32_t A0 = pack_bf16(p(0, g), p(1, g)), A1 = pack_bf16(p(0, g + 8), p(1, g + 8));
-    const uint32_t A2 = pack_bf16(p(2, g), p(3, g)), A3 = pack_bf16(p(2, g + 8), p(3, g + 8));
-#pragma unroll
-    for (int jt = 0; jt < 3; ++jt) {
-      const int tap = 3 * warp + jt;
-      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
-      long long s[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s[q] = ok[q] ? src_voxel<G>(ci[q], cj[q], ck[q], dx, dy, dz, mq) : -1;
-      auto qv = [&](int q, int ch) { return s[q] >= 0 ? Q[s[q] * kC + ch] : z; };
-      mma16816(acc[jt][0], A0, A1, A2, A3, pack_bf16(qv(0, g), qv(1, g)), pack_bf16(qv(2, g), qv(3, g)));
-      mma16816(acc[jt][1], A0, A1, A2, A3, pack_bf16(qv(0, g + 8), qv(1, g + 8)),
-               pack_bf16(qv(2, g + 8), qv(3, g + 8)));
-    }
-  }
-  float* out = partial + (long long)blockIdx.x * 27 * 256;
-#pragma unroll
-  for (int jt = 0; jt < 3; ++jt) {
-    const int tap = 3 * warp + jt;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int b = 8 * h + 2 * t;
-      out[tap * 256 + g * 16 + b] = acc[jt][h][0];
-      out[tap * 256 + g * 16 + b + 1] = acc[jt][h][1];
-      out[tap * 256 + (g + 8) * 16 + b] = acc[jt][h][2];
-      out[tap * 256 + (g + 8) * 16 + b + 1] = acc[jt][h][3];
-    }
-  }
-}
-
-// Sum the partials in block order and write the layer's weight gradient in the flat layout:
-// conv/down W[o][c][tap] (a = o, b = c); up U[c][o][tap] (a = c, b = o).
-// Sum of the per-block weight-gradient partials [nblocks][27 * 256], in a fixed order: a block
-// takes 32 consecutive entries, its 8 warps sum every eighth partial block (coalesced rows),
-// and one warp adds the 8 sums.
+// Sum of the per-block weight-gradient partials [nblocks][27 * 256] in a fixed order (a block
+// takes 32 consecutive entries, its 8 warps sum every eighth partial block - coalesced rows -
+// and one warp adds the 8 sums), written in the flat layout: conv/down W[o][c][tap] (a = o,
+// b = c); up U[c][o][tap] (a = c, b = o).
 __global__ void __launch_bounds__(256) k_wgrad_reduce(const float* partial, int nblocks, float* grad_w, int kind,
                                                       int cin, int cout) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -951,7 +898,7 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
 // that every 8 x 8 block of a fragment is one ldmatrix: per chunk of 16 positions one
 // ldmatrix.x4.trans gives the A fragment (P^T, channels a x positions) for all the warp's
 // taps, and one per tap gives the B fragments (positions x channels b) of both n-tiles.
-// 9 warps, warp w owns taps 3w..3w+2; per-block partials as in k_wgrad.
+// 9 warps, warp w owns taps 3w..3w+2; per-block partials reduced by k_wgrad_reduce.
 constexpr int kWgThreads = 288;
 
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
@@ -1023,6 +970,128 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
           uint32_t b0, b1, b2, b3;
           ldsm_x4_trans(smem_u32(slot(z + dz)) + (uint32_t)(((lm >> 1) * L + row + (lm & 1) * 8 + lr) * 16), b0, b1,
                         b2, b3);
+          mma16816(acc[jt][0], a0, a1, a2, a3, b0, b1);
+          mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+  float* out = partial + (long long)blockIdx.x * 27 * 256;
+#pragma unroll
+  for (int jt = 0; jt < 3; ++jt) {
+    const int tap = 3 * warp + jt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = 8 * h + 2 * t;
+      out[tap * 256 + g * 16 + b] = acc[jt][h][0];
+      out[tap * 256 + g * 16 + b + 1] = acc[jt][h][1];
+      out[tap * 256 + (g + 8) * 16 + b] = acc[jt][h][2];
+      out[tap * 256 + (g + 8) * 16 + b + 1] = acc[jt][h][3];
+    }
+  }
+}
+
+// Weight gradient of the stride-2 gather (the down-convolution), tiled like k_wgrad_s1:
+// G[tap][a][b] = sum_v P[v][a] Q[2 v + d_tap][b] over the coarse grid (Q on the fine grid,
+// zero outside it).  A unit is a segment of `seg` coarse voxels (a multiple of 16, zero past
+// the grid) of one coarse row cy, along a column of zc coarse planes.  Per coarse plane cz it
+// stages the segment's P rows and, of fine planes 2 cz - 1 .. 2 cz + 1, the fine rows 2 cy - 1
+// .. 2 cy + 1 over fine x 2 x0 - 1 .. 2 (x0 + seg) - 1 (Wf = 2 seg + 1 positions per row), as
+// 16-byte channel halves, in a ring of five fine-plane slots: the two fine planes of the next
+// coarse plane and its P rows are copied while this one computes.  The A fragment (P^T) comes
+// from ldmatrix.trans as in k_wgrad_s1; the B rows of position k and tap (dx, dy) are the
+// staged fine voxels 2 k + dx + 1 of row dy + 1, one ldmatrix row address per lane.
+constexpr int kW2Seg = 80;     // widest segment
+constexpr int kW2Slots = 5;
+
+int wgrad_s2_seg(int mp, int* nseg) {
+  *nseg = (mp + kW2Seg - 1) / kW2Seg;
+  return ((mp + *nseg - 1) / *nseg + 15) / 16 * 16;
+}
+size_t wgrad_s2_smem(int seg) { return 2 * 2 * (size_t)seg * 16 + kW2Slots * 2 * 3 * (size_t)(2 * seg + 1) * 16; }
+
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __restrict__ P, int mp,
+                                                         const __nv_bfloat16* __restrict__ Q, int mq, int seg,
+                                                         int nseg, int zc, float* partial) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int Wf = 2 * seg + 1, hs = 3 * Wf * 16;  // bytes per staged fine half
+  unsigned char* sP0 = sm;                        // [2 buffers][2 halves][seg][16 B]
+  unsigned char* sQ = sm + 2 * 2 * seg * 16;      // [kW2Slots][2 halves][3 rows][Wf][16 B]
+  auto slot = [&](int f) { return sQ + ((f + kW2Slots) % kW2Slots) * 2 * hs; };  // fine plane f >= -1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int lm = lane >> 3, lr = lane & 7;
+  const uint4* qg = reinterpret_cast<const uint4*>(Q);
+  const uint4* pg = reinterpret_cast<const uint4*>(P);
+  const int nzc = (mp + zc - 1) / zc;
+  const long long nunits = (long long)mp * nseg * nzc;
+  float acc[3][2][4] = {};
+  unsigned tt = 0;  // coarse planes done by this block; the P rows of plane tt are in buffer tt & 1
+  // fine rows 2 cy - 1 .. 2 cy + 1 of fine plane f over fine x 2 x0 - 1 .. 2 x0 + 2 seg - 1
+  auto stage_fine = [&](int f, int cy, int x0) {
+    const uint32_t d = smem_u32(slot(f));
+    const bool fin = f >= 0 && f < mq;
+    for (int r = 0; r < 3; ++r) {
+      const int fy = 2 * cy - 1 + r;
+      for (int i = threadIdx.x; i < Wf; i += blockDim.x) {
+        const int fx = 2 * x0 - 1 + i;
+        const uint4* src = qg;
+        uint32_t bytes = 0;
+        if (fin && fy >= 0 && fy < mq && fx >= 0 && fx < mq) {
+          src = qg + 2 * (fx + (long long)mq * (fy + (long long)mq * f));
+          bytes = 16;
+        }
+        cp_async16(d + (uint32_t)(r * Wf + i) * 16u, src, bytes);
+        cp_async16(d + (uint32_t)hs + (uint32_t)(r * Wf + i) * 16u, src + 1, bytes);
+      }
+    }
+  };
+  // P rows of coarse voxels (x0 + k, cy, cz), k < seg, zero past the grid
+  auto stage_p = [&](int cz, int cy, int x0, unsigned char* buf) {
+    const uint32_t d = smem_u32(buf);
+    for (int k = threadIdx.x; k < seg; k += blockDim.x) {
+      const uint4* src = pg;
+      uint32_t bytes = 0;
+      if (x0 + k < mp) {
+        src = pg + 2 * ((x0 + k) + (long long)mp * (cy + (long long)mp * cz));
+        bytes = 16;
+      }
+      cp_async16(d + (uint32_t)k * 16u, src, bytes);
+      cp_async16(d + (uint32_t)(seg + k) * 16u, src + 1, bytes);
+    }
+  };
+  for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int cy = int(unit % mp);
+    const long long rest = unit / mp;
+    const int x0 = int(rest % nseg) * seg, zb = int(rest / nseg) * zc, ze = min(mp, zb + zc);
+    for (int f = 2 * zb - 1; f <= 2 * zb + 1; ++f) stage_fine(f, cy, x0);
+    stage_p(zb, cy, x0, sP0 + (tt & 1u) * 2 * seg * 16);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    cp_async_wait_all();
+    __syncthreads();
+    for (int cz = zb; cz < ze; ++cz, ++tt) {
+      if (cz + 1 < ze) {  // fine planes 2 cz + 2, 2 cz + 3 take the slots of 2 cz - 3, 2 cz - 2
+        stage_fine(2 * cz + 2, cy, x0);
+        stage_fine(2 * cz + 3, cy, x0);
+        stage_p(cz + 1, cy, x0, sP0 + ((tt + 1) & 1u) * 2 * seg * 16);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      const uint32_t sp = smem_u32(sP0 + (tt & 1u) * 2 * seg * 16);
+      for (int c = 0; c < seg / 16; ++c) {
+        // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * seg + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
+        const int k = 16 * c + (lm & 1) * 8 + lr;  // this lane's B row: position k, channel half lm >> 1
+#pragma unroll
+        for (int jt = 0; jt < 3; ++jt) {
+          const int tap = 3 * warp + jt;
+          const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+          // B: matrices (k 0-7, b lo), (k 8-15, b lo), (k 0-7, b hi), (k 8-15, b hi)
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4_trans(smem_u32(slot(2 * cz + dz)) +
+                            (uint32_t)((lm >> 1) * hs + ((dy + 1) * Wf + 2 * k + dx + 1) * 16),
+                        b0, b1, b2, b3);
           mma16816(acc[jt][0], a0, a1, a2, a3, b0, b1);
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
@@ -1144,10 +1213,15 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
     const int zc = tc_column(per_plane, mp);
     blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
     k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, u.partial);
-  } else {
-    const long long nks = ((long long)mp * mp * mp + 15) / 16;
-    blocks = (int)std::min<long long>(kWgBlocks, nks);
-    k_wgrad<DOWN2><<<blocks, 288, 0, s>>>(P, mp, Q, mq, u.partial);
+  } else {  // stride 2: P on the coarse grid, Q on the fine grid
+    int nseg = 0;
+    const int seg = wgrad_s2_seg(mp, &nseg);
+    const size_t smem = wgrad_s2_smem(seg);
+    cudaFuncSetAttribute(k_wgrad_s2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long per_plane = (long long)mp * nseg;
+    const int zc = (int)std::max<long long>(1, std::min<long long>(kTcZ, per_plane * mp / kTcUnits));
+    blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
+    k_wgrad_s2<<<blocks, kWgThreads, smem, s>>>(P, mp, Q, mq, seg, nseg, zc, u.partial);
   }
   const UNetLayer& L = u.L[layer];
   k_wgrad_reduce<<<27 * 256 / 32, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
