@@ -33,6 +33,7 @@ enum Gather { S1 = 0, DOWN2 = 1, UP2 = 2 };
 enum Kind { CONV = 0, DOWN = 1, UP = 2 };
 constexpr int kConvBlocks = 1216;  // 8 per SM
 constexpr int kWgBlocks = 608;     // weight-gradient partial blocks (4 per SM)
+constexpr int kBgBlocks = 1216;    // bias-gradient partial blocks (8 per SM)
 
 __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
@@ -150,22 +151,37 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
 }
 
 // Sum of the per-block weight-gradient partials [nblocks][27 * 256] in a fixed order (a block
-// takes 32 consecutive entries, its 8 warps sum every eighth partial block - coalesced rows -
-// and one warp adds the 8 sums), written in the flat layout: conv/down W[o][c][tap] (a = o,
-// b = c); up U[c][o][tap] (a = c, b = o).
-__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* partial, int nblocks, float* grad_w, int kind,
-                                                      int cin, int cout) {
+// takes 32 consecutive entries, its 32 warps sum every 32nd partial block - coalesced rows -
+// and one warp adds the 32 sums), written in the flat layout: conv/down W[o][c][tap] (a = o,
+// b = c); up U[c][o][tap] (a = c, b = o).  With grad_b, one more block sums the per-block bias
+// partials [nblocks][16] the same way.
+__global__ void __launch_bounds__(1024) k_wgrad_reduce(const float* partial, const float* bpartial, int nblocks,
+                                                       float* grad_w, float* grad_b, int kind, int cin, int cout) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int idx = blockIdx.x * 32 + tx;  // gridDim.x = 27 * 256 / 32
+  __shared__ float sh[32][33];
+  if (blockIdx.x == 27 * 256 / 32) {  // the bias block
+    const int ch = threadIdx.x & 15, g = threadIdx.x >> 4;  // 64 groups of 16 channels
+    float s = 0.f;
+    for (int b = g; b < nblocks; b += 64) s += bpartial[b * 16 + ch];
+    float* flat = &sh[0][0];
+    flat[g * 16 + ch] = s;
+    __syncthreads();
+    if (threadIdx.x < 16 && threadIdx.x < cout) {
+      float t = 0.f;
+      for (int j = 0; j < 64; ++j) t += flat[j * 16 + threadIdx.x];
+      grad_b[threadIdx.x] = t;
+    }
+    return;
+  }
+  const int idx = blockIdx.x * 32 + tx;
   float s = 0.f;
-  for (int b = ty; b < nblocks; b += 8) s += partial[(long long)b * 27 * 256 + idx];
-  __shared__ float sh[8][33];
+  for (int b = ty; b < nblocks; b += 32) s += partial[(long long)b * 27 * 256 + idx];
   sh[ty][tx] = s;
   __syncthreads();
   if (ty != 0) return;
   s = 0.f;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) s += sh[j][tx];
+  for (int j = 0; j < 32; ++j) s += sh[j][tx];
   const int tap = idx / 256, aa = (idx / 16) % 16, bb = idx % 16;
   if (kind == UP) {
     if (aa < cin && bb < cout) grad_w[((long long)aa * cout + bb) * 27 + tap] = s;
@@ -815,21 +831,23 @@ constexpr int kUpCols = 128;
 constexpr size_t kUpSmemMin = 52 * 1024;  // at most 4 blocks (4 x 128 TMEM columns) per SM
 
 size_t up_tc_smem(int mi) {
-  const size_t need = 27 * 512 + 3 * 2 * (size_t)(129 + mi + 1) * 16 + 16;
+  const size_t need = 27 * 512 + 3 * 2 * (size_t)(129 + mi + 1) * 16 + 16 + 64;
   return std::max(need, kUpSmemMin);
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, unsigned* status) {
+__global__ void __launch_bounds__(kTcThreads, 4) k_up_tc(const ConvArgs a, int zc, unsigned* status) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int mi = a.m_in, mo = a.m_out, R = mi + 1, L = 129 + R;
   unsigned char* sB = sm;
   unsigned char* sA = sm + 27 * 512;                       // [3 slots][2 halves][L][16 B]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + 6 * L * 16);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  float* sbias = reinterpret_cast<float*>(bar + 2);        // [16]
   const uint32_t s_bar = smem_u32(bar);
   const int warp = threadIdx.x >> 5;
   auto slot = [&](int plane) { return sA + (plane % 3) * 2 * L * 16; };  // plane >= 0
-  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kUpCols);
+  if (threadIdx.x < 16) sbias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.f;
+  const uint32_t tmem = tc_setup(a.w, sB, tslot, s_bar, kUpCols);  // synchronises the block
 
   const int per_plane = (mi * R + 127) / 128, nzc = (mi + zc - 1) / zc;
   const long long nunits = (long long)per_plane * nzc, nvox = (long long)mo * mo * mo;
@@ -864,24 +882,55 @@ __global__ void __launch_bounds__(kTcThreads) k_up_tc(const ConvArgs a, int zc, 
       }
       // plane cz + 2 goes to the slot of plane cz - 1; the copy runs during the MMAs and the epilogue
       if (cz + 1 < ze) tc_stage_async(a.in, mi, R, L, p0, 0, 0, cz + 2, slot(cz + 2), threadIdx.x, blockDim.x);
-      const bool done = tc_wait(s_bar, phase);
+      // row threadIdx.x is coarse position p; its fine voxels are the 8 classes (qx, qy, qz).  The
+      // skip rows of classes 0-3 load while the MMAs run, those of 4-7 while 0-3 are written
+      // (the mask, in the backward pass, is read at the store)
+      const int p = p0 + threadIdx.x, y = p / R, x = p % R;
+      const bool ok = p < mi * R && x < mi;
+      auto fine = [&](int cl, long long& v) -> bool {
+        const int qx = cl & 1, qy = (cl >> 1) & 1, qz = cl >> 2;
+        v = (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz));
+        return ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1);
+      };
+      auto load_skip = [&](int cl, uint4 (&q)[2]) {
+        long long v;
+        q[0] = q[1] = make_uint4(0u, 0u, 0u, 0u);
+        if (a.add && fine(cl, v)) {
+          const uint4* src = reinterpret_cast<const uint4*>(a.add + v * kC);
+          q[0] = src[0];
+          q[1] = src[1];
+        }
+      };
+      auto store = [&](int cl, const uint4 (&q)[2]) {
+        uint32_t r[16];
+        tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + (uint32_t)(16 * cl), r);
+        long long v;
+        if (fine(cl, v)) {
+          uint4 mk[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+          if (a.mask) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.mask + v * kC);
+            mk[0] = src[0];
+            mk[1] = src[1];
+          }
+          tc_emit(a, v, nvox, r, sbias, q, mk);
+        }
+      };
+      uint4 pre[4][2];
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) load_skip(c4, pre[c4]);
+      bool done = true;
+      if (threadIdx.x == 0) done = tc_wait(s_bar, phase);
       phase ^= 1u;
       timed_out = __syncthreads_or(!done) != 0;
       if (timed_out) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int p = p0 + threadIdx.x, y = p / R, x = p % R;  // row threadIdx.x is coarse position p
-      const bool ok = p < mi * R && x < mi;
-      for (int cl = 0; cl < 8; ++cl) {
-        const int qx = cl & 1, qy = (cl >> 1) & 1, qz = cl >> 2;
-        uint32_t r[16];
-        tc_ld16(tmem + ((32u * (uint32_t)warp) << 16) + (uint32_t)(16 * cl), r);
-        if (ok && (!qx || x < mi - 1) && (!qy || y < mi - 1) && (!qz || cz < mi - 1)) {
-          const long long v = (2 * x + qx) + (long long)mo * ((2 * y + qy) + (long long)mo * (2 * cz + qz));
-          uint4 ad[2], mk[2];
-          tc_load_addmask(a, v, ad, mk);
-          tc_emit(a, v, nvox, r, a.bias, ad, mk);
-        }
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        store(c4, pre[c4]);
+        load_skip(c4 + 4, pre[c4]);
       }
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) store(c4 + 4, pre[c4]);
       cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_sync();
@@ -904,6 +953,32 @@ constexpr int kWgThreads = 288;
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+
+// Sum of channel threadIdx.x % 16 of the staged P rows r0 + 16 k (k = 0 .. n - 1, offset by
+// threadIdx.x / 16 * n) of a [2 halves][rows][16 B] buffer: the bias gradient's share of a tile.
+__device__ __forceinline__ float p_rows_sum(const unsigned char* buf, int rows, int r0, int n) {
+  const int ch = threadIdx.x & 15, part = threadIdx.x >> 4;
+  const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(buf + (ch >> 3) * rows * 16) + (ch & 7);
+  float s = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const int r = r0 + part * n + k;
+    if (r < rows) s += __bfloat162float(h[r * 8]);
+  }
+  return s;
+}
+// Threads 0-255 hold channel threadIdx.x % 16 sums; the block's 16 channel totals (added over
+// the 16 thread groups in order) go to bpartial[blockIdx.x][16].
+__device__ __forceinline__ void bias_partial_store(float bsum, float* bpartial) {
+  __shared__ float bsh[16][17];
+  if (threadIdx.x < 256) bsh[threadIdx.x >> 4][threadIdx.x & 15] = bsum;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    float t = 0.f;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) t += bsh[g][threadIdx.x];
+    bpartial[blockIdx.x * 16 + threadIdx.x] = t;
+  }
 }
 
 size_t wgrad_s1_smem(int m) { return 2 * 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16; }
@@ -930,7 +1005,7 @@ __device__ __forceinline__ void wg_stage_rows_async(const __nv_bfloat16* __restr
 
 __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __restrict__ P,
                                                          const __nv_bfloat16* __restrict__ Q, int m, int zc,
-                                                         float* partial) {
+                                                         float* partial, float* bpartial) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int R = m + 2, L = 130 + 2 * R;
   unsigned char* sP0 = sm;                      // [2 buffers][2 halves][128][16 B]
@@ -941,6 +1016,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
   const long long nunits = (long long)per_plane * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // tiles done by this block; the P rows of tile tt are in buffer tt & 1
+  float bsum = 0.f;  // threads 0-255: channel threadIdx.x % 16 of P over their share of the rows
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
   for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -974,10 +1050,12 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
       }
+      if (bpartial && threadIdx.x < 256) bsum += p_rows_sum(sP0 + (tt & 1u) * 4096, 128, 0, 8);
       cp_async_wait_all();
       __syncthreads();
     }
   }
+  if (bpartial) bias_partial_store(bsum, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
@@ -1014,7 +1092,7 @@ size_t wgrad_s2_smem(int seg) { return 2 * 2 * (size_t)seg * 16 + kW2Slots * 2 *
 
 __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __restrict__ P, int mp,
                                                          const __nv_bfloat16* __restrict__ Q, int mq, int seg,
-                                                         int nseg, int zc, float* partial) {
+                                                         int nseg, int zc, float* partial, float* bpartial) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int Wf = 2 * seg + 1, hs = 3 * Wf * 16;  // bytes per staged fine half
   unsigned char* sP0 = sm;                        // [2 buffers][2 halves][seg][16 B]
@@ -1028,6 +1106,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
   const long long nunits = (long long)mp * nseg * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // coarse planes done by this block; the P rows of plane tt are in buffer tt & 1
+  float bsum = 0.f;  // threads 0-255: channel threadIdx.x % 16 of P over their share of the rows
   // fine rows 2 cy - 1 .. 2 cy + 1 of fine plane f over fine x 2 x0 - 1 .. 2 x0 + 2 seg - 1
   auto stage_fine = [&](int f, int cy, int x0) {
     const uint32_t d = smem_u32(slot(f));
@@ -1096,10 +1175,12 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
       }
+      if (bpartial && threadIdx.x < 256) bsum += p_rows_sum(sP0 + (tt & 1u) * 2 * seg * 16, seg, 0, (seg + 15) / 16);
       cp_async_wait_all();
       __syncthreads();
     }
   }
+  if (bpartial) bias_partial_store(bsum, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
@@ -1203,8 +1284,11 @@ void conv(int gather, const __nv_bfloat16* in, int m_in, const __nv_bfloat16* w,
     up_tc_launch(a, status, s);
 }
 
+// Weight gradient of `layer`; with bias_from_p also its bias gradient (the channel sums of P,
+// the layer's output gradient), from the same kernel.
 void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const __nv_bfloat16* Q, int mq,
-           cudaStream_t s) {
+           bool bias_from_p, cudaStream_t s) {
+  float* bpart = bias_from_p ? u.partial + (long long)kWgBlocks * 27 * 256 : nullptr;
   int blocks;
   if (gather == S1) {  // stride 1: P and Q on the same grid (mp == mq)
     const size_t smem = wgrad_s1_smem(mp);
@@ -1212,7 +1296,7 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
     const long long per_plane = ((long long)mp * (mp + 2) + 127) / 128;
     const int zc = tc_column(per_plane, mp);
     blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
-    k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, u.partial);
+    k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, u.partial, bpart);
   } else {  // stride 2: P on the coarse grid, Q on the fine grid
     int nseg = 0;
     const int seg = wgrad_s2_seg(mp, &nseg);
@@ -1221,14 +1305,15 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
     const long long per_plane = (long long)mp * nseg;
     const int zc = (int)std::max<long long>(1, std::min<long long>(kTcZ, per_plane * mp / kTcUnits));
     blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
-    k_wgrad_s2<<<blocks, kWgThreads, smem, s>>>(P, mp, Q, mq, seg, nseg, zc, u.partial);
+    k_wgrad_s2<<<blocks, kWgThreads, smem, s>>>(P, mp, Q, mq, seg, nseg, zc, u.partial, bpart);
   }
   const UNetLayer& L = u.L[layer];
-  k_wgrad_reduce<<<27 * 256 / 32, 256, 0, s>>>(u.partial, blocks, u.grads + L.woff, L.kind, L.cin, L.cout);
+  k_wgrad_reduce<<<27 * 256 / 32 + (bias_from_p ? 1 : 0), 1024, 0, s>>>(
+      u.partial, bpart, blocks, u.grads + L.woff, bias_from_p ? u.grads + L.boff : nullptr, L.kind, L.cin, L.cout);
 }
 
 void bgrad(UNet& u, int layer, const __nv_bfloat16* P, long long nvox, cudaStream_t s) {
-  const int blocks = 256;
+  const int blocks = (int)std::min<long long>(kBgBlocks, (nvox + 255) / 256);
   float* part = u.partial + (long long)kWgBlocks * 27 * 256;
   k_bgrad_partial<<<blocks, 256, 0, s>>>(P, nvox, part);
   k_bgrad_reduce<<<1, 256, 0, s>>>(part, blocks, u.grads + u.L[layer].boff, u.L[layer].cout);
@@ -1284,7 +1369,7 @@ nhmf_status unet_alloc(nhmf_ctx* c, int cap) {
   for (__nv_bfloat16** p : {&u->d1, &u->s1, &u->u1, &u->t1, &u->g1a, &u->g1b, &u->g1c}) A((void**)p, b1);
   for (__nv_bfloat16** p : {&u->d2, &u->m2, &u->g2a, &u->g2b}) A((void**)p, b2);
   A((void**)&u->y, 3 * u->N0 * sizeof(float));
-  A((void**)&u->partial, ((size_t)kWgBlocks * 27 * 256 + 256 * 16) * sizeof(float));
+  A((void**)&u->partial, ((size_t)kWgBlocks * 27 * 256 + (size_t)kBgBlocks * 16) * sizeof(float));
   A((void**)&u->sc, 16 * sizeof(double));
   if (cap > 0) A((void**)&u->pairs, (size_t)cap * 2 * 3 * u->N0 * sizeof(float));
   if (!ok) return fail(c, NHMF_ERR_OOM, "unet: device allocation failed");
@@ -1337,38 +1422,29 @@ void unet_backward(UNet& u, cudaStream_t s) {
   __nv_bfloat16 *dy = u.g0a, *dt0 = u.g0b, *du0 = u.g0c, *ds0 = u.g0a;
   __nv_bfloat16 *dt1 = u.g1a, *du1 = u.g1b, *ds1 = u.g1c, *dd1 = u.g1a;
   __nv_bfloat16 *dm2 = u.g2a, *dd2 = u.g2b;
-  wgrad(u, L_OUT, S1, dy, M0, u.t0, M0, s);
-  bgrad(u, L_OUT, dy, u.N0, s);
+  wgrad(u, L_OUT, S1, dy, M0, u.t0, M0, true, s);
   conv(S1, dy, M0, u.L[L_OUT].wb, nullptr, nullptr, u.t0, false, dt0, nullptr, M0, s, u.status);
-  wgrad(u, L_T0, S1, dt0, M0, u.u0, M0, s);
-  bgrad(u, L_T0, dt0, u.N0, s);
+  wgrad(u, L_T0, S1, dt0, M0, u.u0, M0, true, s);
   conv(S1, dt0, M0, u.L[L_T0].wb, nullptr, nullptr, u.u0, false, du0, nullptr, M0, s, u.status);
-  wgrad(u, L_U0, DOWN2, u.t1, M1, du0, M0, s);  // dU[c][o] = sum t1[c] du0[o](2v'+d)
+  wgrad(u, L_U0, DOWN2, u.t1, M1, du0, M0, false, s);  // dU[c][o] = sum t1[c] du0[o](2v'+d)
   bgrad(u, L_U0, du0, u.N0, s);
   conv(DOWN2, du0, M0, u.L[L_U0].wb, nullptr, nullptr, u.t1, false, dt1, nullptr, M1, s, u.status);
-  wgrad(u, L_T1, S1, dt1, M1, u.u1, M1, s);
-  bgrad(u, L_T1, dt1, u.N1, s);
+  wgrad(u, L_T1, S1, dt1, M1, u.u1, M1, true, s);
   conv(S1, dt1, M1, u.L[L_T1].wb, nullptr, nullptr, u.u1, false, du1, nullptr, M1, s, u.status);
-  wgrad(u, L_U1, DOWN2, u.m2, M2, du1, M1, s);
+  wgrad(u, L_U1, DOWN2, u.m2, M2, du1, M1, false, s);
   bgrad(u, L_U1, du1, u.N1, s);
   conv(DOWN2, du1, M1, u.L[L_U1].wb, nullptr, nullptr, u.m2, false, dm2, nullptr, M2, s, u.status);
-  wgrad(u, L_M2, S1, dm2, M2, u.d2, M2, s);
-  bgrad(u, L_M2, dm2, u.N2, s);
+  wgrad(u, L_M2, S1, dm2, M2, u.d2, M2, true, s);
   conv(S1, dm2, M2, u.L[L_M2].wb, nullptr, nullptr, u.d2, false, dd2, nullptr, M2, s, u.status);
-  wgrad(u, L_D2, DOWN2, dd2, M2, u.s1, M1, s);
-  bgrad(u, L_D2, dd2, u.N2, s);
+  wgrad(u, L_D2, DOWN2, dd2, M2, u.s1, M1, true, s);
   conv(UP2, dd2, M2, u.L[L_D2].wb, nullptr, du1, u.s1, false, ds1, nullptr, M1, s, u.status);  // + skip grad, ReLU mask
-  wgrad(u, L_E1, S1, ds1, M1, u.d1, M1, s);
-  bgrad(u, L_E1, ds1, u.N1, s);
+  wgrad(u, L_E1, S1, ds1, M1, u.d1, M1, true, s);
   conv(S1, ds1, M1, u.L[L_E1].wb, nullptr, nullptr, u.d1, false, dd1, nullptr, M1, s, u.status);
-  wgrad(u, L_D1, DOWN2, dd1, M1, u.s0, M0, s);
-  bgrad(u, L_D1, dd1, u.N1, s);
+  wgrad(u, L_D1, DOWN2, dd1, M1, u.s0, M0, true, s);
   conv(UP2, dd1, M1, u.L[L_D1].wb, nullptr, du0, u.s0, false, ds0, nullptr, M0, s, u.status);
-  wgrad(u, L_E0, S1, ds0, M0, u.a0, M0, s);
-  bgrad(u, L_E0, ds0, u.N0, s);
+  wgrad(u, L_E0, S1, ds0, M0, u.a0, M0, true, s);
   conv(S1, ds0, M0, u.L[L_E0].wb, nullptr, nullptr, u.a0, false, dt0, nullptr, M0, s, u.status);  // da0 in dt0's buffer
-  wgrad(u, L_IN, S1, dt0, M0, u.x16, M0, s);
-  bgrad(u, L_IN, dt0, u.N0, s);
+  wgrad(u, L_IN, S1, dt0, M0, u.x16, M0, true, s);
 }
 
 // x16 from an FP64 planar vector scaled to unit RMS.
