@@ -955,29 +955,28 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint3
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
 }
 
-// Sum of channel threadIdx.x % 16 of the staged P rows r0 + 16 k (k = 0 .. n - 1, offset by
-// threadIdx.x / 16 * n) of a [2 halves][rows][16 B] buffer: the bias gradient's share of a tile.
-__device__ __forceinline__ float p_rows_sum(const unsigned char* buf, int rows, int r0, int n) {
-  const int ch = threadIdx.x & 15, part = threadIdx.x >> 4;
-  const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(buf + (ch >> 3) * rows * 16) + (ch & 7);
-  float s = 0.f;
-  for (int k = 0; k < n; ++k) {
-    const int r = r0 + part * n + k;
-    if (r < rows) s += __bfloat162float(h[r * 8]);
-  }
-  return s;
+// Bias-gradient share of an A fragment (P^T, channels x 16 positions, m16n8k16 layout): lane
+// (g, t) holds channels g (a0, a2) and g + 8 (a1, a3) at 4 of the positions.
+__device__ __forceinline__ void frag_channel_sums(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, float& sg,
+                                                  float& sg8) {
+  const __nv_bfloat162 x0 = *reinterpret_cast<const __nv_bfloat162*>(&a0),
+                       x1 = *reinterpret_cast<const __nv_bfloat162*>(&a1),
+                       x2 = *reinterpret_cast<const __nv_bfloat162*>(&a2),
+                       x3 = *reinterpret_cast<const __nv_bfloat162*>(&a3);
+  sg += (__low2float(x0) + __high2float(x0)) + (__low2float(x2) + __high2float(x2));
+  sg8 += (__low2float(x1) + __high2float(x1)) + (__low2float(x3) + __high2float(x3));
 }
-// Threads 0-255 hold channel threadIdx.x % 16 sums; the block's 16 channel totals (added over
-// the 16 thread groups in order) go to bpartial[blockIdx.x][16].
-__device__ __forceinline__ void bias_partial_store(float bsum, float* bpartial) {
-  __shared__ float bsh[16][17];
-  if (threadIdx.x < 256) bsh[threadIdx.x >> 4][threadIdx.x & 15] = bsum;
-  __syncthreads();
-  if (threadIdx.x < 16) {
-    float t = 0.f;
-#pragma unroll
-    for (int g = 0; g < 16; ++g) t += bsh[g][threadIdx.x];
-    bpartial[blockIdx.x * 16 + threadIdx.x] = t;
+// Warp 0: the block's 16 channel totals (the 4 lanes of each channel added in a fixed order)
+// to bpartial[blockIdx.x][16].
+__device__ __forceinline__ void bias_partial_store(float sg, float sg8, float* bpartial) {
+  sg += __shfl_xor_sync(0xffffffffu, sg, 1);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
+  sg += __shfl_xor_sync(0xffffffffu, sg, 2);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
+  const int lane = threadIdx.x & 31;
+  if ((lane & 3) == 0) {
+    bpartial[blockIdx.x * 16 + (lane >> 2)] = sg;
+    bpartial[blockIdx.x * 16 + (lane >> 2) + 8] = sg8;
   }
 }
 
@@ -1016,7 +1015,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
   const long long nunits = (long long)per_plane * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // tiles done by this block; the P rows of tile tt are in buffer tt & 1
-  float bsum = 0.f;  // threads 0-255: channel threadIdx.x % 16 of P over their share of the rows
+  float bsg = 0.f, bsg8 = 0.f;  // warp 0: channels g, g + 8 of P over its fragments (bias gradient)
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
   for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -1037,6 +1036,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
         // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
         uint32_t a0, a1, a2, a3;
         ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * 128 + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
+        if (bpartial && warp == 0) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
 #pragma unroll
         for (int jt = 0; jt < 3; ++jt) {
           const int tap = 3 * warp + jt;
@@ -1050,12 +1050,11 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
       }
-      if (bpartial && threadIdx.x < 256) bsum += p_rows_sum(sP0 + (tt & 1u) * 4096, 128, 0, 8);
       cp_async_wait_all();
       __syncthreads();
     }
   }
-  if (bpartial) bias_partial_store(bsum, bpartial);
+  if (bpartial && warp == 0) bias_partial_store(bsg, bsg8, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
@@ -1106,7 +1105,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
   const long long nunits = (long long)mp * nseg * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // coarse planes done by this block; the P rows of plane tt are in buffer tt & 1
-  float bsum = 0.f;  // threads 0-255: channel threadIdx.x % 16 of P over their share of the rows
+  float bsg = 0.f, bsg8 = 0.f;  // warp 0: channels g, g + 8 of P over its fragments (bias gradient)
   // fine rows 2 cy - 1 .. 2 cy + 1 of fine plane f over fine x 2 x0 - 1 .. 2 x0 + 2 seg - 1
   auto stage_fine = [&](int f, int cy, int x0) {
     const uint32_t d = smem_u32(slot(f));
@@ -1161,6 +1160,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
         // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
         uint32_t a0, a1, a2, a3;
         ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * seg + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
+        if (bpartial && warp == 0) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
         const int k = 16 * c + (lm & 1) * 8 + lr;  // this lane's B row: position k, channel half lm >> 1
 #pragma unroll
         for (int jt = 0; jt < 3; ++jt) {
@@ -1175,12 +1175,11 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
       }
-      if (bpartial && threadIdx.x < 256) bsum += p_rows_sum(sP0 + (tt & 1u) * 2 * seg * 16, seg, 0, (seg + 15) / 16);
       cp_async_wait_all();
       __syncthreads();
     }
   }
-  if (bpartial) bias_partial_store(bsum, bpartial);
+  if (bpartial && warp == 0) bias_partial_store(bsg, bsg8, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
