@@ -304,7 +304,9 @@ __global__ void k_input(const TS* src, long long n, const double* den, double mu
 // Masked loss sums: partials of ||f (y - e)||^2 and ||f e||^2.
 __global__ void __launch_bounds__(kRedThreads) k_loss_partials(const float* y, const float* e, long long n, int bc,
                                                                int M, double* partials) {
-  double num = 0.0, den = 0.0;
+  // per thread in FP32 (a few dozen terms: relative error ~1e-6, exact for integer data), then
+  // FP64 across threads and blocks
+  float numf = 0.f, denf = 0.f;
   const int nn = (int)n, MM = M * M;  // grids of at most 785^3 nodes
   for (int v = blockIdx.x * kRedThreads + threadIdx.x; v < nn; v += kRedBlocks * kRedThreads) {
     const int i = v % M, k = v / MM;
@@ -312,11 +314,12 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_partials(const float* y, c
     for (int c = 0; c < 3; ++c) {
       const bool fixed = bc == NHMF_BC_CLAMP_X0 ? i == 0 : bc == NHMF_BC_COMPRESSION && (k == 0 || (c == 2 && k == M - 1));
       if (fixed) continue;
-      const double ev = double(e[(long long)c * n + v]), d = double(y[(long long)c * n + v]) - ev;
-      num += d * d;
-      den += ev * ev;
+      const float ev = e[(long long)c * n + v], d = y[(long long)c * n + v] - ev;
+      numf = fmaf(d, d, numf);
+      denf = fmaf(ev, ev, denf);
     }
   }
+  double num = numf, den = denf;
   __shared__ double sh[2][kRedThreads / 32];
   for (int o = 16; o > 0; o >>= 1) {
     num += __shfl_down_sync(0xffffffffu, num, o);
@@ -966,17 +969,25 @@ __device__ __forceinline__ void frag_channel_sums(uint32_t a0, uint32_t a1, uint
   sg += (__low2float(x0) + __high2float(x0)) + (__low2float(x2) + __high2float(x2));
   sg8 += (__low2float(x1) + __high2float(x1)) + (__low2float(x3) + __high2float(x3));
 }
-// Warp 0: the block's 16 channel totals (the 4 lanes of each channel added in a fixed order)
-// to bpartial[blockIdx.x][16].
+// All 9 warps: the block's 16 channel totals (per warp the 4 lanes of each channel, then the
+// warps in order) to bpartial[blockIdx.x][16].  Ends with a block barrier.
 __device__ __forceinline__ void bias_partial_store(float sg, float sg8, float* bpartial) {
+  __shared__ float bsh[kWgThreads / 32][16];
   sg += __shfl_xor_sync(0xffffffffu, sg, 1);
   sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
   sg += __shfl_xor_sync(0xffffffffu, sg, 2);
   sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if ((lane & 3) == 0) {
-    bpartial[blockIdx.x * 16 + (lane >> 2)] = sg;
-    bpartial[blockIdx.x * 16 + (lane >> 2) + 8] = sg8;
+    bsh[warp][lane >> 2] = sg;
+    bsh[warp][(lane >> 2) + 8] = sg8;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWgThreads / 32; ++w) t += bsh[w][threadIdx.x];
+    bpartial[blockIdx.x * 16 + threadIdx.x] = t;
   }
 }
 
@@ -1015,7 +1026,8 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
   const long long nunits = (long long)per_plane * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // tiles done by this block; the P rows of tile tt are in buffer tt & 1
-  float bsg = 0.f, bsg8 = 0.f;  // warp 0: channels g, g + 8 of P over its fragments (bias gradient)
+  float bsg = 0.f, bsg8 = 0.f;  // channels g, g + 8 of P over this warp's share of the chunks (bias gradient)
+  unsigned chunk = 0;            // chunks of 16 positions done by this block; chunk % 9 adds its fragments
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
   for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -1036,7 +1048,6 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
         // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
         uint32_t a0, a1, a2, a3;
         ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * 128 + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
-        if (bpartial && warp == 0) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
 #pragma unroll
         for (int jt = 0; jt < 3; ++jt) {
           const int tap = 3 * warp + jt;
@@ -1049,12 +1060,15 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
           mma16816(acc[jt][0], a0, a1, a2, a3, b0, b1);
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
+        // the bias gradient's share, after the MMAs have consumed the fragment
+        if (bpartial && chunk % (kWgThreads / 32) == (unsigned)warp) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
+        ++chunk;
       }
       cp_async_wait_all();
       __syncthreads();
     }
   }
-  if (bpartial && warp == 0) bias_partial_store(bsg, bsg8, bpartial);
+  if (bpartial) bias_partial_store(bsg, bsg8, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
@@ -1105,7 +1119,8 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
   const long long nunits = (long long)mp * nseg * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // coarse planes done by this block; the P rows of plane tt are in buffer tt & 1
-  float bsg = 0.f, bsg8 = 0.f;  // warp 0: channels g, g + 8 of P over its fragments (bias gradient)
+  float bsg = 0.f, bsg8 = 0.f;  // channels g, g + 8 of P over this warp's share of the chunks (bias gradient)
+  unsigned chunk = 0;            // chunks of 16 positions done by this block; chunk % 9 adds its fragments
   // fine rows 2 cy - 1 .. 2 cy + 1 of fine plane f over fine x 2 x0 - 1 .. 2 x0 + 2 seg - 1
   auto stage_fine = [&](int f, int cy, int x0) {
     const uint32_t d = smem_u32(slot(f));
@@ -1160,7 +1175,6 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
         // A = P^T on positions 16c..16c+15: matrices (k 0-7, a lo), (k 0-7, a hi), (k 8-15, a lo), (k 8-15, a hi)
         uint32_t a0, a1, a2, a3;
         ldsm_x4_trans(sp + (uint32_t)(((lm & 1) * seg + 16 * c + (lm >> 1) * 8 + lr) * 16), a0, a1, a2, a3);
-        if (bpartial && warp == 0) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
         const int k = 16 * c + (lm & 1) * 8 + lr;  // this lane's B row: position k, channel half lm >> 1
 #pragma unroll
         for (int jt = 0; jt < 3; ++jt) {
@@ -1174,12 +1188,15 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
           mma16816(acc[jt][0], a0, a1, a2, a3, b0, b1);
           mma16816(acc[jt][1], a0, a1, a2, a3, b2, b3);
         }
+        // the bias gradient's share, after the MMAs have consumed the fragment
+        if (bpartial && chunk % (kWgThreads / 32) == (unsigned)warp) frag_channel_sums(a0, a1, a2, a3, bsg, bsg8);
+        ++chunk;
       }
       cp_async_wait_all();
       __syncthreads();
     }
   }
-  if (bpartial && warp == 0) bias_partial_store(bsg, bsg8, bpartial);
+  if (bpartial) bias_partial_store(bsg, bsg8, bpartial);
   float* out = partial + (long long)blockIdx.x * 27 * 256;
 #pragma unroll
   for (int jt = 0; jt < 3; ++jt) {
