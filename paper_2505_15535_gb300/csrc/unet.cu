@@ -944,9 +944,10 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_up_tc(const ConvArgs a, int z
 }
 
 // Weight gradient of the stride-1 gather, tiled: G[tap][a][b] = sum_v P[v][a] Q[v + d_tap][b].
-// A block takes tiles of 128 consecutive positions of one z-plane in x-padded row order (as
-// k_conv_tc) along a column in z.  It stages the tile's P rows and a ring of Q planes (the
-// z - 1 .. z + 1 windows of all taps, zero outside the grid) as 16-byte channel halves, so
+// A block takes tiles of 128 consecutive positions of one z-plane of an x-strip in x-padded
+// row order (as k_conv_tc) along a column in z.  It stages the tile's P rows and a ring of Q
+// planes (the z - 1 .. z + 1 windows of all taps, zero outside the grid, the neighbouring
+// strip's data in the halo columns) as 16-byte channel halves, so
 // that every 8 x 8 block of a fragment is one ldmatrix: per chunk of 16 positions one
 // ldmatrix.x4.trans gives the A fragment (P^T, channels a x positions) for all the warp's
 // taps, and one per tap gives the B fragments (positions x channels b) of both n-tiles.
@@ -991,19 +992,20 @@ __device__ __forceinline__ void bias_partial_store(float sg, float sg8, float* b
   }
 }
 
-size_t wgrad_s1_smem(int m) { return 2 * 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (m + 2)) * 16; }
+size_t wgrad_s1_smem(int W) { return 2 * 2 * 128 * 16 + 4 * 2 * (size_t)(130 + 2 * (W + 2)) * 16; }
 
-// P rows of a tile, asynchronously: position p0 + j = y R + x + 1 of plane z (zero on the pad
-// columns and past the plane) to row j of both 16-byte channel halves (128 rows apart).
+// P rows of a tile, asynchronously: position p0 + j = y R + xl + 1 of plane z in the x-strip
+// of W columns from x0 (zero on the pad columns, past the strip or the grid) to row j of both
+// 16-byte channel halves (128 rows apart).
 __device__ __forceinline__ void wg_stage_rows_async(const __nv_bfloat16* __restrict__ P, int m, int R, int p0, int z,
-                                                    unsigned char* sP) {
+                                                    int x0, int W, unsigned char* sP) {
   const uint32_t s = smem_u32(sP);
   const uint4* g = reinterpret_cast<const uint4*>(P);
   for (int j = threadIdx.x; j < 128; j += blockDim.x) {
-    const int p = p0 + j, y = p / R, x = p % R - 1;
+    const int p = p0 + j, y = p / R, xl = p % R - 1, x = x0 + xl;
     const uint4* src = g;
     uint32_t bytes = 0;
-    if (p < m * R && x >= 0 && x < m) {
+    if (p < m * R && xl >= 0 && xl < W && x < m) {
       src = g + 2 * (x + (long long)m * (y + (long long)m * z));
       bytes = 16;
     }
@@ -1013,17 +1015,20 @@ __device__ __forceinline__ void wg_stage_rows_async(const __nv_bfloat16* __restr
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __restrict__ P,
-                                                         const __nv_bfloat16* __restrict__ Q, int m, int zc,
-                                                         float* partial, float* bpartial) {
+#ifndef NHMF_WG_MINB
+#define NHMF_WG_MINB 4
+#endif
+__global__ void __launch_bounds__(kWgThreads, NHMF_WG_MINB) k_wgrad_s1(const __nv_bfloat16* __restrict__ P,
+                                                         const __nv_bfloat16* __restrict__ Q, int m, int zc, int W,
+                                                         int nstrips, float* partial, float* bpartial) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const int R = m + 2, L = 130 + 2 * R;
+  const int R = W + 2, L = 130 + 2 * R;
   unsigned char* sP0 = sm;                      // [2 buffers][2 halves][128][16 B]
   unsigned char* sQ = sm + 2 * 2 * 128 * 16;    // [4 slots][2 halves][L][16 B]
   auto slot = [&](int plane) { return sQ + ((plane + 4) & 3) * 2 * L * 16; };  // plane >= -1
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int per_plane = (m * R + 127) / 128, nzc = (m + zc - 1) / zc;
-  const long long nunits = (long long)per_plane * nzc;
+  const long long nunits = (long long)per_plane * nstrips * nzc;
   float acc[3][2][4] = {};
   unsigned tt = 0;  // tiles done by this block; the P rows of tile tt are in buffer tt & 1
   float bsg = 0.f, bsg8 = 0.f;  // channels g, g + 8 of P over this warp's share of the chunks (bias gradient)
@@ -1031,17 +1036,20 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s1(const __nv_bfloat16* __
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
   for (long long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-    const int p0 = int(unit % per_plane) * 128, zb = int(unit / per_plane) * zc, ze = min(m, zb + zc);
+    const int p0 = int(unit % per_plane) * 128;
+    const long long rest = unit / per_plane;
+    const int x0 = int(rest % nstrips) * W, zb = int(rest / nstrips) * zc, ze = min(m, zb + zc);
     // planes z - 1 .. z + 1 of Q and the P rows of plane z are in shared memory when tile z
     // starts; plane z + 2 and the rows of plane z + 1 are copied while tile z computes
-    for (int pl = zb - 1; pl <= zb + 1; ++pl) tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, pl, slot(pl), threadIdx.x, blockDim.x);
-    wg_stage_rows_async(P, m, R, p0, zb, sP0 + (tt & 1u) * 4096);
+    for (int pl = zb - 1; pl <= zb + 1; ++pl)
+      tc_stage_async(Q, m, R, L, p0 - 1, 1 - x0, 1, pl, slot(pl), threadIdx.x, blockDim.x);
+    wg_stage_rows_async(P, m, R, p0, zb, x0, W, sP0 + (tt & 1u) * 4096);
     cp_async_wait_all();
     __syncthreads();
     for (int z = zb; z < ze; ++z, ++tt) {
       if (z + 1 < ze) {
-        tc_stage_async(Q, m, R, L, p0 - 1, 1, 1, z + 2, slot(z + 2), threadIdx.x, blockDim.x);
-        wg_stage_rows_async(P, m, R, p0, z + 1, sP0 + ((tt + 1) & 1u) * 4096);
+        tc_stage_async(Q, m, R, L, p0 - 1, 1 - x0, 1, z + 2, slot(z + 2), threadIdx.x, blockDim.x);
+        wg_stage_rows_async(P, m, R, p0, z + 1, x0, W, sP0 + ((tt + 1) & 1u) * 4096);
       }
       const uint32_t sp = smem_u32(sP0 + (tt & 1u) * 4096);
       for (int c = 0; c < 8; ++c) {
@@ -1306,13 +1314,15 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
            bool bias_from_p, cudaStream_t s) {
   float* bpart = bias_from_p ? u.partial + (long long)kWgBlocks * 27 * 256 : nullptr;
   int blocks;
-  if (gather == S1) {  // stride 1: P and Q on the same grid (mp == mq)
-    const size_t smem = wgrad_s1_smem(mp);
+  if (gather == S1) {  // stride 1: P and Q on the same grid (mp == mq), in x-strips as k_conv_tc
+    int nstrips = 0;
+    const int W = conv_strip_width(mp, &nstrips);
+    const size_t smem = wgrad_s1_smem(W);
     cudaFuncSetAttribute(k_wgrad_s1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const long long per_plane = ((long long)mp * (mp + 2) + 127) / 128;
-    const int zc = tc_column(per_plane, mp);
-    blocks = (int)std::min<long long>(kWgBlocks, per_plane * ((mp + zc - 1) / zc));
-    k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, u.partial, bpart);
+    const long long per_plane = ((long long)mp * (W + 2) + 127) / 128;
+    const int zc = tc_column(per_plane * nstrips, mp);
+    blocks = (int)std::min<long long>(kWgBlocks, per_plane * nstrips * ((mp + zc - 1) / zc));
+    k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, W, nstrips, u.partial, bpart);
   } else {  // stride 2: P on the coarse grid, Q on the fine grid
     int nseg = 0;
     const int seg = wgrad_s2_seg(mp, &nseg);
