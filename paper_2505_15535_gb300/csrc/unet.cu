@@ -1282,14 +1282,11 @@ void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   const long long per_plane = ((long long)m * R + 127) / 128;
   const int zc = tc_column(per_plane * nstrips, m);
   const long long nunits = per_plane * nstrips * ((m + zc - 1) / zc);
-  static int nsm = 0, smem_sm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    nsm = std::max(nsm, 1);
-  }
+  int dev = 0, nsm = 0, smem_sm = 0;  // of the current device (attribute queries are cheap)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm = std::max(nsm, 1);
   const int per_sm = std::max(1, std::min(4, smem_sm / (int)(smem + 1024)));
   k_conv_tc<<<(int)std::min<long long>(nunits, (long long)per_sm * nsm), kTcSThreads, smem, s>>>(a, map, zc, W, nstrips,
                                                                                                   status);
