@@ -133,7 +133,8 @@ nhmf_status nhmf_tangent_apply(nhmf_ctx* ctx, int precision, int strategy, const
 nhmf_status nhmf_tangent_apply_at(nhmf_ctx* ctx, const double* u, const double* du, double* v, void* stream);
 
 /* r = R(u) (Eq. F, no traction) in FP64 for the device vector u; rows on D are zero.
- * Synchronises and returns NHMF_ERR_NONPOS_J / NHMF_ERR_NONFINITE on failure. */
+ * Synchronises and returns NHMF_ERR_NONPOS_J if det F <= 0 at a point, NHMF_ERR_NONFINITE if
+ * u holds a non-finite value or the stress overflows. */
 nhmf_status nhmf_residual(nhmf_ctx* ctx, const double* u, double* r, void* stream);
 
 /* d = diag(A(u)) in FP64 at the current linearisation point (1 on D).  Asynchronous. */
@@ -337,6 +338,44 @@ nhmf_status nhmf_profile_read(nhmf_ctx* ctx, int kind, double* elapsed_ms, long 
  * best of three timed launches after one warm-up (CUDA events).  Allocates and frees a few
  * bytes; synchronises the device. */
 nhmf_status nhmf_measure_fma_peak(int precision, double* tflops);
+
+/* ------------------------------------------------------------------ diagnostics
+ * Fault injection on the host: the solvers' failure paths, exercised without a device fault.
+ * Flags, OR-able; each applies to the next call where it can act and then clears itself:
+ *   NHMF_INJECT_NAN_DU        the next Newton update of nhmf_solve carries a NaN: the trial
+ *                             residual reports it, and nhmf_solve returns NHMF_ERR_NONFINITE
+ *                             with u as after the last accepted update;
+ *   NHMF_INJECT_CG_STALL      the preconditioner of the next flexible Krylov solve (mixed,
+ *                             multigrid and learned solvers) returns z = 0 throughout: the
+ *                             solve breaks down and finishes with Jacobi-CG (one fallback);
+ *   NHMF_INJECT_UNET_GARBAGE  the next learned solve replaces every network output with a
+ *                             fixed pseudo-random field: the solve stalls and falls back to
+ *                             Jacobi-CG (the correction on the V-cycle instead takes a step
+ *                             near zero and converges without it).
+ * nhmf_create also takes flags from the environment variable NHMF_INJECT, a comma-separated
+ * list of nan_in_du, cg_stall, unet_garbage. */
+enum {
+  NHMF_INJECT_NAN_DU = 1,
+  NHMF_INJECT_CG_STALL = 2,
+  NHMF_INJECT_UNET_GARBAGE = 4,
+  NHMF_INJECT_UNKNOWN = 1 << 30
+};
+nhmf_status nhmf_set_inject(nhmf_ctx* ctx, unsigned flags);
+/* The injection flags still pending (a flag clears when it fires). */
+unsigned nhmf_inject_pending(const nhmf_ctx* ctx);
+/* Flags of a spec in the NHMF_INJECT syntax (NULL or "" gives 0); NHMF_INJECT_UNKNOWN is set
+ * when a name is not recognised.  Host only: needs no device. */
+unsigned nhmf_parse_inject(const char* spec);
+
+/* Metrics: with a path set, calls append one JSON object per line to that file - one per
+ * Newton iteration and one per load step of nhmf_solve, one per nhmf_linear_solve, and one per
+ * nhmf_tangent_apply (which then synchronises to time itself with CUDA events).  Every object
+ * has "event"; the other keys name their units (seconds, ms, GDoF/s) or are counts and
+ * relative residuals.  NULL or "" closes the file.  nhmf_create also opens the file named by
+ * the environment variable NHMF_METRICS_JSONL.  NVTX ranges (apply, residual, diagonal,
+ * set_linearization, solve, load step, Newton iteration, linear solve, U-Net training) are
+ * always emitted; without a profiler attached they cost a function call each. */
+nhmf_status nhmf_set_metrics_log(nhmf_ctx* ctx, const char* path);
 
 #ifdef __cplusplus
 }

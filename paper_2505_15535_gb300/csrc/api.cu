@@ -1,6 +1,8 @@
 // C ABI of the library (declarations and contracts in include/nhmf.h).
 #include <algorithm>
+#include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -48,13 +50,26 @@ static void build_geometry(const nhmf_params& p, Geometry* g) {
 
 static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-}  // namespace nhmf
+void metrics_line(nhmf_ctx* c, const char* fmt, ...) {
+  if (!c || !c->metrics) return;
+  va_list ap;
+  va_start(ap, fmt);
+  std::fputc('{', c->metrics);
+  std::vfprintf(c->metrics, fmt, ap);
+  std::fputs("}\n", c->metrics);
+  va_end(ap);
+  std::fflush(c->metrics);
+}
 
-using namespace nhmf;
+static nhmf_status open_metrics(nhmf_ctx* c, const char* path) {
+  if (c->metrics) std::fclose(c->metrics);
+  c->metrics = nullptr;
+  if (!path || !*path) return NHMF_OK;
+  c->metrics = std::fopen(path, "a");
+  return c->metrics ? NHMF_OK : fail(c, NHMF_ERR_ARG, std::string("metrics log: cannot open ") + path);
+}
 
-extern "C" {
-
-nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
+nhmf_status create_context(const nhmf_params* prm, nhmf_ctx** out) {
   if (!prm || !out) return NHMF_ERR_ARG;
   *out = nullptr;
   if (prm->n_el < 1 || prm->n_el > 4096 || prm->degree < 1 || prm->degree > 4 || !(prm->mu > 0.0) ||
@@ -83,6 +98,29 @@ nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
   return NHMF_OK;
 }
 
+static const char* precision_name(int p) { return p == NHMF_FP64 ? "fp64" : p == NHMF_FP32 ? "fp32" : "df64"; }
+static const char* strategy_name(int s) {
+  return s == NHMF_CACHED ? "cached" : s == NHMF_ON_THE_FLY ? "on_the_fly" : "spatial";
+}
+
+}  // namespace nhmf
+
+using namespace nhmf;
+
+extern "C" {
+
+nhmf_status nhmf_create(const nhmf_params* prm, nhmf_ctx** out) {
+  nhmf_status st = create_context(prm, out);
+  if (st != NHMF_OK) return st;
+  nhmf_ctx* c = *out;
+  c->inject = nhmf_parse_inject(std::getenv("NHMF_INJECT")) & ~(unsigned)NHMF_INJECT_UNKNOWN;
+  if ((st = open_metrics(c, std::getenv("NHMF_METRICS_JSONL"))) != NHMF_OK) {
+    nhmf_destroy(c);
+    *out = nullptr;
+  }
+  return st;
+}
+
 void nhmf_destroy(nhmf_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
@@ -101,7 +139,45 @@ void nhmf_destroy(nhmf_ctx* c) {
   gmg_free(c);
   free_work(c);
   unet_free(c);
+  if (c->metrics) std::fclose(c->metrics);
   delete c;
+}
+
+unsigned nhmf_parse_inject(const char* spec) {
+  unsigned flags = 0;
+  if (!spec) return 0;
+  const char* p = spec;
+  while (*p) {
+    while (*p == ',' || *p == ' ') ++p;
+    const char* q = p;
+    while (*q && *q != ',' && *q != ' ') ++q;
+    const std::string name(p, (size_t)(q - p));
+    if (name == "nan_in_du")
+      flags |= NHMF_INJECT_NAN_DU;
+    else if (name == "cg_stall")
+      flags |= NHMF_INJECT_CG_STALL;
+    else if (name == "unet_garbage")
+      flags |= NHMF_INJECT_UNET_GARBAGE;
+    else if (!name.empty())
+      flags |= NHMF_INJECT_UNKNOWN;
+    p = q;
+  }
+  return flags;
+}
+
+nhmf_status nhmf_set_inject(nhmf_ctx* c, unsigned flags) {
+  if (!c) return NHMF_ERR_ARG;
+  if (flags & ~(unsigned)(NHMF_INJECT_NAN_DU | NHMF_INJECT_CG_STALL | NHMF_INJECT_UNET_GARBAGE))
+    return fail(c, NHMF_ERR_ARG, "set_inject: unknown flag");
+  c->inject = flags;
+  return NHMF_OK;
+}
+
+unsigned nhmf_inject_pending(const nhmf_ctx* c) { return c ? c->inject : 0; }
+
+nhmf_status nhmf_set_metrics_log(nhmf_ctx* c, const char* path) {
+  if (!c) return NHMF_ERR_ARG;
+  return open_metrics(c, path);
 }
 
 size_t nhmf_num_dofs(const nhmf_ctx* c) { return c ? (size_t)(3 * c->g.M3) : 0; }
@@ -146,6 +222,7 @@ nhmf_status nhmf_set_linearization(nhmf_ctx* c, const double* u, int mask, void*
   if (!c || !u || mask < 0 || mask > 15) return fail(c, NHMF_ERR_ARG, "set_linearization: bad argument");
   if (c->prm.model == NHMF_MODEL_SPLIT && (mask & (NHMF_CACHE_FP64 | NHMF_CACHE_FP32 | NHMF_CACHE_DF64)))
     return fail(c, NHMF_ERR_ARG, "set_linearization: the split model has only the spatial (Algorithm 2) cache");
+  NvtxRange range("nhmf_set_linearization");
   cudaStream_t s = as_stream(stream);
   const size_t n = 3 * c->g.M3;
   c->have_lin = false;
@@ -197,7 +274,30 @@ nhmf_status nhmf_tangent_apply(nhmf_ctx* c, int precision, int strategy, const v
   if (strategy == NHMF_CACHED && ((precision == NHMF_FP64 && !c->cache64) || (precision == NHMF_FP32 && !c->cache32) ||
                                   (precision == NHMF_DF64 && !c->cachedf)))
     return fail(c, NHMF_ERR_STATE, "tangent_apply: no point cache of this precision");
-  return launch_apply(c, precision, strategy, du, v, as_stream(stream));
+  NvtxRange range("nhmf_tangent_apply");
+  if (!c->metrics) return launch_apply(c, precision, strategy, du, v, as_stream(stream));
+  // timed with events on the caller's stream for the metrics line
+  cudaEvent_t e0, e1;
+  nhmf_status st = cuda_check(c, cudaEventCreate(&e0), "metrics event");
+  if (st != NHMF_OK) return st;
+  if ((st = cuda_check(c, cudaEventCreate(&e1), "metrics event")) != NHMF_OK) {
+    cudaEventDestroy(e0);
+    return st;
+  }
+  cudaEventRecord(e0, as_stream(stream));
+  st = launch_apply(c, precision, strategy, du, v, as_stream(stream));
+  cudaEventRecord(e1, as_stream(stream));
+  float ms = 0.f;
+  if (st == NHMF_OK) st = cuda_check(c, cudaEventSynchronize(e1), "metrics sync");
+  if (st == NHMF_OK) st = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "metrics time");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == NHMF_OK)
+    metrics_line(c, "\"event\": \"tangent_apply\", \"precision\": \"%s\", \"strategy\": \"%s\", \"dofs\": %lld, "
+                 "\"ms\": %.6f, \"gdofs\": %.6f",
+                 precision_name(precision), strategy_name(strategy), 3 * c->g.M3, (double)ms,
+                 ms > 0.f ? 3.0 * c->g.M3 / (ms * 1e6) : 0.0);
+  return st;
 }
 
 nhmf_status nhmf_tangent_apply_at(nhmf_ctx* c, const double* u, const double* du, double* v, void* stream) {
@@ -213,6 +313,7 @@ nhmf_status nhmf_tangent_apply_at(nhmf_ctx* c, const double* u, const double* du
 nhmf_status nhmf_residual(nhmf_ctx* c, const double* u, double* r, void* stream) {
   if (!c) return NHMF_ERR_ARG;
   if (!u || !r || (const void*)u == (void*)r) return fail(c, NHMF_ERR_ARG, "residual: bad argument");
+  NvtxRange range("nhmf_residual");
   nhmf_status st = launch_residual(c, u, r, as_stream(stream));
   if (st != NHMF_OK) return st;
   return nhmf_check_status(c, stream);
@@ -222,6 +323,7 @@ nhmf_status nhmf_diagonal(nhmf_ctx* c, double* d, void* stream) {
   if (!c) return NHMF_ERR_ARG;
   if (!d) return fail(c, NHMF_ERR_ARG, "diagonal: bad argument");
   if (!c->have_lin) return fail(c, NHMF_ERR_STATE, "diagonal: no linearisation point set");
+  NvtxRange range("nhmf_diagonal");
   return launch_diagonal(c, d, as_stream(stream));
 }
 

@@ -114,6 +114,16 @@ __global__ void k_axpby(long long n, double sa, const double* pa, const double* 
 }
 
 // out = num / den (device scalars), with a sign.
+__global__ void k_noise(long long n, double* z, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long v = (unsigned long long)i + seed * 0x9E3779B97F4A7C15ull;
+    v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+    v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+    v ^= v >> 31;
+    z[i] = double(v >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
 __global__ void k_ratio(const double* num, const double* den, double sign, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = sign * (*num / *den);
 }
@@ -201,6 +211,9 @@ void axpby(long long n, double a, const double* pa, const double* x, double b, c
 }
 void ratio(const double* num, const double* den, double sign, double* out, cudaStream_t s) {
   k_ratio<<<1, 32, 0, s>>>(num, den, sign, out);
+}
+void fill_noise(long long n, double* z, unsigned long long seed, cudaStream_t s) {
+  k_noise<<<kRedBlocks, kRedThreads, 0, s>>>(n, z, seed);
 }
 void ratio_or_zero(const double* num, const double* den, double* out, cudaStream_t s) {
   k_ratio_or_zero<<<1, 32, 0, s>>>(num, den, out);

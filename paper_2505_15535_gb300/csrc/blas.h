@@ -28,5 +28,8 @@ void to_fp64_scaled(long long n, const float* x, const double* scale, double* y,
 // x *= dinv (element-wise)
 void jacobi_apply(long long n, const double* dinv, double* x, cudaStream_t s);
 void reciprocal(long long n, const double* d, double* dinv64, float* dinv32, cudaStream_t s);
+// z[i] in [-1, 1) from a hash of (i, seed) (splitmix64 finaliser): a field uncorrelated with
+// any residual, for the fault injection of the learned solvers
+void fill_noise(long long n, double* z, unsigned long long seed, cudaStream_t s);
 
 }  // namespace nhmf

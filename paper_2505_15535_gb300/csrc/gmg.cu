@@ -76,11 +76,6 @@ __global__ void k_start(long long n, double* v) {
   }
 }
 
-__global__ void k_mul(long long n, const double* __restrict__ a, double* __restrict__ x) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] *= a[i];
-}
-
 // x *= 1 / *nrm (x stays as it is when *nrm is not positive)
 template <typename T>
 __global__ void k_scale_inv(long long n, const double* __restrict__ nrm, T* __restrict__ x) {
@@ -99,11 +94,6 @@ template <typename T>
 __global__ void k_to(long long n, const double* __restrict__ x, T* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = T(x[i]);
-}
-
-__global__ void k_scale(long long n, double s, double* __restrict__ x) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] *= s;
 }
 
 constexpr int kB = 1216, kT = 256;
@@ -265,7 +255,7 @@ nhmf_status gmg_build(nhmf_ctx* c) {
       nhmf_params prm = c->prm;
       prm.n_el = Ns[k];
       prm.degree = Ps[k];
-      nhmf_status st = nhmf_create(&prm, &L.ctx);
+      nhmf_status st = create_context(&prm, &L.ctx);
       if (st != NHMF_OK) {
         gmg_free(c);
         return fail(c, st, "gmg: level context");

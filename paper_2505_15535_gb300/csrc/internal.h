@@ -1,6 +1,9 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 
 #include <string>
 #include <vector>
@@ -115,9 +118,27 @@ struct nhmf_ctx {
   nhmf::SolverWork* work = nullptr;
   nhmf::UNet* unet = nullptr;
   nhmf::Gmg* gmg = nullptr;    // multigrid hierarchy, built on first use
+  unsigned inject = 0;         // pending NHMF_INJECT_* flags (host-side fault injection)
+  FILE* metrics = nullptr;     // JSONL metrics file (nhmf_set_metrics_log), or null
 };
 
 namespace nhmf {
+
+// NVTX range for the lifetime of the object (no cost without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// One JSON object (printf-style body without the braces) as a line of the metrics file.
+void metrics_line(nhmf_ctx* c, const char* fmt, ...);
+// Takes a pending injection flag: true (and the flag cleared) if it was set.
+inline bool take_inject(nhmf_ctx* c, unsigned flag) {
+  if (!(c->inject & flag)) return false;
+  c->inject &= ~flag;
+  return true;
+}
 
 enum : unsigned { kStatusNonPosJ = 1u, kStatusNonFinite = 2u, kStatusBreakdown = 4u, kStatusTcTimeout = 8u, kStatusTmaSetup = 16u };
 void free_work(nhmf_ctx* c);
@@ -155,5 +176,7 @@ nhmf_status cuda_check(nhmf_ctx* c, cudaError_t e, const char* what);
 // Resolves, once per device, the device address of the allocation-free solve's static
 // scratch array (noalloc.cu); called by nhmf_create with the context's device current.
 nhmf_status noalloc_setup(nhmf_ctx* c);
+// nhmf_create without the environment (NHMF_INJECT, NHMF_METRICS_JSONL): internal contexts.
+nhmf_status create_context(const nhmf_params* prm, nhmf_ctx** out);
 
 }  // namespace nhmf

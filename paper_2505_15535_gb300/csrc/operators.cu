@@ -739,7 +739,10 @@ __global__ void __launch_bounds__(LaunchCfg<P, double, 0>::THREADS) k_residual(c
 #pragma unroll
     for (int k = 0; k < 9; ++k) H[k] *= invh;
     const double Jm1 = kinematics(H, Fi, lnJ);
-    if (!(Jm1 > -1.0)) flags |= kStatusNonPosJ;
+    // a NaN deformation gradient is a non-finite input; det F <= 0 makes P non-finite too,
+    // but is reported as what it is (the Newton backtracking acts on it)
+    const bool inverted = Jm1 <= -1.0;
+    if (inverted) flags |= kStatusNonPosJ;
     const double s = sW[t % n3] * elem_factor(a, e0 + min(t / n3, nvalid - 1));
     double F[9], P[9];
 #pragma unroll
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(LaunchCfg<P, double, 0>::THREADS) k_residual(c
     model_piola(a.model, F, Fi, lnJ, Jm1, a.mu, a.lam, P);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      if (!isfinite(P[k])) flags |= kStatusNonFinite;
+      if (!inverted && !isfinite(P[k])) flags |= kStatusNonFinite;
       G[k * NI + t] = s * P[k];
     }
   }

@@ -4,6 +4,7 @@
 // only every `check_every` iterations.
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <type_traits>
 #include <vector>
 
@@ -456,6 +457,22 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
   SolverWork& w = x.w;
   *inner = 0;
   x.outer = o.outer_apply == NHMF_DF64 ? NHMF_DF64 : NHMF_FP64;  // the flexible solvers' outer applies
+  // host-side fault injection: a preconditioner that returns z = 0 (a stalled flexible solve),
+  // a network whose output is noise
+  const bool learned_any = o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED ||
+                           o.solver == NHMF_SOLVER_MIXED_GMG_LEARNED;
+  const bool stall = o.solver != NHMF_SOLVER_JACOBI_CG && take_inject(x.c, NHMF_INJECT_CG_STALL);
+  const bool garbage = learned_any && take_inject(x.c, NHMF_INJECT_UNET_GARBAGE);
+  auto zero = [&](double* z) -> nhmf_status {
+    return cuda_check(x.c, cudaMemsetAsync(z, 0, x.n * sizeof(double), x.s), "injected stall");
+  };
+  // a flexible solve that broke down (p^T A p <= 0) is solved again by Jacobi-CG from scratch
+  auto restart_cg = [&]() -> nhmf_status {
+    *fallbacks += 1;
+    cudaMemsetAsync(x.c->status, 0, sizeof(unsigned), x.s);
+    return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
+                       o.check_every, RZ0, outer, relres);
+  };
   if (o.solver == NHMF_SOLVER_JACOBI_CG) {
     UNet* u = x.c->unet;
     if (!(o.record_pairs && u && u->npairs < u->cap))
@@ -477,8 +494,11 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     return cuda_check(x.c, cudaGetLastError(), "pair recording");
   }
   if (o.solver == NHMF_SOLVER_MIXED_FCG) {
-    auto precond = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
-    return fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+    auto precond = [&](const double* r, double* z) -> nhmf_status {
+      return stall ? zero(z) : mixed_inner(x, o, r, z, inner);
+    };
+    const nhmf_status st = fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
+    return st == NHMF_ERR_BREAKDOWN ? restart_cg() : st;
   }
   // fall back to Jacobi-CG on the remaining residual w.r of a stalled flexible solve:
   // A d = r, sol += d
@@ -536,6 +556,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     const int ltop = (int)x.c->gmg->L.size() - 1;
     const int strat32 = o.strategy == NHMF_SPATIAL ? NHMF_ON_THE_FLY : o.strategy;
     auto precond = [&](const double* r, double* z) -> nhmf_status {
+      if (stall) return zero(z);
       if (!f32) return vcycle<double>(x.c, ltop, o, r, z, x.s, inner);
       norm2(x.n, r, w.sc + TMP, w.partials, x.s);
       to_fp32_scaled(x.n, r, w.sc + TMP, true, top.b32, x.s);
@@ -561,6 +582,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
           // training pairs are normalised): z += omega c with the A-optimal step
           // omega = (c . t) / (c . A c), A c from an FP32 apply
           unet_precondition(x.c, w.t, w.x2, x.s);
+          if (garbage) fill_noise(x.n, w.x2, 0x5EEDull + (unsigned long long)jprec, x.s);
           norm2(x.n, w.x2, w.sc + CNORM, w.partials, x.s);
           to_fp32_scaled(x.n, w.x2, w.sc + CNORM, true, top.b32, x.s);
           if ((s2 = launch_apply(x.c, NHMF_FP32, strat32, top.b32, top.r32, x.s)) != NHMF_OK) return s2;
@@ -576,6 +598,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     if (learned) {
       st = fcg(x, o.strategy, b, sol, o.linear_rtol, std::max(1, o.linear_max_iter / 4), precond, outer, relres,
                o.learned_stall_window, o.learned_stall_factor);
+      if (st == NHMF_ERR_BREAKDOWN) return restart_cg();
       return st == NHMF_ERR_NOT_CONVERGED ? fallback_cg() : st;
     }
     st = fcg(x, o.strategy, b, sol, o.linear_rtol, o.linear_max_iter, precond, outer, relres);
@@ -585,18 +608,20 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
     }
     if (st != NHMF_ERR_BREAKDOWN) return st;
     // a breakdown left: solve with Jacobi-CG from scratch (the reference solver of the method)
-    *fallbacks += 1;
-    cudaMemsetAsync(x.c->status, 0, sizeof(unsigned), x.s);
-    return pcg<double>(x, o.strategy, b, sol, w.dinv, w.r, w.z, w.p, w.q, o.linear_rtol, o.linear_max_iter,
-                       o.check_every, RZ0, outer, relres);
+    return restart_cg();
   }
   if (o.solver == NHMF_SOLVER_LEARNED_FCG || o.solver == NHMF_SOLVER_MIXED_LEARNED) {
     if (!x.c->unet) return fail(x.c, NHMF_ERR_STATE, "learned preconditioner: no network in this context");
+    long long napp = 0;
     auto network = [&](const double* r, double* z) -> nhmf_status {
+      if (stall) return zero(z);
       unet_precondition(x.c, r, z, x.s);
+      if (garbage) fill_noise(x.n, z, 0x5EEDull + (unsigned long long)napp++, x.s);
       return cuda_check(x.c, cudaGetLastError(), "network direction");
     };
-    auto inner_cg = [&](const double* r, double* z) -> nhmf_status { return mixed_inner(x, o, r, z, inner); };
+    auto inner_cg = [&](const double* r, double* z) -> nhmf_status {
+      return stall ? zero(z) : mixed_inner(x, o, r, z, inner);
+    };
     const int cap = std::max(1, o.linear_max_iter / 4);
     nhmf_status st =
         o.solver == NHMF_SOLVER_LEARNED_FCG
@@ -604,6 +629,7 @@ nhmf_status linear(Ctx& x, const nhmf_solve_opts& o, const double* b, double* so
                   o.learned_stall_factor)
             : mpcg2(x, o.strategy, b, sol, o.linear_rtol, cap, inner_cg, network, outer, relres,
                     o.learned_stall_window, o.learned_stall_factor);
+    if (st == NHMF_ERR_BREAKDOWN) return restart_cg();
     if (st != NHMF_ERR_NOT_CONVERGED) return st;
     return fallback_cg();
   }
@@ -695,6 +721,8 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
                                      ((cache_mask(*o) & NHMF_CACHE_DF64) && !c->cachedf)))
     return fail(c, NHMF_ERR_STATE, "linear_solve: the cached strategy needs the point caches");
   if ((st = ensure_work(c)) != NHMF_OK) return st;
+  NvtxRange range("nhmf_linear_solve");
+  const auto t0 = std::chrono::steady_clock::now();
   Ctx x{c, c->work->stream, 3 * c->g.M3, *c->work};
   cudaEventRecord(x.w.ev_in, static_cast<cudaStream_t>(stream));
   cudaStreamWaitEvent(x.s, x.w.ev_in, 0);
@@ -715,7 +743,12 @@ nhmf_status nhmf_linear_solve(nhmf_ctx* c, const nhmf_solve_opts* o, const doubl
   if ((st = norm(x, x.w.t, TMP, &rn)) != NHMF_OK) return finish(st);
   if ((st = norm(x, b, TMP, &bn)) != NHMF_OK) return finish(st);
   *rel_res = bn > 0 ? rn / bn : 0.0;
-  return finish(NHMF_OK);
+  const nhmf_status done = finish(NHMF_OK);
+  metrics_line(c, "\"event\": \"linear_solve\", \"solver\": %d, \"iters\": %lld, \"inner_iters\": %lld, "
+               "\"fallbacks\": %d, \"rel_residual\": %.6e, \"seconds\": %.6f",
+               o->solver, *iters, *inner_iters, fb, *rel_res,
+               std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+  return done;
 }
 
 static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_solve_stats* stats) {
@@ -737,12 +770,14 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
   const auto t_all = clk::now();
   for (int step = first; step <= last; ++step) {
     const int k = step - first;
+    NvtxRange step_range("load step");
     const auto t0 = clk::now();
     const double top = c->prm.bc == NHMF_BC_COMPRESSION ? -o->compression * step / S : 0.0;
     double ref = -1.0, bnh = 0.0;
     bool converged = false;
     int it = 0;
     for (; it <= o->newton_max_iter; ++it) {
+      NvtxRange iter_range("newton iteration");
       if ((st = launch_residual(c, u, w.R, x.s)) != NHMF_OK) return st;
       if ((st = nhmf_check_status(c, x.s)) != NHMF_OK) return st;
       cudaMemsetAsync(w.d, 0, x.n * sizeof(double), x.s);
@@ -767,6 +802,12 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
       long long outer = 0, inner = 0;
       double rel = 0.0;
       if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel, &stats->fallbacks[k])) != NHMF_OK) return st;
+      if (take_inject(c, NHMF_INJECT_NAN_DU)) {  // host-side fault injection: a NaN in the update
+        const double nan = std::numeric_limits<double>::quiet_NaN();
+        if ((st = cuda_check(c, cudaMemcpyAsync(w.du + x.n / 2, &nan, sizeof(double), cudaMemcpyHostToDevice, x.s),
+                             "injected NaN")) != NHMF_OK)
+          return st;
+      }
       if (o->record_pairs && o->solver == NHMF_SOLVER_JACOBI_CG && c->unet) {
         if ((st = unet_record(c, w.b, w.du, x.s)) != NHMF_OK) return st;   // Newton pair (b, du)
         for (int q = 0; q < o->synthetic_pairs; ++q) {                     // (K e, e), smooth e
@@ -794,6 +835,11 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
         theta *= 0.5;
       }
       if (!ok) return fail(c, NHMF_ERR_NONPOS_J, "Newton: backtracking could not keep det F > 0");
+      metrics_line(c, "\"event\": \"newton_iteration\", \"step\": %d, \"iteration\": %d, \"rel_residual\": %.6e, "
+                   "\"linear_iters\": %lld, \"inner_iters\": %lld, \"linear_rel_residual\": %.6e, \"theta\": %.6g, "
+                   "\"seconds\": %.6f",
+                   step, it, ref > 0.0 ? bnh / ref : 0.0, outer, inner, rel, theta,
+                   std::chrono::duration<double>(clk::now() - t0).count());
       cudaMemcpyAsync(u, w.utry, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
       if (theta == 1.0 && c->prm.bc != NHMF_BC_NONE)
         k_bc<<<bc_blocks, 256, 0, x.s>>>(c->prm.bc, c->g.M, c->g.M3, top, u, nullptr, 1);  // u_D = g exactly
@@ -805,6 +851,11 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
     stats->total_linear_iters += stats->linear_iters[k];
     stats->total_inner_iters += stats->inner_iters[k];
     stats->steps_done = k + 1;
+    metrics_line(c, "\"event\": \"load_step\", \"step\": %d, \"newton_iters\": %d, \"linear_iters\": %lld, "
+                 "\"inner_iters\": %lld, \"fallbacks\": %d, \"rel_residual\": %.6e, \"seconds\": %.6f, "
+                 "\"converged\": %s",
+                 step, it, stats->linear_iters[k], stats->inner_iters[k], stats->fallbacks[k], stats->rel_residual[k],
+                 stats->seconds[k], converged ? "true" : "false");
     if (!converged) {
       stats->total_seconds = std::chrono::duration<double>(clk::now() - t_all).count();
       return fail(c, NHMF_ERR_NOT_CONVERGED, "Newton: load step " + std::to_string(step) + " did not converge");
@@ -820,6 +871,7 @@ nhmf_status nhmf_solve(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, nhmf_so
   if (!c) return NHMF_ERR_ARG;
   nhmf_status st = ensure_work(c);
   if (st != NHMF_OK) return st;
+  NvtxRange range("nhmf_solve");
   // the solver runs on the context's own stream, ordered after the caller's stream
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaEventRecord(c->work->ev_in, cs);

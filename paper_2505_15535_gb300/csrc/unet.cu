@@ -1709,6 +1709,7 @@ nhmf_status nhmf_unet_train(nhmf_ctx* c, int epochs, double lr, double* loss_fir
   if (epochs < 1 || !(lr > 0.0) || !loss_first || !loss_last) return fail(c, NHMF_ERR_ARG, "unet_train: bad argument");
   UNet& u = *c->unet;
   if (u.npairs == 0) return fail(c, NHMF_ERR_STATE, "unet_train: no recorded pairs");
+  NvtxRange range("nhmf_unet_train");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t pair_stride = (size_t)2 * 3 * u.N0;
   for (int ep = 0; ep < epochs; ++ep) {

@@ -20,6 +20,7 @@ NHMF_ON_THE_FLY, NHMF_CACHED, NHMF_SPATIAL = 0, 1, 2
 NHMF_BC_NONE, NHMF_BC_CLAMP_X0, NHMF_BC_COMPRESSION = 0, 1, 2
 NHMF_CACHE_FP64, NHMF_CACHE_FP32, NHMF_CACHE_DF64, NHMF_CACHE_SPATIAL = 1, 2, 4, 8
 NHMF_KIND_APPLY, NHMF_KIND_CACHE, NHMF_KIND_RESIDUAL, NHMF_KIND_DIAGONAL = 0, 1, 2, 3
+NHMF_INJECT_NAN_DU, NHMF_INJECT_CG_STALL, NHMF_INJECT_UNET_GARBAGE, NHMF_INJECT_UNKNOWN = 1, 2, 4, 1 << 30
 
 
 class NhmfError(RuntimeError):
@@ -108,6 +109,10 @@ _SIGS = {
     "nhmf_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong)]),
     "nhmf_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "nhmf_set_inject": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "nhmf_inject_pending": (ctypes.c_uint, [_P]),
+    "nhmf_parse_inject": (ctypes.c_uint, [ctypes.c_char_p]),
+    "nhmf_set_metrics_log": (ctypes.c_int, [_P, ctypes.c_char_p]),
 }
 
 
@@ -211,6 +216,22 @@ def nhmf_profile_read(ctx, kind):
     n = ctypes.c_longlong()
     _check(ctx, lib().nhmf_profile_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def nhmf_set_inject(ctx, flags):
+    _check(ctx, lib().nhmf_set_inject(ctx, flags))
+
+
+def nhmf_inject_pending(ctx):
+    return lib().nhmf_inject_pending(ctx)
+
+
+def nhmf_parse_inject(spec):
+    return lib().nhmf_parse_inject(spec.encode() if spec is not None else None)
+
+
+def nhmf_set_metrics_log(ctx, path):
+    _check(ctx, lib().nhmf_set_metrics_log(ctx, path.encode() if path else None))
 
 
 def nhmf_measure_fma_peak(precision):
