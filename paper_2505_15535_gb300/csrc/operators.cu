@@ -22,7 +22,7 @@ namespace {
 // Table slots ahead of the per-item arrays: B, Dc, D, n^3 weights and NE factors, or in the
 // apply B, Dc, BW, DcW, Dch, 3 even-odd sets and NE factors (whichever is larger).
 constexpr int kTabSlots = 3 * kMaxN * kMaxN + 128 + 32;
-static_assert(5 * kMaxN * kMaxN + 3 * kEoSlots + 32 <= kTabSlots, "apply tables exceed the table slots");
+static_assert(5 * kMaxN * kMaxN + 4 * kEoSlots + 32 <= kTabSlots, "apply tables exceed the table slots");
 
 template <int P, typename T>
 __device__ __forceinline__ void load_tables(const OpArgs& a, T* sB, T* sDc, T* sD, T* sW, double wscale) {
@@ -48,7 +48,7 @@ __device__ __forceinline__ void load_apply_tables(const OpArgs& a, T* tab) {
     tab[3 * S + i] = T(a.DcW[i]);
     tab[4 * S + i] = T(a.Dch[i]);
   }
-  for (int i = threadIdx.x; i < 3 * kEoSlots; i += blockDim.x)
+  for (int i = threadIdx.x; i < 4 * kEoSlots; i += blockDim.x)
     tab[5 * S + i] = T(a.eo[i / kEoSlots][i % kEoSlots]);
 }
 
@@ -147,12 +147,15 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 // dP / mu without any scaling.  For odd n (Q2, Q4) every non-accumulating pass (forward B,
 // forward collocation derivative, transposed B) runs one thread per line in even-odd form, and
 // the gradient of du reaches the point code through shared memory.
+#ifndef NHMF_EO_GRADT
+#define NHMF_EO_GRADT 1
+#endif
 template <int P, typename T, int STRAT, int MODEL>
 __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
   constexpr int S = kMaxN * kMaxN, TH = LaunchCfg<P, T, STRAT>::THREADS;
   constexpr bool EO = n % 2 == 1;
-  static_assert(5 * S + 3 * kEoSlots + NE <= kTabSlots, "the factor table exceeds the table slots");
+  static_assert(5 * S + 4 * kEoSlots + NE <= kTabSlots, "the factor table exceeds the table slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);
   const T* sB = tab;
@@ -160,10 +163,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   const T* sBW = tab + 2 * S;
   const T* sDcW = tab + 3 * S;
   const T* sDch = tab + 4 * S;
-  const T* kB = tab + 5 * S;                    // even-odd coefficients of B, Dc, BW^T
+  const T* kB = tab + 5 * S;                    // even-odd coefficients of B, Dc, BW^T, DcW^T
   const T* kDc = kB + kEoSlots;
   const T* kBW = kDc + kEoSlots;
-  T* sF = tab + 5 * S + 3 * kEoSlots;          // [NE] material factors of the block's elements
+  const T* kDcWT = kBW + kEoSlots;              // even-odd coefficients of DcW^T
+  T* sF = tab + 5 * S + 4 * kEoSlots;          // [NE] material factors of the block's elements
   T* U = tab + kTabSlots;                       // [3][NI] ubar at the points (on the fly)
   T* Vq = U + (STRAT == NHMF_ON_THE_FLY ? 3 * NI : 0);  // [3][NI] du at the points
   T* G = Vq + 3 * NI;                           // [9][NI] gradients, then fluxes; G[0..2] gathers
@@ -295,7 +299,16 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   if (bad) atomicOr(a.status, kStatusNonPosJ);
   __syncthreads();
   if constexpr (EO) {
-    colloc_grad_T<n, NI>(sDcW, G, Vq, nitems);
+    if constexpr (std::is_same<T, float>::value && NHMF_EO_GRADT) {
+      // FP32: the transposed derivative as three even-odd line passes, Vq[c] = sum_d DcW^T_d G[3c+d]
+      eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 1, 0, 3, 0, false>(kDcWT, G, Vq, nlines);
+      __syncthreads();
+      eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 1, 0, 3, 1, true>(kDcWT, G, Vq, nlines);
+      __syncthreads();
+      eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 1, 0, 3, 2, true>(kDcWT, G, Vq, nlines);
+    } else {
+      colloc_grad_T<n, NI>(sDcW, G, Vq, nitems);
+    }
     __syncthreads();
     eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G, nlines);
     __syncthreads();
@@ -925,19 +938,21 @@ OpArgs base_args(nhmf_ctx* c) {
     a.wf[q] = float(c->tab.w[q]);
   }
   // tables of the tangent apply (see OpArgs)
-  double BWt[kMaxN * kMaxN];
+  double BWt[kMaxN * kMaxN], DcWt[kMaxN * kMaxN];
   for (int q = 0; q < n; ++q)
     for (int i = 0; i < n; ++i) {
       const double wq = c->tab.w[q];
       a.BW[q * n + i] = c->tab.B[q][i] * wq;
       BWt[i * n + q] = a.BW[q * n + i];
       a.DcW[q * n + i] = c->tab.Dc[q][i] * wq / c->tab.w[i] * c->prm.mu * c->g.h;
+      DcWt[i * n + q] = a.DcW[q * n + i];
       a.Dch[q * n + i] = c->tab.Dc[q][i] / c->g.h;
     }
   if (n % 2 == 1) {
     eo_pack(a.B, n, a.eo[0]);
     eo_pack(a.Dc, n, a.eo[1]);
     eo_pack(BWt, n, a.eo[2]);
+    eo_pack(DcWt, n, a.eo[3]);  // DcW^T is anti-centro-symmetric like Dc (symmetric weights)
   }
   a.r2mu = 2.0 * c->prm.lambda / c->prm.mu;
   a.reg32 = c->reg32 ? 1 : 0;
@@ -946,7 +961,7 @@ OpArgs base_args(nhmf_ctx* c) {
     a.DcWf[i] = float(a.DcW[i]);
     a.Dchf[i] = float(a.Dch[i]);
   }
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     for (int i = 0; i < kEoSlots; ++i) a.eof[k][i] = float(a.eo[k][i]);
   a.status = c->status;
   a.factor = c->factor;

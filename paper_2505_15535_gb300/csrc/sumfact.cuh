@@ -76,12 +76,13 @@ struct OpArgs {
   // Tables of the tangent apply, which carry the quadrature weight, mu and h so that its
   // point code returns dP / mu unweighted:
   //   BW[q][i] = B[q][i] w_q,  DcW[m][r] = Dc[m][r] w_m / w_r mu h,  Dch = Dc / h,
-  //   eo[0..2]: even-odd coefficients of B, Dc and BW^T (odd n, see eo_line), r2mu = 2 lambda / mu.
+  //   eo[0..3]: even-odd coefficients of B, Dc, BW^T and DcW^T (odd n, see eo_line),
+  //   r2mu = 2 lambda / mu.
   double BW[kMaxN * kMaxN], DcW[kMaxN * kMaxN], Dch[kMaxN * kMaxN];
-  double eo[3][kEoSlots];
+  double eo[4][kEoSlots];
   double r2mu;
   int reg32;  // FP32 point cache in the register kernel's [10][n^3][E] layout (see kRegMaxP)
-  float BWf[kMaxN * kMaxN], DcWf[kMaxN * kMaxN], Dchf[kMaxN * kMaxN], eof[3][kEoSlots];  // FP32 copies
+  float BWf[kMaxN * kMaxN], DcWf[kMaxN * kMaxN], Dchf[kMaxN * kMaxN], eof[4][kEoSlots];  // FP32 copies
   float Bf[kMaxN * kMaxN], Dcf[kMaxN * kMaxN], wf[kMaxN];  // FP32 copies (register kernels)
   const double* u64;
   const float* u32;
@@ -268,12 +269,13 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 }
 
 // One 1D pass along DIR over NC fields with one thread per (field, line of n items), odd n:
-//   out[(c OS + OO)][line] = M in[c][line]
+//   out[(c OS + OO)][line] (+)= M in[(c IS + IO)][line]  (+= when ACC)
 // where M is given by its even-odd coefficients `coef` (see eo_line).
 // TH is the block size; the task loop is unrolled so that independent lines interleave (not for
 // double-float, whose unrolled lines would cost an SM its second block).
 // Lines of absent elements (line index >= nlines; they come last) are skipped.
-template <int n, int NI, int NC, int DIR, bool ANTI, int FORM, int TH, int OS = 1, int OO = 0, typename T>
+template <int n, int NI, int NC, int DIR, bool ANTI, int FORM, int TH, int OS = 1, int OO = 0, int IS = 1,
+          int IO = 0, bool ACC = false, typename T>
 __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __restrict__ in,
                                         T* __restrict__ out, int nlines = NI / n) {
   constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n, ITER = (NC * NL + TH - 1) / TH;
@@ -291,10 +293,15 @@ __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __r
                    : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
     T x[n], y[n];
 #pragma unroll
-    for (int m = 0; m < n; ++m) x[m] = in[c * NI + base + m * s];
+    for (int m = 0; m < n; ++m) x[m] = in[(c * IS + IO) * NI + base + m * s];
     eo_line<n, ANTI, FORM>(k, x, y);
 #pragma unroll
-    for (int m = 0; m < n; ++m) out[(c * OS + OO) * NI + base + m * s] = y[m];
+    for (int m = 0; m < n; ++m) {
+      if (ACC)
+        out[(c * OS + OO) * NI + base + m * s] += y[m];
+      else
+        out[(c * OS + OO) * NI + base + m * s] = y[m];
+    }
   }
 }
 
