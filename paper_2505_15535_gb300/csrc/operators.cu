@@ -150,6 +150,9 @@ __device__ __forceinline__ void from_points(const T* sB, const T* sDc, T* G, T* 
 #ifndef NHMF_EO_GRADT
 #define NHMF_EO_GRADT 1
 #endif
+#ifndef NHMF_LINEMAP
+#define NHMF_LINEMAP 1
+#endif
 template <int P, typename T, int STRAT, int MODEL>
 __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const OpArgs a) {
   constexpr int n = P + 1, n3 = n * n * n, NE = LaunchCfg<P, T, STRAT>::NE, NI = NE * n3;
@@ -172,6 +175,10 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   T* Vq = U + (STRAT == NHMF_ON_THE_FLY ? 3 * NI : 0);  // [3][NI] du at the points
   T* G = Vq + 3 * NI;                           // [9][NI] gradients, then fluxes; G[0..2] gathers
 
+  // FP32: the passes' task decomposition computed once (the FP32 kernel is issue bound)
+  using LM = typename std::conditional<std::is_same<T, float>::value && NHMF_LINEMAP && EO, LineMap<n, NI, TH>,
+                                       NoLineMap>::type;
+  const LM lm{};
   load_apply_tables<P>(a, tab);
   const long long e0 = (long long)blockIdx.x * NE;
   const int nvalid = (int)min((long long)NE, (long long)a.col.count - e0);
@@ -186,11 +193,11 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
       gather<P, NI>(a, a.u32, e0, nvalid, false, G);
     __syncthreads();
     if constexpr (EO) {
-      eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
+      eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines, lm);
       __syncthreads();
-      eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines);
+      eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines, lm);
       __syncthreads();
-      eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, U, nlines);
+      eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, U, nlines, lm);
       __syncthreads();
     } else {
       to_points<n, NI>(sB, G, Vq, U, nitems);
@@ -200,16 +207,16 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
                 a.factor ? (const T*)sF : nullptr);
   __syncthreads();
   if constexpr (EO) {
-    eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
+    eo_pass<n, NI, 3, 0, false, kEoCentreRow, TH>(kB, G, Vq, nlines, lm);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines);
+    eo_pass<n, NI, 3, 1, false, kEoCentreRow, TH>(kB, Vq, G, nlines, lm);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, Vq, nlines);
+    eo_pass<n, NI, 3, 2, false, kEoCentreRow, TH>(kB, G, Vq, nlines, lm);
     __syncthreads();
     // reference gradient of du: G[3c+d] = Dc along d of du[c]
-    eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 3, 0>(kDc, Vq, G, nlines);
-    eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 3, 1>(kDc, Vq, G, nlines);
-    eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 3, 2>(kDc, Vq, G, nlines);
+    eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 3, 0>(kDc, Vq, G, nlines, lm);
+    eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 3, 1>(kDc, Vq, G, nlines, lm);
+    eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 3, 2>(kDc, Vq, G, nlines, lm);
     __syncthreads();
   } else {
     to_points<n, NI>(sB, G, Vq + 0, Vq, nitems);  // passes ping-pong via G: x G->Vq, y Vq->G, z G->Vq
@@ -301,20 +308,20 @@ __global__ void __launch_bounds__(LaunchCfg<P, T, STRAT>::THREADS) k_apply(const
   if constexpr (EO) {
     if constexpr (std::is_same<T, float>::value && NHMF_EO_GRADT) {
       // FP32: the transposed derivative as three even-odd line passes, Vq[c] = sum_d DcW^T_d G[3c+d]
-      eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 1, 0, 3, 0, false>(kDcWT, G, Vq, nlines);
+      eo_pass<n, NI, 3, 0, true, kEoGeneral, TH, 1, 0, 3, 0, false>(kDcWT, G, Vq, nlines, lm);
       __syncthreads();
-      eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 1, 0, 3, 1, true>(kDcWT, G, Vq, nlines);
+      eo_pass<n, NI, 3, 1, true, kEoGeneral, TH, 1, 0, 3, 1, true>(kDcWT, G, Vq, nlines, lm);
       __syncthreads();
-      eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 1, 0, 3, 2, true>(kDcWT, G, Vq, nlines);
+      eo_pass<n, NI, 3, 2, true, kEoGeneral, TH, 1, 0, 3, 2, true>(kDcWT, G, Vq, nlines, lm);
     } else {
       colloc_grad_T<n, NI>(sDcW, G, Vq, nitems);
     }
     __syncthreads();
-    eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G, nlines);
+    eo_pass<n, NI, 3, 0, false, kEoCentreCol, TH>(kBW, Vq, G, nlines, lm);
     __syncthreads();
-    eo_pass<n, NI, 3, 1, false, kEoCentreCol, TH>(kBW, G, Vq, nlines);
+    eo_pass<n, NI, 3, 1, false, kEoCentreCol, TH>(kBW, G, Vq, nlines, lm);
     __syncthreads();
-    eo_pass<n, NI, 3, 2, false, kEoCentreCol, TH>(kBW, Vq, G + 3 * NI, nlines);
+    eo_pass<n, NI, 3, 2, false, kEoCentreCol, TH>(kBW, Vq, G + 3 * NI, nlines, lm);
     __syncthreads();
   } else {
     from_points<n, NI>(sBW, sDcW, G, Vq, G + 3 * NI, nitems);

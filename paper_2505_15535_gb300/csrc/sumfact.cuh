@@ -268,6 +268,26 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
   }
 }
 
+// The tasks of a pass over 3 fields with one thread per (field, line): this thread's field,
+// line and line start for each direction, computed once per kernel instead of in every pass.
+struct NoLineMap {};
+template <int n, int NI, int TH>
+struct LineMap {
+  static constexpr int NL = NI / n, ITER = (3 * NL + TH - 1) / TH;
+  int c[ITER], L[ITER], base[3][ITER];
+  __device__ __forceinline__ LineMap() {
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+      const int task = threadIdx.x + it * TH;
+      c[it] = task / NL;  // >= 3: no task
+      L[it] = task - c[it] * NL;
+      base[0][it] = L[it] * n;
+      base[1][it] = (L[it] % n) + (L[it] / n) * n * n;
+      base[2][it] = (L[it] % (n * n)) + (L[it] / (n * n)) * n * n * n;
+    }
+  }
+};
+
 // One 1D pass along DIR over NC fields with one thread per (field, line of n items), odd n:
 //   out[(c OS + OO)][line] (+)= M in[(c IS + IO)][line]  (+= when ACC)
 // where M is given by its even-odd coefficients `coef` (see eo_line).
@@ -275,9 +295,9 @@ __device__ __forceinline__ void eo_line(const T (&k)[kEoSlots], const T (&x)[n],
 // double-float, whose unrolled lines would cost an SM its second block).
 // Lines of absent elements (line index >= nlines; they come last) are skipped.
 template <int n, int NI, int NC, int DIR, bool ANTI, int FORM, int TH, int OS = 1, int OO = 0, int IS = 1,
-          int IO = 0, bool ACC = false, typename T>
+          int IO = 0, bool ACC = false, typename T, typename MAP = NoLineMap>
 __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __restrict__ in,
-                                        T* __restrict__ out, int nlines = NI / n) {
+                                        T* __restrict__ out, int nlines = NI / n, const MAP& map = MAP()) {
   constexpr int s = DIR == 0 ? 1 : (DIR == 1 ? n : n * n), NL = NI / n, ITER = (NC * NL + TH - 1) / TH;
   constexpr int UNROLL = std::is_same<T, df64>::value ? 1 : ITER;
   T k[kEoSlots];
@@ -285,12 +305,22 @@ __device__ __forceinline__ void eo_pass(const T* __restrict__ coef, const T* __r
   for (int i = 0; i < kEoSlots; ++i) k[i] = coef[i];
 #pragma unroll UNROLL
   for (int it = 0; it < ITER; ++it) {
-    const int task = threadIdx.x + it * TH;
-    if (ITER * TH != NC * NL && task >= NC * NL) break;
-    const int c = task / NL, L = task - c * NL;
+    int c, L, base;
+    if constexpr (std::is_same<MAP, NoLineMap>::value) {
+      const int task = threadIdx.x + it * TH;
+      if (ITER * TH != NC * NL && task >= NC * NL) break;
+      c = task / NL;
+      L = task - c * NL;
+      base = DIR == 0 ? L * n
+                      : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
+    } else {
+      static_assert(NC == 3 && MAP::ITER == ITER && MAP::NL == NL, "a line map covers passes over 3 fields");
+      c = map.c[it];
+      if (ITER * TH != NC * NL && c >= NC) break;
+      L = map.L[it];
+      base = map.base[DIR][it];
+    }
     if (L >= nlines) continue;
-    const int base = DIR == 0 ? L * n
-                   : (DIR == 1 ? (L % n) + (L / n) * n * n : (L % (n * n)) + (L / (n * n)) * n * n * n);
     T x[n], y[n];
 #pragma unroll
     for (int m = 0; m < n; ++m) x[m] = in[(c * IS + IO) * NI + base + m * s];
