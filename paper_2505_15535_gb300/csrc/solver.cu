@@ -778,6 +778,7 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
     int it = 0;
     for (; it <= o->newton_max_iter; ++it) {
       NvtxRange iter_range("newton iteration");
+      const auto t_it = clk::now();
       if ((st = launch_residual(c, u, w.R, x.s)) != NHMF_OK) return st;
       if ((st = nhmf_check_status(c, x.s)) != NHMF_OK) return st;
       cudaMemsetAsync(w.d, 0, x.n * sizeof(double), x.s);
@@ -801,7 +802,11 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
       if ((st = update_diagonal(x)) != NHMF_OK) return st;
       long long outer = 0, inner = 0;
       double rel = 0.0;
+      if (c->metrics) cudaStreamSynchronize(x.s);  // split the iteration's time at the linear solve
+      const auto t_lin = clk::now();
       if ((st = linear(x, *o, w.b, w.du, &outer, &inner, &rel, &stats->fallbacks[k])) != NHMF_OK) return st;
+      if (c->metrics) cudaStreamSynchronize(x.s);
+      const auto t_lin_end = clk::now();
       if (take_inject(c, NHMF_INJECT_NAN_DU)) {  // host-side fault injection: a NaN in the update
         const double nan = std::numeric_limits<double>::quiet_NaN();
         if ((st = cuda_check(c, cudaMemcpyAsync(w.du + x.n / 2, &nan, sizeof(double), cudaMemcpyHostToDevice, x.s),
@@ -837,8 +842,11 @@ static nhmf_status solve_impl(nhmf_ctx* c, const nhmf_solve_opts* o, double* u, 
       if (!ok) return fail(c, NHMF_ERR_NONPOS_J, "Newton: backtracking could not keep det F > 0");
       metrics_line(c, "\"event\": \"newton_iteration\", \"step\": %d, \"iteration\": %d, \"rel_residual\": %.6e, "
                    "\"linear_iters\": %lld, \"inner_iters\": %lld, \"linear_rel_residual\": %.6e, \"theta\": %.6g, "
-                   "\"seconds\": %.6f",
+                   "\"setup_seconds\": %.6f, \"linear_seconds\": %.6f, \"update_seconds\": %.6f, \"seconds\": %.6f",
                    step, it, ref > 0.0 ? bnh / ref : 0.0, outer, inner, rel, theta,
+                   std::chrono::duration<double>(t_lin - t_it).count(),
+                   std::chrono::duration<double>(t_lin_end - t_lin).count(),
+                   std::chrono::duration<double>(clk::now() - t_lin_end).count(),
                    std::chrono::duration<double>(clk::now() - t0).count());
       cudaMemcpyAsync(u, w.utry, x.n * sizeof(double), cudaMemcpyDeviceToDevice, x.s);
       if (theta == 1.0 && c->prm.bc != NHMF_BC_NONE)
