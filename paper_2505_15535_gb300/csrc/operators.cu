@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
   const long long node = ij + (long long)M * M * blockIdx.y, M3 = (long long)M * M * M;
   const unsigned long long done_pol = l2_evict_first();  // each element-local value is read once
   // per direction: the element below the node (local index P), if any, then the element at or
-  // above it (local index g % P); absent elements get a clamped (valid) index and are masked
-  // after the load, so that all 24 loads are independent and in flight together
+  // above it (local index g % P); an absent element in x gets a clamped (valid) index and is
+  // masked after the load
   int el[3][2], lo[3][2];
   bool has[3][2];
 #pragma unroll
@@ -605,11 +605,17 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
     el[d][1] = min(gp, N - 1);
     lo[d][1] = gr;
   }
+  // the (z, y) element pairs are the same for every node of a grid row, so a warp skips the
+  // absent ones as a whole (a branch, not 6 issued loads); the loads of the present ones are
+  // issued before any of them is used
   float val[3][8];
 #pragma unroll
   for (int z = 0; z < 2; ++z)
 #pragma unroll
-    for (int y = 0; y < 2; ++y)
+    for (int y = 0; y < 2; ++y) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) val[c][4 * z + 2 * y] = val[c][4 * z + 2 * y + 1] = 0.f;
+      if (!(has[2][z] && has[1][y])) continue;
 #pragma unroll
       for (int x = 0; x < 2; ++x) {
         const unsigned e = (unsigned)el[0][x] + (unsigned)N * ((unsigned)el[1][y] + (unsigned)N * (unsigned)el[2][z]);
@@ -618,6 +624,7 @@ __global__ void __launch_bounds__(256) k_gather_local(const float* __restrict__ 
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c][4 * z + 2 * y + x] = ld_policy(src + c * n3 * kTile, done_pol);
       }
+    }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float s = 0.f;
