@@ -820,6 +820,205 @@ __global__ void __launch_bounds__(kTcSThreads) k_conv_tc(const ConvArgs a, const
   tc_teardown(tmem, kTcSCols, timed_out, status);
 }
 
+// ------------------------------------------------------------------ stride-2 conv on tcgen05
+// out[o] = sum_d W_d in[2 o + d] (the down-convolution and the up layers' backward-data) in the
+// plane-streaming form of k_conv_tc, with planes staged by cp.async.  A tile is 128
+// consecutive coarse positions of one output plane in x-padded row order (R = W + 2 for an
+// x-strip of W coarse columns from x0).  A fine plane f is staged as four parity sub-planes
+// (py, px): row j of a sub-plane is padded coarse position P0 + j = Y R + X (P0 = p0 - R - 1,
+// L = R + 129 rows) and holds the fine voxel (2 (x0 + X - 1) + px, 2 Y + py, f), zero outside the
+// grid, so that tap (dx, dy) reads a contiguous 128-row window of sub-plane (dy != 0, dx != 0)
+// from row R + 1 + sx + sy R (s = -1 for d = -1, else 0).  Plane f adds to output f / 2 (dz = 0) if f is
+// even and to outputs (f - 1) / 2 (dz = +1) and (f + 1) / 2 (dz = -1) if f is odd; the weights of
+// each (dx, dy) are a strip of dz = +1, -1, 0 blocks, so one MMA of N = 16 or 32 per (dx, dy)
+// covers the plane's outputs in the column.  Output o is complete after plane min(2 o + 1,
+// m_in - 1) and is read back while later planes run.  One thread of warp 4 issues the MMAs;
+// warps 0-3 stage planes two ahead (three slots) and read accumulators back.
+constexpr int kDnStripMax = 32;
+#ifndef NHMF_DN_SLOTS
+#define NHMF_DN_SLOTS 3
+#endif
+constexpr int kDnSlots = NHMF_DN_SLOTS;  // planes staged up to kDnSlots - 1 ahead
+
+// Wait until at most n (0 .. 3) of this thread's cp.async groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  if (n <= 0)
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (n == 1)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else if (n == 2)
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
+
+__device__ __forceinline__ void dn_weights_strips(const __nv_bfloat16* w, unsigned char* sB) {
+  const uint4* wg = reinterpret_cast<const uint4*>(w);
+  for (int i = threadIdx.x; i < 27 * 16 * 2; i += blockDim.x) {
+    const int tap = i >> 5, co = (i >> 1) & 15, hf = i & 1, dz = tap / 9 - 1;
+    const int r = 16 * (dz == 1 ? 0 : (dz == -1 ? 1 : 2)) + co;
+    *reinterpret_cast<uint4*>(sB + (tap % 9) * 1536 + (r & 7) * 16 + (r >> 3) * 128 + hf * 768) = wg[i];
+  }
+}
+
+// Fine plane f into `slot` ([4 sub-planes][2 halves][L][16 B]) by threads tid = 0 .. nthr - 1.
+__device__ __forceinline__ void dn_stage_async(const __nv_bfloat16* __restrict__ in, int mi, int R, int L, int P0,
+                                               int x0, int f, unsigned char* slot, int tid, int nthr) {
+  const uint32_t s = smem_u32(slot);
+  const uint4* g = reinterpret_cast<const uint4*>(in);
+  const bool plane_in = f >= 0 && f < mi;
+  int Yr = (P0 + tid + 2 * R) / R - 2, Xr = (P0 + tid + 2 * R) % R;  // row and column of P0 + j (P0 >= -R - 1)
+  for (int j = tid; j < L; j += nthr) {
+    const int cx = 2 * (Xr - 1 + x0), cy = 2 * Yr;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int fx = cx + (sp & 1), fy = cy + (sp >> 1);
+      const uint4* src = g;  // a valid address for the zero-filled copies
+      uint32_t bytes = 0;
+      if (plane_in && fx >= 0 && fx < mi && fy >= 0 && fy < mi) {
+        src = g + 2 * (fx + (long long)mi * (fy + (long long)mi * f));
+        bytes = 16;
+      }
+      cp_async16(s + (uint32_t)((2 * sp) * L + j) * 16u, src, bytes);
+      cp_async16(s + (uint32_t)((2 * sp + 1) * L + j) * 16u, src + 1, bytes);
+    }
+    Xr += nthr;
+    while (Xr >= R) {
+      Xr -= R;
+      ++Yr;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+size_t down_tc_smem(int W) {
+  const int L = W + 2 + 129;
+  const size_t need = 9 * 1536 + (size_t)kDnSlots * 4 * 2 * L * 16 + 8 * 2 + 8 + 64;
+  return std::max(need, kTcSSmemMin);
+}
+
+__global__ void __launch_bounds__(kTcSThreads) k_down_tc(const ConvArgs a, int zc, int W, int nstrips,
+                                                         unsigned* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int mo = a.m_out, mi = a.m_in, R = W + 2, L = R + 129;
+  const uint32_t slot_bytes = 4u * 2u * (uint32_t)L * 16u;
+  unsigned char* sB = sm;                                  // [9 strips][1536 B] weights
+  unsigned char* sA = sm + 9 * 1536;                       // [kDnSlots][4 sub-planes][2 halves][L][16 B]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sA + kDnSlots * slot_bytes);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  float* sbias = reinterpret_cast<float*>(bar + 3);        // [16]
+  const uint32_t s_done = smem_u32(bar);
+  const int warp = threadIdx.x >> 5;
+  const bool epi = warp < 4, issuer = threadIdx.x == 128;
+  auto slot = [&](int f) { return sA + (f % kDnSlots) * slot_bytes; };  // f >= 0
+  dn_weights_strips(a.w, sB);
+  if (threadIdx.x < 16) sbias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.f;
+  const uint32_t tmem = tc_alloc_init(tslot, s_done, 2, kTcSCols);  // synchronises the block
+  const uint32_t lanes = tmem + ((32u * (uint32_t)(warp & 3)) << 16);
+  const uint32_t sB0 = smem_u32(sB);
+
+  const int per_plane = (mo * R + 127) / 128, nzc = (mo + zc - 1) / zc;
+  const long long nunits = (long long)per_plane * nstrips * nzc, nvox = (long long)mo * mo * mo;
+  unsigned k = 0, kc = 0;  // planes issued: plane kk commits to mbarrier kk & 1, phase kk >> 1
+  bool timed_out = false;
+  auto plane_done = [&](unsigned kk) { return tc_wait(s_done + 8u * (kk & 1u), (kk >> 1) & 1u); };
+  auto wait_plane = [&](unsigned kk) -> bool {
+    bool done = true;
+    if (threadIdx.x == 0) done = plane_done(kk);
+    if (bar_or_128(!done)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return true;
+  };
+  auto sync_or = [&](bool fail) -> bool {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool any = __syncthreads_or(fail) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return any;
+  };
+  for (long long unit = blockIdx.x; unit < nunits && !timed_out; unit += gridDim.x) {
+    const int p0 = int(unit % per_plane) * 128;
+    const long long rest = unit / per_plane;
+    const int x0 = int(rest % nstrips) * W, zb = int(rest / nstrips) * zc, ze = min(mo, zb + zc);
+    const int ffirst = max(2 * zb - 1, 0), flast = min(2 * ze - 1, mi - 1);  // fine planes of the column
+    const int p = p0 + (int)threadIdx.x, y = p / R, xl = p % R - 1;
+    const bool own = epi && p < mo * R && xl >= 0 && xl < W && x0 + xl < mo;
+    const long long v0 = (x0 + xl) + (long long)mo * y;
+    auto finish = [&](int o) {
+      uint32_t r[16];
+      tc_ld16(lanes + 16u * (uint32_t)(o - zb), r);
+      if (own) {
+        uint4 ad[2], mk[2];
+        tc_load_addmask(a, v0 + (long long)mo * mo * o, ad, mk);
+        tc_emit(a, v0 + (long long)mo * mo * o, nvox, r, sbias, ad, mk);
+      }
+    };
+    if (epi) {
+      for (int c = 0; c < ze - zb; ++c) tc_st16_zero(lanes + 16u * (uint32_t)c);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      const int fpre = min(ffirst + kDnSlots - 2, flast);
+      for (int f = ffirst; f <= fpre; ++f)
+        dn_stage_async(a.in, mi, R, L, p0 - R - 1, x0, f, slot(f), threadIdx.x, 128);
+      cp_async_wait_pending(fpre - ffirst);  // plane ffirst has landed
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    sync_or(false);
+    int next_out = zb;  // the next output plane to read back
+    for (int f = ffirst; f <= flast; ++f, ++k) {
+      if (issuer) {
+        int olo, nb, blo;
+        if ((f & 1) == 0) {
+          olo = f / 2, nb = 1, blo = 2;
+        } else {
+          const bool lo_in = (f - 1) / 2 >= zb, hi_in = (f + 1) / 2 < ze;
+          olo = lo_in ? (f - 1) / 2 : (f + 1) / 2;
+          nb = (lo_in && hi_in) ? 2 : 1;
+          blo = lo_in ? 0 : 1;
+        }
+        const uint32_t idesc = tc_idesc(16 * nb), acc = tmem + 16u * (uint32_t)(olo - zb);
+        const uint32_t sa = smem_u32(slot(f)), sb = sB0 + 256u * (uint32_t)blo;
+#pragma unroll
+        for (int s9 = 0; s9 < 9; ++s9) {
+          const int dx = s9 % 3 - 1, dy = s9 / 3 - 1;
+          const int sp = (dy != 0 ? 2 : 0) + (dx != 0 ? 1 : 0);
+          const int j0 = R + 1 + (dx < 0 ? -1 : 0) + (dy < 0 ? -R : 0);
+          tc_mma(acc, tc_desc(sa + (uint32_t)(2 * sp * L + j0) * 16u, (uint32_t)(L * 16), 128u),
+                 tc_desc(sb + 1536u * (uint32_t)s9, 768u, 128u), true, idesc);
+        }
+        tc_commit(s_done + 8u * (k & 1u));
+        kc = k + 1;
+      }
+      bool fail = false;
+      if (epi) {
+        fail = f > ffirst && !wait_plane(k - 1);
+        if (!fail) {
+          // plane f - 1's MMAs are done: its slot takes plane f + kDnSlots - 1, and the outputs
+          // whose last plane is at most f - 1 are complete
+          const int fa = f + kDnSlots - 1;
+          if (fa <= flast) dn_stage_async(a.in, mi, R, L, p0 - R - 1, x0, fa, slot(fa), threadIdx.x, 128);
+          while (f > ffirst && next_out < ze && min(2 * next_out + 1, mi - 1) <= f - 1) finish(next_out++);
+          cp_async_wait_pending(min(fa, flast) - f - 1);  // plane f + 1 has landed
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+      }
+      if (sync_or(fail)) {
+        timed_out = true;
+        break;
+      }
+    }
+    if (!timed_out) {
+      bool fail = false;
+      if (epi) {
+        fail = !wait_plane(k - 1);
+        while (!fail && next_out < ze) finish(next_out++);
+      }
+      if (sync_or(fail)) timed_out = true;
+    }
+  }
+  if (epi) cp_async_wait_all();
+  if (issuer && timed_out && kc > 0) plane_done(kc - 1);  // MMAs still in flight end before TMEM is freed
+  tc_teardown(tmem, kTcSCols, timed_out, status);
+}
+
 // ------------------------------------------------------------------ transposed stride-2 conv on tcgen05
 // out[o] = sum over taps d with o - d even of W_d in[(o - d) / 2], per direction.  Writing
 // o = 2c + q (q = 0, 1), class q = 0 takes tap d = 0 (source c) and q = 1 takes d = -1 (source
@@ -1228,6 +1427,20 @@ void conv_launch(const ConvArgs& a, cudaStream_t s) {
 // stride-1 convolution on the tensor cores (tcgen05); 3 blocks per SM
 // Tiles per block column along z for a grid of m planes with per_plane tiles each: kTcZ, or
 // fewer so that a small grid still gives about kTcUnits column units.
+// Column height z (<= kTcZ output planes per unit) for `slots` resident blocks and `per_slab`
+// units per z-slab: fewest plane steps on the slowest block, ceil(units / slots) units of
+// `mult` z + `add` steps each (input planes of the column plus about two steps of set-up).
+int wave_column(long long per_slab, int m, long long slots, int mult, int add) {
+  int zc = 1;
+  long long best = -1;
+  for (int z = 1; z <= kTcZ; ++z) {
+    const long long units = per_slab * ((m + z - 1) / z);
+    const long long cost = (units + slots - 1) / slots * (mult * z + add);
+    if (best < 0 || cost < best) best = cost, zc = z;
+  }
+  return zc;
+}
+
 int tc_column(long long per_plane, int m) {
   return (int)std::max<long long>(1, std::min<long long>(kTcZ, per_plane * m / kTcUnits));
 }
@@ -1280,16 +1493,33 @@ void conv_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   const long long per_plane = ((long long)m * R + 127) / 128;
-  const int zc = tc_column(per_plane * nstrips, m);
-  const long long nunits = per_plane * nstrips * ((m + zc - 1) / zc);
   int dev = 0, nsm = 0, smem_sm = 0;  // of the current device (attribute queries are cheap)
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  nsm = std::max(nsm, 1);
-  const int per_sm = std::max(1, std::min(4, smem_sm / (int)(smem + 1024)));
-  k_conv_tc<<<(int)std::min<long long>(nunits, (long long)per_sm * nsm), kTcSThreads, smem, s>>>(a, map, zc, W, nstrips,
-                                                                                                  status);
+  const long long slots = (long long)std::max(1, std::min(4, smem_sm / (int)(smem + 1024))) * std::max(nsm, 1);
+  const int zc = wave_column(per_plane * nstrips, m, slots, 1, 4);  // z + 2 planes per column
+  const long long nunits = per_plane * nstrips * ((m + zc - 1) / zc);
+  k_conv_tc<<<(int)std::min<long long>(nunits, slots), kTcSThreads, smem, s>>>(a, map, zc, W, nstrips, status);
+}
+
+// A stride-2 convolution on tcgen05 (k_down_tc): x-strips of at most kDnStripMax coarse
+// columns, blocks per SM by shared memory (at most 4, the TMEM budget).
+void down_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
+  const int mo = a.m_out;
+  const int nstrips = (mo + kDnStripMax - 1) / kDnStripMax, W = (mo + nstrips - 1) / nstrips;
+  const size_t smem = down_tc_smem(W);
+  cudaFuncSetAttribute(k_down_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_down_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const long long per_plane = ((long long)mo * (W + 2) + 127) / 128;
+  int dev = 0, nsm = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long slots = (long long)std::max(1, std::min(4, smem_sm / (int)(smem + 1024))) * std::max(nsm, 1);
+  const int zc = wave_column(per_plane * nstrips, mo, slots, 2, 3);  // 2 z + 1 planes per column
+  const long long nunits = per_plane * nstrips * ((mo + zc - 1) / zc);
+  k_down_tc<<<(int)std::min<long long>(nunits, slots), kTcSThreads, smem, s>>>(a, zc, W, nstrips, status);
 }
 
 // out = act(conv_G(in; w) + bias + add) * mask
@@ -1300,7 +1530,7 @@ void conv(int gather, const __nv_bfloat16* in, int m_in, const __nv_bfloat16* w,
   if (gather == S1)
     conv_tc_launch(a, status, s);
   else if (gather == DOWN2)
-    conv_launch<DOWN2>(a, s);
+    down_tc_launch(a, status, s);
   else
     up_tc_launch(a, status, s);
 }
@@ -1317,7 +1547,7 @@ void wgrad(UNet& u, int layer, int gather, const __nv_bfloat16* P, int mp, const
     const size_t smem = wgrad_s1_smem(W);
     cudaFuncSetAttribute(k_wgrad_s1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const long long per_plane = ((long long)mp * (W + 2) + 127) / 128;
-    const int zc = tc_column(per_plane * nstrips, mp);
+    const int zc = wave_column(per_plane * nstrips, mp, kWgBlocks, 1, 4);
     blocks = (int)std::min<long long>(kWgBlocks, per_plane * nstrips * ((mp + zc - 1) / zc));
     k_wgrad_s1<<<blocks, kWgThreads, smem, s>>>(P, Q, mp, zc, W, nstrips, u.partial, bpart);
   } else {  // stride 2: P on the coarse grid, Q on the fine grid

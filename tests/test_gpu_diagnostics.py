@@ -112,7 +112,8 @@ def test_metrics_jsonl(nhmf, tmp_path):
     assert all(i["rel_residual"] > 0 and i["seconds"] >= 0 for i in iters)
     for i in iters:  # the iteration's time splits into setup, linear solve and update
         assert min(i["setup_seconds"], i["linear_seconds"], i["update_seconds"]) >= 0
-        assert i["setup_seconds"] + i["linear_seconds"] + i["update_seconds"] <= i["seconds"] + 1e-6
+        # each of the four times is printed to 6 decimals: the sum may exceed by 4 x 0.5 us
+        assert i["setup_seconds"] + i["linear_seconds"] + i["update_seconds"] <= i["seconds"] + 2.5e-6
     apply = [l for l in lines if l["event"] == "tangent_apply"]
     assert len(apply) == 1 and apply[0]["precision"] == "fp64" and apply[0]["strategy"] == "cached"
     assert apply[0]["ms"] > 0 and apply[0]["gdofs"] > 0 and apply[0]["dofs"] == prob.n_dofs
