@@ -19,7 +19,7 @@ namespace {
 
 // Scratch: 6 FP64 vectors of up to kNoAllocMaxDofs entries (r, z, p, q, diagonal, inverse
 // diagonal / true-residual workspace), the reduction partials and 8 scalars; 6.3 MB on
-// every GPU that loads the library, held until the process exits.
+// every device on which a context was created, held until the process exits.
 constexpr long long kNoAllocMaxDofs = 131072;
 constexpr long long kVec = kNoAllocMaxDofs;
 constexpr long long kScratchDoubles = 6 * kVec + kPartialSlots + 8;
