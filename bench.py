@@ -561,7 +561,8 @@ def run_newton(args):
         nhmf.nhmf_unet_create(prob.ctx, args.pairs)
         nhmf.nhmf_unet_set_params(prob.ctx, he_init_flat())
     base = dict(compression=w.compression, load_steps=S, linear_rtol=args.linear_rtol,
-                newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter)
+                newton_rtol=1e-8, inner_rtol=args.inner_rtol, inner_max_iter=args.inner_max_iter,
+                smoother_degree=args.smoother_degree, smoother_range=args.smoother_range)
     outer = {"fp64": nhmf.NHMF_FP64, "df64": nhmf.NHMF_DF64}[args.outer]
     ids = {"plain": nhmf.NHMF_SOLVER_JACOBI_CG, "mixed": nhmf.NHMF_SOLVER_MIXED_FCG,
            "learned": nhmf.NHMF_SOLVER_LEARNED_FCG, "mixed_learned": nhmf.NHMF_SOLVER_MIXED_LEARNED,
@@ -584,7 +585,8 @@ def run_newton(args):
 
     out = {"metric": NEWTON_METRIC, "mode": "newton", "workload": f"{w.name}: " + describe(w) +
            f"; {S} load steps of {w.compression / S:g}", "steps_run": last, "solvers": {},
-           "outer_apply": args.outer + " (flexible solvers; plain Jacobi-CG always FP64)"}
+           "outer_apply": args.outer + " (flexible solvers; plain Jacobi-CG always FP64)",
+           "smoother": {"degree": args.smoother_degree or 3, "range": args.smoother_range or 15.0}}
     states = {}
     for name in solvers:
         u = torch.zeros(w.n_dofs, dtype=torch.float64, device=dev)
@@ -746,6 +748,10 @@ def main():
                     help="newton mode: arithmetic of the flexible solvers' outer applies")
     ap.add_argument("--gmg-pair-iters", type=int, default=4,
                     help="newton mode: pairs per linear solve recorded by mixed_gmg for mixed_gmg_learned")
+    ap.add_argument("--smoother-degree", type=int, default=0,
+                    help="multigrid solvers: Chebyshev steps per smoothing (0: the library's default, 3)")
+    ap.add_argument("--smoother-range", type=float, default=0.0,
+                    help="multigrid solvers: lmax / lmin of the Chebyshev interval (0: the library's default, 15)")
     ap.add_argument("--linear-rtol", type=float, default=1e-8)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--inner-max-iter", type=int, default=1000)
