@@ -9,11 +9,12 @@
 // transposed stride-2 convolution).  Activations are channels-last [voxel][16] BF16 (32 B
 // per voxel, one DRAM sector); inputs and outputs with 3 channels are padded to 16 with
 // zero weights.  Every convolution is an implicit GEMM on the tensor cores, BF16 -> FP32:
-//   stride-1 forward/backward-data (k_conv_tc) and the transposed stride-2 convolution
-//   (k_up_tc): tcgen05 MMAs with accumulators in tensor memory, M = 128 positions, K = 16
-//   input channels, N = output channels (stacked over dz in the stride-1 form);
-//   stride-2 down-convolution (k_conv) and weight gradients (k_wgrad_s1, k_wgrad_s2): mma.sync
-//   m16n8k16; weight gradients as partial sums per block, reduced in a fixed order.
+//   stride-1 forward/backward-data (k_conv_tc), the stride-2 down-convolution and the up
+//   layers' backward-data (k_down_tc), and the transposed stride-2 convolution (k_up_tc):
+//   tcgen05 MMAs with accumulators in tensor memory, M = 128 positions, K = 16 input
+//   channels, N = output channels (stacked over dz in the streaming forms);
+//   weight gradients (k_wgrad_s1, k_wgrad_s2): mma.sync m16n8k16, partial sums per block,
+//   reduced in a fixed order.
 #include <cuda.h>  // CUtensorMap and the encoder's types; the encoder itself comes from the driver at run time
 #include <cuda_bf16.h>
 
@@ -31,7 +32,7 @@ namespace {
 constexpr int kC = 16;
 enum Gather { S1 = 0, DOWN2 = 1, UP2 = 2 };
 enum Kind { CONV = 0, DOWN = 1, UP = 2 };
-constexpr int kConvBlocks = 1216;  // 8 per SM
+constexpr int kConvBlocks = 1216;  // elementwise kernels: 8 blocks of 256 per SM
 constexpr int kWgBlocks = 608;     // weight-gradient partial blocks (4 per SM)
 constexpr int kBgBlocks = 1216;    // bias-gradient partial blocks (8 per SM)
 
@@ -42,29 +43,6 @@ __device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Source coordinate of output coordinate o for tap offset d (-1, 0, 1), or -1 if outside.
-template <int G>
-__device__ __forceinline__ int src1(int o, int d, int m_in) {
-  int s;
-  if (G == S1) {
-    s = o + d;
-  } else if (G == DOWN2) {
-    s = 2 * o + d;
-  } else {
-    const int t = o - d;
-    if (t & 1) return -1;
-    s = t >> 1;
-  }
-  return (s >= 0 && s < m_in) ? s : -1;
-}
-
-template <int G>
-__device__ __forceinline__ long long src_voxel(int i, int j, int k, int dx, int dy, int dz, int m_in) {
-  const int x = src1<G>(i, dx, m_in), y = src1<G>(j, dy, m_in), z = src1<G>(k, dz, m_in);
-  if (x < 0 || y < 0 || z < 0) return -1;
-  return x + (long long)m_in * (y + (long long)m_in * z);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -83,72 +61,6 @@ struct ConvArgs {
   float* out_planar;           // or [3][m_out^3] FP32 (channels 0..2)
   int m_out;
 };
-
-template <int G>
-__global__ void __launch_bounds__(256) k_conv(const ConvArgs a) {
-  __shared__ uint32_t sw[27 * 16 * 12];  // rows of 8 u32 (16 ci) padded to 12: conflict-free B loads
-  const uint32_t* wg = reinterpret_cast<const uint32_t*>(a.w);
-  for (int idx = threadIdx.x; idx < 27 * 16 * 8; idx += blockDim.x) sw[(idx >> 3) * 12 + (idx & 7)] = wg[idx];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const long long mo = a.m_out, nvox = mo * mo * mo, ntiles = (nvox + 15) / 16;
-  const uint32_t* in32 = reinterpret_cast<const uint32_t*>(a.in);
-  for (long long tile = (long long)blockIdx.x * 8 + warp; tile < ntiles; tile += (long long)gridDim.x * 8) {
-    const long long v0 = tile * 16 + g, v1 = v0 + 8;
-    const bool ok0 = v0 < nvox, ok1 = v1 < nvox;
-    const int i0 = int(v0 % mo), j0 = int((v0 / mo) % mo), k0 = int(v0 / (mo * mo));
-    const int i1 = int(v1 % mo), j1 = int((v1 / mo) % mo), k1 = int(v1 / (mo * mo));
-    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 3
-    for (int tap = 0; tap < 27; ++tap) {
-      const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
-      const long long s0 = ok0 ? src_voxel<G>(i0, j0, k0, dx, dy, dz, a.m_in) : -1;
-      const long long s1 = ok1 ? src_voxel<G>(i1, j1, k1, dx, dy, dz, a.m_in) : -1;
-      const uint32_t A0 = s0 >= 0 ? __ldg(in32 + s0 * 8 + t) : 0u;
-      const uint32_t A1 = s1 >= 0 ? __ldg(in32 + s1 * 8 + t) : 0u;
-      const uint32_t A2 = s0 >= 0 ? __ldg(in32 + s0 * 8 + 4 + t) : 0u;
-      const uint32_t A3 = s1 >= 0 ? __ldg(in32 + s1 * 8 + 4 + t) : 0u;
-      const uint32_t* w0 = sw + (tap * 16 + g) * 12;
-      const uint32_t* w1 = sw + (tap * 16 + 8 + g) * 12;
-      mma16816(acc0, A0, A1, A2, A3, w0[t], w0[4 + t]);
-      mma16816(acc1, A0, A1, A2, A3, w1[t], w1[4 + t]);
-    }
-    auto emit = [&](long long v, int ch, float x0, float x1) {
-      if (a.bias) {
-        x0 += a.bias[ch];
-        x1 += a.bias[ch + 1];
-      }
-      if (a.add) {
-        const __nv_bfloat162 ad = *reinterpret_cast<const __nv_bfloat162*>(a.add + v * kC + ch);
-        x0 += __low2float(ad);
-        x1 += __high2float(ad);
-      }
-      if (a.relu) {
-        x0 = fmaxf(x0, 0.f);
-        x1 = fmaxf(x1, 0.f);
-      }
-      if (a.mask) {
-        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kC + ch);
-        x0 = __low2float(mk) > 0.f ? x0 : 0.f;
-        x1 = __high2float(mk) > 0.f ? x1 : 0.f;
-      }
-      if (a.out_planar) {
-        if (ch < 3) a.out_planar[ch * nvox + v] = x0;
-        if (ch + 1 < 3) a.out_planar[(ch + 1) * nvox + v] = x1;
-      } else {
-        *reinterpret_cast<__nv_bfloat162*>(a.out + v * kC + ch) = __floats2bfloat162_rn(x0, x1);
-      }
-    };
-    if (ok0) {
-      emit(v0, 2 * t, acc0[0], acc0[1]);
-      emit(v0, 8 + 2 * t, acc1[0], acc1[1]);
-    }
-    if (ok1) {
-      emit(v1, 2 * t, acc0[2], acc0[3]);
-      emit(v1, 8 + 2 * t, acc1[2], acc1[3]);
-    }
-  }
-}
 
 // Sum of the per-block weight-gradient partials [nblocks][27 * 256] in a fixed order (a block
 // takes 32 consecutive entries, its 32 warps sum every 32nd partial block - coalesced rows -
@@ -1419,14 +1331,6 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_s2(const __nv_bfloat16* __
   }
 }
 
-template <int G>
-void conv_launch(const ConvArgs& a, cudaStream_t s) {
-  k_conv<G><<<kConvBlocks, 256, 0, s>>>(a);
-}
-
-// stride-1 convolution on the tensor cores (tcgen05); 3 blocks per SM
-// Tiles per block column along z for a grid of m planes with per_plane tiles each: kTcZ, or
-// fewer so that a small grid still gives about kTcUnits column units.
 // Column height z (<= kTcZ output planes per unit) for `slots` resident blocks and `per_slab`
 // units per z-slab: fewest plane steps on the slowest block, ceil(units / slots) units of
 // `mult` z + `add` steps each (input planes of the column plus about two steps of set-up).
@@ -1441,6 +1345,8 @@ int wave_column(long long per_slab, int m, long long slots, int mult, int add) {
   return zc;
 }
 
+// Tiles per block column along z of the transposed convolution, for a grid of m planes with
+// per_plane tiles each: kTcZ, or fewer so that a small grid still gives about kTcUnits units.
 int tc_column(long long per_plane, int m) {
   return (int)std::max<long long>(1, std::min<long long>(kTcZ, per_plane * m / kTcUnits));
 }
@@ -1451,7 +1357,11 @@ void up_tc_launch(const ConvArgs& a, unsigned* status, cudaStream_t s) {
   const long long mi = a.m_in, per_plane = (mi * (mi + 1) + 127) / 128;
   const int zc = tc_column(per_plane, (int)mi);
   const long long nunits = per_plane * ((mi + zc - 1) / zc);
-  k_up_tc<<<(int)std::min<long long>(nunits, 4 * 152), kTcThreads, smem, s>>>(a, zc, status);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long slots = 4ll * std::max(nsm, 1);  // 4 blocks per SM (launch bounds, TMEM)
+  k_up_tc<<<(int)std::min<long long>(nunits, slots), kTcThreads, smem, s>>>(a, zc, status);
 }
 
 typedef CUresult (*TensorMapEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
