@@ -13,6 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnhmf.so")
 
 NHMF_OK = 0
+(NHMF_ERR_ARG, NHMF_ERR_CUDA, NHMF_ERR_OOM, NHMF_ERR_NONPOS_J, NHMF_ERR_NONFINITE, NHMF_ERR_BREAKDOWN,
+ NHMF_ERR_NOT_CONVERGED, NHMF_ERR_STATE) = range(1, 9)
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONPOS_J",
                 5: "ERR_NONFINITE", 6: "ERR_BREAKDOWN", 7: "ERR_NOT_CONVERGED", 8: "ERR_STATE"}
 NHMF_FP64, NHMF_FP32, NHMF_DF64 = 0, 1, 2
